@@ -1,0 +1,262 @@
+"""FP64 CPU oracle for the Heisenberg spin-glass Monte Carlo (test infrastructure).
+
+Only tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg may
+import this package.  It wraps ``hsg_oracle.c`` (plain C, binary64, built with
+``-ffp-contract=off``) through ctypes and drives it in the order the method
+prescribes: a step is n_hb heat-bath sweeps, n_or over-relaxation sweeps, an
+energy evaluation and one parallel-tempering pass (Sec. 3.2).  Each sweep is an
+even half-sweep followed by an odd half-sweep (Sec. 3.1).
+
+Nothing here is shared with the CUDA library; the two agree only on the
+conventions written in ``hsg_oracle.h``.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import shutil
+import subprocess
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hsg_oracle.c")
+_LIB = os.path.join(_HERE, "libhsg_oracle.so")
+
+CODECS = {"none": 0, "fp32": 0, "fp16": 1, "bf16": 2, "angle16": 3, "oct16": 4}
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library next to its source (gcc, -O2, no FP contraction)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "hsg_oracle.h"))):
+        return _LIB
+    cc = os.environ.get("CC", "gcc")
+    if shutil.which(cc) is None:
+        raise RuntimeError("no C compiler for the oracle")
+    base = [cc, "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+            _SRC, "-o", _LIB + ".tmp", "-lm"]
+    try:
+        subprocess.run(base[:6] + ["-fopenmp"] + base[6:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        dp = ctypes.POINTER(ctypes.c_double)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        c_int, c_long, u64, u32 = ctypes.c_int, ctypes.c_long, ctypes.c_uint64, ctypes.c_uint32
+        sig = {
+            "orc_philox4x32_10": (None, [u32p, u32p, u32p]),
+            "orc_philox_many": (None, [u32p, c_long, u64, u32p]),
+            "orc_uniform": (ctypes.c_double, [u32]),
+            "orc_codec_roundtrip_many": (None, [dp, c_long, c_int]),
+            "orc_round_fp16": (ctypes.c_double, [ctypes.c_double]),
+            "orc_round_bf16": (ctypes.c_double, [ctypes.c_double]),
+            "orc_init_spins": (None, [dp, c_int, c_int, u64, u64, c_int]),
+            "orc_local_field": (None, [dp, dp, dp, c_int, c_long, dp]),
+            "orc_hb_many": (None, [dp, dp, dp, dp, dp, c_long]),
+            "orc_or_half": (None, [dp, dp, dp, c_int, c_int, c_int, c_int]),
+            "orc_hb_half": (None, [dp, dp, dp, c_int, c_int, c_int, dp, u64, u64, u32, c_int]),
+            "orc_energy": (None, [dp, dp, dp, c_int, c_int, dp]),
+            "orc_pt": (None, [dp, dp, i32p, c_int, c_int, u64, u64, u32, i32p]),
+            "orc_measure": (None, [dp, c_int, c_int, i32p, dp, dp]),
+            "orc_num_threads": (c_int, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _dp(a):
+    return None if a is None else _p(a, ctypes.c_double)
+
+
+# --- thin functional wrappers -------------------------------------------------
+
+def philox(ctr: np.ndarray, seed: int) -> np.ndarray:
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    out = np.empty_like(ctr)
+    lib().orc_philox_many(_p(ctr, ctypes.c_uint32), ctr.shape[0], seed, _p(out, ctypes.c_uint32))
+    return out
+
+
+def uniform(x: np.ndarray) -> np.ndarray:
+    f = lib().orc_uniform
+    return np.array([f(int(v)) for v in np.asarray(x, dtype=np.uint32).ravel()])
+
+
+def codec_roundtrip(v: np.ndarray, codec: str) -> np.ndarray:
+    v = np.ascontiguousarray(v, dtype=np.float64).copy()
+    lib().orc_codec_roundtrip_many(_dp(v), v.size // 3, CODECS[codec])
+    return v
+
+
+def local_field(s_sys: np.ndarray, J: np.ndarray, H: Optional[np.ndarray], L: int, i: int):
+    h = np.zeros(3)
+    lib().orc_local_field(_dp(np.ascontiguousarray(s_sys)), _dp(np.ascontiguousarray(J)),
+                          _dp(None if H is None else np.ascontiguousarray(H)), L, i, _dp(h))
+    return h
+
+
+def hb_moves(s, h, beta, u1, u2) -> np.ndarray:
+    """Heat-bath draws for independent spins in fixed fields h (arrays [n,3], [n])."""
+    s = np.ascontiguousarray(s, dtype=np.float64).copy()
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    n = s.shape[0]
+    b = np.ascontiguousarray(np.broadcast_to(beta, (n,)), dtype=np.float64)
+    u1 = np.ascontiguousarray(u1, dtype=np.float64)
+    u2 = np.ascontiguousarray(u2, dtype=np.float64)
+    lib().orc_hb_many(_dp(s), _dp(h), _dp(b), _dp(u1), _dp(u2), n)
+    return s
+
+
+def energy(s: np.ndarray, J: np.ndarray, H: Optional[np.ndarray], L: int) -> np.ndarray:
+    W = s.shape[0]
+    E = np.zeros(W)
+    lib().orc_energy(_dp(np.ascontiguousarray(s)), _dp(np.ascontiguousarray(J)),
+                     _dp(None if H is None else np.ascontiguousarray(H)), L, W, _dp(E))
+    return E
+
+
+def pt(E, temps, perm, R_O, R_T, chain_base, seed, pt_step):
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    temps = np.ascontiguousarray(temps, dtype=np.float64)
+    perm = np.ascontiguousarray(perm, dtype=np.int32).copy()
+    acc = np.zeros((R_O, max(R_T - 1, 1)), dtype=np.int32)
+    lib().orc_pt(_dp(E), _dp(temps), _p(perm, ctypes.c_int32), R_O, R_T, chain_base, seed,
+                 pt_step, _p(acc, ctypes.c_int32))
+    return perm, acc
+
+
+class OracleSample:
+    """State of one disorder sample: W = n_replicas * n_temps systems."""
+
+    def __init__(self, L, J, H, temps, n_replicas, sys_base, chain_base, seed, codec):
+        self.L = int(L)
+        self.N = self.L ** 3
+        self.J = np.ascontiguousarray(J, dtype=np.float64).reshape(self.N, 3)
+        self.H = None if H is None else np.ascontiguousarray(H, dtype=np.float64).reshape(self.N, 3)
+        self.temps = np.ascontiguousarray(temps, dtype=np.float64)
+        self.R_T = len(self.temps)
+        self.R_O = int(n_replicas)
+        self.W = self.R_T * self.R_O
+        self.sys_base = int(sys_base)
+        self.chain_base = int(chain_base)
+        self.seed = int(seed)
+        self.codec = codec
+        self.s = np.zeros((self.W, self.N, 3))
+        lib().orc_init_spins(_dp(self.s), self.L, self.W, self.sys_base, self.seed, codec)
+        self.perm = np.tile(np.arange(self.R_T, dtype=np.int32), (self.R_O, 1))
+
+    def beta_sys(self) -> np.ndarray:
+        b = np.zeros(self.W)
+        for r in range(self.R_O):
+            for t in range(self.R_T):
+                b[r * self.R_T + self.perm[r, t]] = 1.0 / self.temps[t]
+        return b
+
+    def or_half(self, parity):
+        lib().orc_or_half(_dp(self.s), _dp(self.J), _dp(self.H), self.L, self.W, parity, self.codec)
+
+    def hb_half(self, parity, sweep):
+        beta = self.beta_sys()
+        lib().orc_hb_half(_dp(self.s), _dp(self.J), _dp(self.H), self.L, self.W, parity, _dp(beta),
+                          self.sys_base, self.seed, sweep, self.codec)
+
+    def energies(self) -> np.ndarray:
+        E = np.zeros(self.W)
+        lib().orc_energy(_dp(self.s), _dp(self.J), _dp(self.H), self.L, self.W, _dp(E))
+        return E
+
+    def pt(self, E, pt_step):
+        self.perm, acc = pt(E, self.temps, self.perm, self.R_O, self.R_T, self.chain_base,
+                            self.seed, pt_step)
+        return acc
+
+    def measure(self):
+        q = np.zeros((self.R_T, 3, 3))
+        qk = np.zeros((self.R_T, 3, 3, 3, 2))
+        if self.R_O >= 2:
+            lib().orc_measure(_dp(self.s), self.L, self.R_T, _p(self.perm, ctypes.c_int32),
+                              _dp(q), _dp(qk))
+        E = self.energies()
+        E_slot = np.array([[E[r * self.R_T + self.perm[r, t]] for t in range(self.R_T)]
+                           for r in range(self.R_O)])
+        return {"E": E_slot, "q": q, "qk": qk, "perm": self.perm.copy()}
+
+
+class OracleSim:
+    """The Markov chain of the library, on the CPU in FP64, for a batch of samples.
+
+    ``samples`` is a list of objects with attributes L, J, H, temps.  System and
+    chain ids are numbered across the batch in sample order, as in the library.
+    """
+
+    def __init__(self, samples: Sequence, n_replicas: int, seed: int, codec: str = "none"):
+        self.seed = int(seed)
+        self.codec = CODECS[codec]
+        self.samples: List[OracleSample] = []
+        sys_base = chain_base = 0
+        for smp in samples:
+            o = OracleSample(smp.L, smp.J, smp.H, smp.temps, n_replicas, sys_base, chain_base,
+                             seed, self.codec)
+            self.samples.append(o)
+            sys_base += o.W
+            chain_base += o.R_O
+        self.sweep = 0
+        self.pt_step = 0
+
+    def sweep_or(self, n: int = 1):
+        for _ in range(n):
+            for o in self.samples:
+                o.or_half(0)
+                o.or_half(1)
+            self.sweep += 1
+
+    def sweep_hb(self, n: int = 1):
+        for _ in range(n):
+            for o in self.samples:
+                o.hb_half(0, self.sweep)
+                o.hb_half(1, self.sweep)
+            self.sweep += 1
+
+    def energies(self) -> List[np.ndarray]:
+        return [o.energies() for o in self.samples]
+
+    def pt_exchange(self, energies: Optional[List[np.ndarray]] = None):
+        if energies is None:
+            energies = self.energies()
+        acc = [o.pt(E, self.pt_step) for o, E in zip(self.samples, energies)]
+        self.pt_step += 1
+        return acc
+
+    def step(self, n: int = 1, n_hb: int = 1, n_or: int = 5):
+        for _ in range(n):
+            self.sweep_hb(n_hb)
+            self.sweep_or(n_or)
+            self.pt_exchange()
+
+    def measure(self):
+        return [o.measure() for o in self.samples]
+
+    def spins(self) -> List[np.ndarray]:
+        return [o.s for o in self.samples]
