@@ -1,0 +1,455 @@
+#!/usr/bin/env python
+"""Benchmark: ns per spin update of the heat-bath + over-relaxation + parallel
+tempering step on one GB300 (and N GPUs as independent replicas).
+
+A step is the whole hot path once: 1 heat-bath sweep, 5 over-relaxation
+sweeps, FP64 energies and one parallel-tempering pass (hsg_step), with the
+overlap measurement (hsg_measure) every 10th step.  t_update follows the
+paper's definition, t_run / [(n_OR + n_HB) * steps * systems * N] (Sec. 4).
+
+Default workload: L = 128, 2 replicas x 24 temperatures in [0.08, 0.3], FP16
+spins and couplings, H_r = 0.1 (100.7M spins, 604 MB of spin state, larger
+than L2, so no flush is needed between steps).  The line also carries the
+plain-FP32 form of the same lattice and the plain-FP32 L = 32 production
+shape (25 MB, L2 flushed between timed steps) for the compressed-vs-plain
+comparison.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ns per spin update"
+UNIT = "ns/spin-update"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="L128_fp16")
+    ap.add_argument("--measure-every", type=int, default=10)
+    ap.add_argument("--no-extras", action="store_true", help="skip the plain-FP32 comparison lines")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.samples = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for row in csv.reader(io.StringIO(out)):
+            if len(row) < 9:
+                continue
+            try:
+                self.samples.append([x.strip() for x in row])
+            except Exception:
+                pass
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.samples if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.samples if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.samples:
+            for k, n in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def algorithmic_half_sweep_bytes(ctx, wl):
+    """Bytes one half-sweep launch must move in the two-pass form: per updated
+    spin its own read + write and one read of the opposite-parity spin it sees
+    (3 S per update), plus the 6 bonds and 3 field components of every updated
+    site (shared by the W systems of the sample)."""
+    S = {"fp32": 12, "fp16": 6, "bf16": 6, "angle16": 4, "oct16": 4}[wl.precision]
+    jb = 2 if wl.j_fp16 else 4
+    sites = sum(s.L ** 3 for s in wl.samples) // 2
+    return sites * (3 * S * ctx.W + 9 * jb)
+
+
+def run_ours(args, wl, torch, dev, rank, world, measure_every, do_roofline=True):
+    from paper_1204_6192_gb300 import hsg
+    stream = torch.cuda.Stream(device=dev)
+    ctx = hsg.Context(wl.samples, wl.n_replicas, wl.seed + rank, precision=wl.precision,
+                      j_fp16=wl.j_fp16, n_hb=wl.n_hb, n_or=wl.n_or, device=dev.index,
+                      stream=stream.cuda_stream)
+    info = ctx.info()
+    spins = info.total_spins
+    sweeps = wl.n_hb + wl.n_or
+    n_meas = 0
+    for k in range(args.warmup):
+        ctx.step(1)
+        if measure_every and (k + 1) % measure_every == 0:
+            ctx.measure()
+    ctx.measure()
+    ctx.sync()
+    res = {"ctx": ctx, "stream": stream}
+    return res, spins, sweeps
+
+
+def timed_steps(ctx, stream, torch, steps, measure_every, flush=None):
+    """Time `steps` steps with CUDA events on the context's stream.  With
+    `flush`, L2 is flushed before every step and only the steps are timed."""
+    n_meas = 0
+    if flush is None:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(steps):
+            ctx.step(1)
+            if measure_every and (k + 1) % measure_every == 0:
+                ctx.measure()
+                n_meas += 1
+        t1.record(stream)
+        t1.synchronize()
+        return t0.elapsed_time(t1), n_meas
+    total = 0.0
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.add_(1.0)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        ctx.step(1)
+        if measure_every and (k + 1) % measure_every == 0:
+            ctx.measure()
+            n_meas += 1
+        t1.record(stream)
+        t1.synchronize()
+        total += t0.elapsed_time(t1)
+    return total, n_meas
+
+
+def roofline(ctx, stream, torch, wl, reps=20):
+    """Average duration of the over-relaxation half-sweep kernel (the dominant
+    kernel: 10 of the 15 launches of a step), timed with CUDA events on its
+    stream: `reps` OR sweeps = 2 * reps half-sweep launches (+1 counter bump)."""
+    ctx.sweep_or(2)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    ctx.sweep_or(reps)
+    t1.record(stream)
+    t1.synchronize()
+    ms_half = t0.elapsed_time(t1) / (2 * reps)
+    # heat-bath half-sweep for the record
+    t0.record(stream)
+    ctx.sweep_hb(reps // 4 or 1)
+    t1.record(stream)
+    t1.synchronize()
+    ms_hb = t0.elapsed_time(t1) / (2 * (reps // 4 or 1))
+    return ms_half, ms_hb
+
+
+def traffic_summary(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if it is current."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        e = d.get(kernel_key)
+        if not e:
+            return None
+        from paper_1204_6192_gb300 import build as b
+        if e.get("source_hash") != b.source_hash():
+            return None
+        return e.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+def e2e_run(ctx, wl, torch, steps):
+    """Through the public API with host buffers: every step uploads the spin
+    state from pinned host memory (hsg_set_spins), runs hsg_step and reads the
+    observables back (hsg_measure); host wall clock around it."""
+    import numpy as np
+    total = ctx.info().total_spins * 3
+    pinned = torch.empty(total, dtype=torch.float32, pin_memory=True)
+    host = pinned.numpy()
+    ctx.get_spins(out=host)
+    obs_bytes = (ctx.n_samples * ctx.n_replicas * ctx.n_temps * (8 + 4) +
+                 ctx.n_samples * ctx.n_temps * (9 + 54) * 8)
+    ctx.set_spins(host)
+    ctx.step(1)
+    ctx.measure()
+    ctx.sync()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ctx.set_spins(host)
+        ctx.step(1)
+        ctx.measure()
+    ctx.sync()
+    dt = time.perf_counter() - t0
+    return dt, total * 4, obs_bytes
+
+
+class OracleSample:
+    """The FP64 oracle as it stands, on this host's cores, on a bounded sample of
+    the workload: the same lattice, couplings and storage codec, 16 of the
+    systems (2 replicas x the 8 lowest temperatures).  One call of step() is one
+    sweep; heat-bath and over-relaxation sweeps alternate in the 1:5 ratio of
+    the step, with energies and a PT pass after every sixth sweep."""
+
+    def __init__(self, wl):
+        import oracle
+        from paper_1204_6192_gb300 import inputs
+        oracle.build()
+        self.threads = int(oracle.lib().orc_num_threads())
+        smp = wl.samples[0]
+        n_t = min(8, len(smp.temps))
+        sub = inputs.Sample(L=smp.L,
+                            J=inputs.round_fp16(smp.J) if wl.j_fp16 else smp.J,
+                            H=inputs.round_fp16(smp.H) if wl.j_fp16 else smp.H,
+                            temps=smp.temps[:n_t])
+        self.codec = "none" if wl.precision == "fp32" else wl.precision
+        self.sim = oracle.OracleSim([sub], 2, wl.seed, codec=self.codec)
+        self.W = 2 * n_t
+        self.L = smp.L
+        self.sweeps = 0
+
+    def step(self):
+        if self.sweeps % 6 == 0:
+            self.sim.sweep_hb(1)
+        else:
+            self.sim.sweep_or(1)
+        self.sweeps += 1
+        if self.sweeps % 6 == 0:
+            self.sim.pt_exchange()
+        return self.W * self.L ** 3
+
+    def describe(self, sweeps, updates, dt):
+        return (f"L={self.L}, {self.codec} storage emulated, {self.W} systems, {sweeps} sweeps "
+                f"(HB:OR 1:5, PT every 6), {updates} spin updates in {dt:.1f} s")
+
+
+def cpu_baseline(wl, max_seconds=20.0):
+    ob = OracleSample(wl)
+    updates = 0
+    t0 = time.perf_counter()
+    n = 0
+    while n < 6 or time.perf_counter() - t0 < max_seconds:
+        updates += ob.step()
+        n += 1
+        if time.perf_counter() - t0 > 3 * max_seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(dt * 1e9 / updates, 4), "unit": UNIT,
+            "cores": min(ob.threads, ob.W), "kind": "oracle",
+            "sample": ob.describe(n, updates, dt)}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    from paper_1204_6192_gb300 import build as cuda_build, inputs
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cuda_build.build()
+
+    wl = inputs.workload(args.workload)
+    # every rank runs its own disorder sample (independent problems, no collective)
+    if rank:
+        import numpy as np
+        rng = np.random.default_rng(1000 + rank)
+        for s in wl.samples:
+            s.J = inputs.gaussian_couplings(s.L, rng)
+    res, spins, sweeps = run_ours(args, wl, torch, dev, rank, world, args.measure_every)
+    ctx, stream = res["ctx"], res["stream"]
+
+    gpu_index = local
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    if cvd and cvd.split(",")[local].strip().isdigit():
+        gpu_index = int(cvd.split(",")[local])
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    time.sleep(0.3)
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ms, n_meas = timed_steps(ctx, stream, torch, args.steps, args.measure_every)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms_half, ms_hb = roofline(ctx, stream, torch, wl)
+    clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+
+    updates_rank = sweeps * spins * args.steps
+    updates = updates_rank * world
+    value = ms * 1e6 / updates
+    peak, peak_kind = measured_peak()
+    A = algorithmic_half_sweep_bytes(ctx, wl)
+    achieved = A / (ms_half * 1e-3) / 1e9
+    traffic = traffic_summary(f"or_half_sweep_{wl.precision}")
+
+    line = {
+        "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 5),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "L": wl.samples[0].L, "n_samples": len(wl.samples),
+                   "replicas": wl.n_replicas, "temps": wl.n_temps, "spins": spins,
+                   "storage": wl.precision, "couplings": "fp16" if wl.j_fp16 else "fp32",
+                   "step": f"{wl.n_hb} HB + {wl.n_or} OR + energies + PT, measure every "
+                           f"{args.measure_every}",
+                   "l2": "state larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+        "spin_updates_per_s": round(updates / (ms * 1e-3), 1),
+        "gpu_launches": args.steps * (2 * sweeps + 3) + n_meas * 4,
+        "roofline": {"bound": "hbm", "kernel": f"k_half_sweep OR {wl.precision}",
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                     "traffic": traffic, "algorithmic_bytes_per_launch": A,
+                     "ms_per_launch": round(ms_half, 5), "hb_ms_per_launch": round(ms_hb, 5)},
+        "clocks": clocks.summary(),
+    }
+
+    if not args.no_e2e:
+        k = min(args.steps, 20)
+        dt, h2d, d2h = e2e_run(ctx, wl, torch, k)
+        line["e2e"] = {"value": round(dt * 1e9 / (sweeps * spins * k), 6), "unit": UNIT,
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                       "steps": k, "api": "hsg_set_spins(host) + hsg_step + hsg_measure(host)"}
+    ctx.close()
+
+    if not args.no_extras and world == 1:
+        extras = {}
+        for name, flush in (("L128_fp32", False), ("L32_fp32", True)):
+            w2 = inputs.workload(name)
+            r2, sp2, sw2 = run_ours(args, w2, torch, dev, rank, world, args.measure_every)
+            buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev) if flush else None
+            k2 = max(20, args.steps // (2 if flush else 3))
+            ms2, _ = timed_steps(r2["ctx"], r2["stream"], torch, k2, args.measure_every, flush=buf)
+            mh2, _ = roofline(r2["ctx"], r2["stream"], torch, w2)
+            A2 = algorithmic_half_sweep_bytes(r2["ctx"], w2)
+            extras[name] = {"value": round(ms2 * 1e6 / (sw2 * sp2 * k2), 6), "unit": UNIT,
+                            "steps": k2, "l2": "flushed between steps" if flush else "state > L2",
+                            "or_half_sweep_GBps": round(A2 / (mh2 * 1e-3) / 1e9, 1),
+                            "or_half_sweep_frac": round(A2 / (mh2 * 1e-3) / 1e9 / peak, 4)}
+            r2["ctx"].close()
+            del buf
+        line["plain_fp32"] = extras
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args, world, rank):
+    """Each step is one sweep of the oracle on the bounded sample above; host
+    wall clock per step; mean over the timed steps."""
+    if rank != 0:
+        return
+    from paper_1204_6192_gb300 import inputs
+    wl = inputs.workload(args.workload)
+    ob = OracleSample(wl)
+    for _ in range(args.warmup):
+        ob.step()
+    updates = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        updates += ob.step()
+    dt = time.perf_counter() - t0
+    value = dt * 1e9 / updates
+    sample = ob.describe(args.steps, updates, dt)
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt * 1e3 / args.steps, 3),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "L": wl.samples[0].L, "storage": wl.precision,
+                       "step": "one oracle sweep of a 16-system sample (HB:OR 1:5, PT every 6)"},
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT,
+                             "cores": min(ob.threads, ob.W), "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

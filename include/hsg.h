@@ -1,0 +1,203 @@
+/*
+ * hsg — Heisenberg spin-glass Monte Carlo on one GB300 (sm_103a).
+ *
+ * C ABI of the CUDA library libhsg.so.  It runs the hot path of the method of
+ * Yavors'kii & Weigel, "Optimized GPU simulation of continuous-spin glass
+ * models" (arXiv:1204.6192): checkerboard heat-bath (HB) and over-relaxation
+ * (OR) sweeps of the 3D Edwards-Anderson Heisenberg model in a random field,
+ * Eq. (1), for many temperatures, replicas and disorder samples at once, the
+ * parallel-tempering (PT) exchange of Eq. (4) and the measurements of Eq. (5)
+ * and its k-dependent form.  No argument is a framework type: plain pointers
+ * and sizes only.
+ *
+ * Conventions
+ *   lattice    L^3 periodic simple cubic, L even and >= 4.  Site index
+ *              i = x + L*(y + L*z), parity p(i) = (x + y + z) mod 2.
+ *   J          float[N][3], J[i][a] = coupling of the bond (i, i + e_a),
+ *              a = x, y, z.  Every bond appears once (Eq. 1 reading).
+ *   H          float[N][3] random field, or NULL for H = 0.
+ *   systems    a sample (one disorder realisation) holds W = n_replicas *
+ *              n_temps systems; system w = r * n_temps + j (replica r, memory
+ *              slot j).  All samples of a context have the same n_temps and
+ *              n_replicas; their L may differ.  Global system id of sample s:
+ *              s * Wp + w with Wp = W rounded up to a multiple of 8.  Global
+ *              chain id: s * n_replicas + r.
+ *   perm       int32[n_samples][n_replicas][n_temps]: perm[s][r][t] = memory
+ *              slot j of replica r that currently holds temperature t.
+ *              Initially perm[s][r][t] = t.  PT permutes temperatures, never
+ *              spins (Sec. 3.2).
+ *   spins      host or device float[...][W][N][3] in sample order: for each
+ *              sample, its W systems in memory-slot order, each N sites, each
+ *              (x, y, z) components.
+ *   random     Philox4x32-10 (Salmon et al., SC'11), key = (seed & 0xffffffff,
+ *              seed >> 32); uniforms u(x) = (2*(x >> 9) + 1) * 2^-24.
+ *              Initial spins:  counter (i, gsys >> 1, 0, 0)
+ *              HB sweep n:     counter (i, gsys >> 1, n, 1)
+ *              PT call m:      counter (k, gchain, m, 2), word 0
+ *              A system uses words 2*(gsys & 1) and 2*(gsys & 1) + 1.  The
+ *              sweep counter n counts every sweep, OR or HB, since creation.
+ *   moves      sweep = even half-sweep then odd half-sweep (Sec. 3.1).
+ *              OR: s' = 2 (s.h)/(h.h) h - s, s' = s if h = 0 (Eq. 3).
+ *              HB: a = beta |h|, d = -log1p((1-u1) expm1(-2a)) / a (a > 1e-12,
+ *              else d = 2 (1 - u1)), cos t = 1 - d, sin t = sqrt(d (2 - d)),
+ *              azimuth 2 pi u2 in the Duff et al. (JCGT 2017) frame around h
+ *              (Eq. 2).  Every move ends with s <- s / |s| and the storage codec.
+ *   step       hsg_step: n_hb HB sweeps, n_or OR sweeps, FP64 energies, one PT
+ *              pass (Sec. 3.2, steps 1-10 with n_T = 1).
+ *
+ * Errors: every call returns hsg_status.  The first device error is sticky:
+ * later calls on the same context return it until hsg_destroy.  Calls are
+ * asynchronous on the context's stream except those that return host data
+ * (hsg_get_*, hsg_energies, hsg_measure, hsg_sync), which synchronise.
+ * A context must be used from one host thread at a time.
+ */
+#ifndef HSG_H
+#define HSG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hsg_ctx hsg_ctx;   /* opaque, owned by the library */
+
+typedef enum {
+  HSG_OK = 0,
+  HSG_EINVAL = 1,     /* bad argument (checked on the host before any device work) */
+  HSG_ENOMEM = 2,     /* device or host allocation failed */
+  HSG_ECUDA = 3,      /* a CUDA call or kernel failed; sticky */
+  HSG_ETIMEOUT = 4,   /* a bounded device wait ran out; sticky */
+  HSG_ESTATE = 5      /* call not valid in the context's current state */
+} hsg_status;
+
+typedef enum {
+  HSG_FP32 = 0,       /* 3 x binary32 per spin (12 bytes) */
+  HSG_FP16 = 1,       /* 3 x binary16, round to nearest even (6 bytes) */
+  HSG_BF16 = 2,       /* 3 x bfloat16, round to nearest even (6 bytes) */
+  HSG_ANGLE16 = 3,    /* polar angle and azimuth, 16 bits each (4 bytes) */
+  HSG_OCT16 = 4       /* octahedral map (Cigolle et al. 2014), 16 bits each (4 bytes) */
+} hsg_precision;
+
+typedef struct {
+  int precision;      /* hsg_precision of the stored spins; arithmetic is always FP32 */
+  int j_fp16;         /* nonzero: J and H stored as binary16 (rounded to nearest even) */
+  int fast_math;      /* nonzero: HB uses the hardware approximate log/exp (Table 1 "fast_math") */
+  int n_hb_per_step;  /* HB sweeps per hsg_step (default 1) */
+  int n_or_per_step;  /* OR sweeps per hsg_step (default 5) */
+  int device;         /* CUDA device ordinal (default 0) */
+  void* stream;       /* cudaStream_t to use; NULL: the library creates a non-blocking stream */
+  int variant;        /* sweep kernel schedule: 0 = automatic, else an HSG_VARIANT_* value */
+} hsg_options;
+
+enum {
+  HSG_VARIANT_AUTO = 0,
+  HSG_VARIANT_TWO_PASS = 1,   /* one launch per half-sweep over all samples */
+  HSG_VARIANT_RESIDENT = 2    /* whole sweeps of a small lattice held in shared memory */
+};
+
+/* Fill *opt with the defaults listed above. */
+void hsg_default_options(hsg_options* opt);
+
+/*
+ * Create a context holding one disorder sample (Sec. 3.2: R = R_T R_O systems
+ * with the same J and H).  temps: n_temps strictly increasing positive
+ * temperatures (host, copied).  J, H: host arrays as described above, copied;
+ * the caller keeps ownership.  Spins start uniform on the sphere from the
+ * Philox init stream.  Returns HSG_EINVAL for odd L, L < 4, n_temps < 1,
+ * n_replicas < 1, unsorted or non-finite temperatures, non-finite J or H.
+ */
+hsg_status hsg_create(hsg_ctx** out, int L, const double* temps, int n_temps, int n_replicas,
+                      const float* J, const float* H, uint64_t seed, const hsg_options* opt);
+
+/*
+ * Create a context holding n_samples independent disorder samples, each with
+ * its own L[s], temperatures temps[s * n_temps + t], J[s] and H[s] (H[s] or H
+ * itself may be NULL).  All samples share n_temps, n_replicas, the seed and
+ * the options; they are updated together by every call (Sec. 3.2, the
+ * disorder average as trivial parallelism).
+ */
+hsg_status hsg_create_batch(hsg_ctx** out, int n_samples, const int* L, const double* temps,
+                            int n_temps, int n_replicas, const float* const* J,
+                            const float* const* H, uint64_t seed, const hsg_options* opt);
+
+/* n_sweeps full OR sweeps (Eq. 3), each an even then an odd half-sweep. */
+hsg_status hsg_sweep_or(hsg_ctx* ctx, int n_sweeps);
+
+/* n_sweeps full HB sweeps (Eq. 2) at each system's current temperature. */
+hsg_status hsg_sweep_hb(hsg_ctx* ctx, int n_sweeps);
+
+/* Recompute every system's energy in FP64 (Eq. 1) and run one PT pass (Eq. 4). */
+hsg_status hsg_pt_exchange(hsg_ctx* ctx);
+
+/* One PT pass with caller-supplied energies E_sys (host, double[n_samples][W],
+   memory-slot order) instead of recomputed ones. */
+hsg_status hsg_pt_exchange_energies(hsg_ctx* ctx, const double* E_sys);
+
+/* n_steps steps of n_hb HB sweeps + n_or OR sweeps + energies + PT, replayed
+   from a CUDA graph captured on the first call. */
+hsg_status hsg_step(hsg_ctx* ctx, int n_steps);
+
+/* FP64 energies (Eq. 1) of every system, memory-slot order, into host
+   double[n_samples][W].  Synchronises. */
+hsg_status hsg_energies(hsg_ctx* ctx, double* E_sys);
+
+/* Observables, caller-owned host buffers (any pointer may be NULL to skip):
+ *   E    double[n_samples][n_replicas][n_temps]   energy by temperature slot
+ *   q    double[n_samples][n_temps][3][3]         q^{mu nu} of replicas 0 and 1 (Eq. 5)
+ *   qk   double[n_samples][n_temps][3][3][3][2]   q^{mu nu}(k) for k = (2 pi/L) e_a,
+ *                                                 a = x, y, z; [re, im]; sign e^{+i k.R}
+ *   perm int32[n_samples][n_replicas][n_temps]
+ * q and qk need n_replicas >= 2 (else they are left untouched).  Synchronises. */
+typedef struct {
+  double* E;
+  double* q;
+  double* qk;
+  int32_t* perm;
+} hsg_obs;
+hsg_status hsg_measure(hsg_ctx* ctx, hsg_obs* out);
+
+/* Spins as FP32 (x, y, z), layout described above.  *_dev take device
+   pointers of the context's device; the others host pointers.  get decodes
+   the stored precision; set encodes with the context's codec. */
+hsg_status hsg_get_spins(hsg_ctx* ctx, float* xyz);
+hsg_status hsg_set_spins(hsg_ctx* ctx, const float* xyz);
+hsg_status hsg_get_spins_dev(hsg_ctx* ctx, float* xyz_dev);
+hsg_status hsg_set_spins_dev(hsg_ctx* ctx, const float* xyz_dev);
+
+/* perm as described above, host int32[n_samples][n_replicas][n_temps]. */
+hsg_status hsg_get_perm(hsg_ctx* ctx, int32_t* perm);
+
+/* Accepted PT exchanges per pair since creation, host
+   uint64[n_samples][n_replicas][n_temps - 1]; and the number of PT calls. */
+hsg_status hsg_get_pt_stats(hsg_ctx* ctx, uint64_t* accepted, uint64_t* n_calls);
+
+typedef struct {
+  int n_samples, n_temps, n_replicas;
+  int W;                   /* systems per sample */
+  int Wp;                  /* systems per sample as stored (multiple of 8) */
+  int precision, j_fp16, variant;
+  long long total_sites;   /* sum over samples of L^3 */
+  long long total_spins;   /* total_sites * W */
+  long long spin_bytes;    /* device bytes of stored spins */
+  long long rec_bytes;     /* device bytes of coupling/field records */
+  uint64_t sweep_count;    /* sweeps done (the HB counter word) */
+  uint64_t pt_count;       /* PT passes done */
+  void* stream;            /* the cudaStream_t the context runs on */
+} hsg_info;
+hsg_status hsg_get_info(hsg_ctx* ctx, hsg_info* info);
+
+/* Wait for all work of the context; returns any pending device error. */
+hsg_status hsg_sync(hsg_ctx* ctx);
+
+/* Text of the last error on ctx (or of the last failed create if ctx is NULL). */
+const char* hsg_last_error(const hsg_ctx* ctx);
+const char* hsg_status_string(hsg_status st);
+
+/* Free every resource of ctx (NULL is accepted). */
+void hsg_destroy(hsg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HSG_H */

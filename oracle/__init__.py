@@ -215,13 +215,14 @@ class OracleSim:
         self.seed = int(seed)
         self.codec = CODECS[codec]
         self.samples: List[OracleSample] = []
-        sys_base = chain_base = 0
-        for smp in samples:
-            o = OracleSample(smp.L, smp.J, smp.H, smp.temps, n_replicas, sys_base, chain_base,
+        # global system ids: sample s owns s * Wp ... s * Wp + W - 1, Wp = W rounded up to 8;
+        # global chain ids: s * n_replicas + r (the library's numbering)
+        W = n_replicas * len(samples[0].temps)
+        Wp = (W + 7) // 8 * 8
+        for k, smp in enumerate(samples):
+            o = OracleSample(smp.L, smp.J, smp.H, smp.temps, n_replicas, k * Wp, k * n_replicas,
                              seed, self.codec)
             self.samples.append(o)
-            sys_base += o.W
-            chain_base += o.R_O
         self.sweep = 0
         self.pt_step = 0
 

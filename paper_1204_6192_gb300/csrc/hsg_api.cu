@@ -1,0 +1,756 @@
+// Host runtime of libhsg: argument checking, device layout and allocation,
+// kernel schedules for sweeps, steps (captured into a CUDA graph), parallel
+// tempering and measurements, and the C ABI declared in include/hsg.h.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hsg.h"
+#include "hsg_internal.h"
+
+using namespace hsg;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct hsg_ctx {
+  hsg_options opt{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int fmt = 0, VEC = 4, PL = 3, ELEM = 4;
+  bool j16 = false;
+  int ns = 0, R_T = 0, R_O = 0, W = 0, Wp = 0, G = 0;
+  int Lmax = 0;
+  long long total_sites = 0;
+  std::vector<int> L;
+  std::vector<SampleDev> sd;
+  uint32_t seed_lo = 0, seed_hi = 0;
+  uint32_t fdG_m = 0, fdG_s = 0;
+
+  // device state
+  unsigned char* spins = nullptr;
+  size_t spin_bytes = 0;
+  void* rec = nullptr;
+  size_t rec_bytes = 0;
+  SampleDev* d_sd = nullptr;
+  int2* d_sweep_blocks = nullptr;
+  int n_sweep_blocks = 0;
+  int2* d_conv_blocks = nullptr;
+  int n_conv_blocks = 0;
+  int4* d_energy_blocks = nullptr;
+  int n_energy_blocks = 0;
+  double* d_epart = nullptr;
+  float* d_beta = nullptr;
+  double* d_temps = nullptr;
+  double* d_inv_temps = nullptr;
+  int* d_perm = nullptr;
+  double* d_E = nullptr;
+  unsigned long long* d_acc = nullptr;
+  unsigned long long* d_counters = nullptr;
+  double* d_mpart = nullptr;
+  double* d_q = nullptr;
+  double* d_qk = nullptr;
+  float* d_xyz = nullptr;
+  long long* d_xyz_off = nullptr;
+  long long xyz_floats = 0;
+  std::vector<long long> xyz_off;
+
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+
+  hsg_status err = HSG_OK;
+  std::string msg;
+  std::vector<void*> allocations;
+};
+
+namespace {
+
+hsg_status fail(hsg_ctx* c, hsg_status st, const std::string& m) {
+  if (c) {
+    if (c->err == HSG_OK) {
+      c->err = st;
+      c->msg = m;
+    }
+  } else {
+    g_create_error = m;
+  }
+  return st;
+}
+
+// argument errors are not sticky
+hsg_status bad_arg(hsg_ctx* c, const std::string& m) {
+  if (c) c->msg = m;
+  else g_create_error = m;
+  return HSG_EINVAL;
+}
+
+#define HSG_CUDA(ctx, call)                                                             \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail((ctx), e_ == cudaErrorMemoryAllocation ? HSG_ENOMEM : HSG_ECUDA,      \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+  } while (0)
+
+#define HSG_CHECK_CTX(ctx)                      \
+  do {                                          \
+    if (!(ctx)) return HSG_EINVAL;              \
+    if ((ctx)->err != HSG_OK) return (ctx)->err; \
+  } while (0)
+
+void fastdiv(uint32_t d, uint32_t* m, uint32_t* s) {
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;
+  *m = (uint32_t)((((1ull << l) - d) << 32) / d + 1ull);
+  *s = l;
+}
+
+template <typename T>
+hsg_status dev_alloc(hsg_ctx* c, T** p, size_t bytes) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes > 0 ? bytes : 16);
+  if (e != cudaSuccess) {
+    return fail(c, HSG_ENOMEM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " +
+                                   cudaGetErrorString(e));
+  }
+  c->allocations.push_back(q);
+  *p = reinterpret_cast<T*>(q);
+  return HSG_OK;
+}
+
+#define HSG_TRY(expr)                  \
+  do {                                 \
+    hsg_status s_ = (expr);            \
+    if (s_ != HSG_OK) return s_;       \
+  } while (0)
+
+int fmt_vec(int f) { return (f == FMT_F16 || f == FMT_BF16) ? 8 : 4; }
+int fmt_planes(int f) { return (f == FMT_ANG16 || f == FMT_OCT16) ? 1 : 3; }
+int fmt_elem(int f) { return (f == FMT_F16 || f == FMT_BF16) ? 2 : 4; }
+
+SweepParams sweep_params(hsg_ctx* c, int parity, int sweep_offset) {
+  SweepParams p;
+  p.spins = c->spins;
+  p.rec = c->rec;
+  p.samples = c->d_sd;
+  p.blocks = c->d_sweep_blocks;
+  p.beta = c->d_beta;
+  p.counters = c->d_counters;
+  p.G = c->G;
+  p.Wp = c->Wp;
+  p.fdG_m = c->fdG_m;
+  p.fdG_s = c->fdG_s;
+  p.seed_lo = c->seed_lo;
+  p.seed_hi = c->seed_hi;
+  p.parity = parity;
+  p.sweep_offset = sweep_offset;
+  return p;
+}
+
+EnergyParams energy_params(hsg_ctx* c) {
+  EnergyParams p;
+  p.spins = c->spins;
+  p.rec = c->rec;
+  p.samples = c->d_sd;
+  p.blocks = c->d_energy_blocks;
+  p.partials = c->d_epart;
+  p.E = c->d_E;
+  p.G = c->G;
+  p.Wp = c->Wp;
+  p.n_samples = c->ns;
+  return p;
+}
+
+PTParams pt_params(hsg_ctx* c, int sweeps_per_call, int bump_pt) {
+  PTParams p;
+  p.E = c->d_E;
+  p.inv_temps = c->d_inv_temps;
+  p.perm = c->d_perm;
+  p.beta = c->d_beta;
+  p.accepted = c->d_acc;
+  p.counters = c->d_counters;
+  p.n_samples = c->ns;
+  p.R_O = c->R_O;
+  p.R_T = c->R_T;
+  p.Wp = c->Wp;
+  p.seed_lo = c->seed_lo;
+  p.seed_hi = c->seed_hi;
+  p.sweeps_per_call = sweeps_per_call;
+  p.bump_pt = bump_pt;
+  return p;
+}
+
+ConvParams conv_params(hsg_ctx* c, float* xyz, const long long* xyz_off) {
+  ConvParams p;
+  p.spins = c->spins;
+  p.samples = c->d_sd;
+  p.blocks = c->d_conv_blocks;
+  p.xyz = xyz;
+  p.xyz_off = xyz_off;
+  p.G = c->G;
+  p.Wp = c->Wp;
+  p.W = c->W;
+  p.fdG_m = c->fdG_m;
+  p.fdG_s = c->fdG_s;
+  p.seed_lo = c->seed_lo;
+  p.seed_hi = c->seed_hi;
+  return p;
+}
+
+hsg_status half_sweeps(hsg_ctx* c, bool hb, int sweep_offset) {
+  for (int parity = 0; parity < 2; ++parity) {
+    SweepParams p = sweep_params(c, parity, sweep_offset);
+    HSG_CUDA(c, launch_half_sweep(c->fmt, hb, c->j16, c->opt.fast_math != 0, p,
+                                  c->n_sweep_blocks, c->stream));
+  }
+  return HSG_OK;
+}
+
+hsg_status enqueue_energy(hsg_ctx* c) {
+  EnergyParams p = energy_params(c);
+  HSG_CUDA(c, launch_energy(c->fmt, c->j16, p, c->n_energy_blocks, c->stream));
+  return HSG_OK;
+}
+
+hsg_status enqueue_step(hsg_ctx* c) {
+  const int nhb = c->opt.n_hb_per_step, nor = c->opt.n_or_per_step;
+  for (int k = 0; k < nhb; ++k) HSG_TRY(half_sweeps(c, true, k));
+  for (int k = 0; k < nor; ++k) HSG_TRY(half_sweeps(c, false, nhb + k));
+  HSG_TRY(enqueue_energy(c));
+  HSG_CUDA(c, launch_pt(pt_params(c, nhb + nor, 1), c->stream));
+  return HSG_OK;
+}
+
+hsg_status ensure_xyz(hsg_ctx* c) {
+  if (c->d_xyz) return HSG_OK;
+  HSG_TRY(dev_alloc(c, &c->d_xyz, (size_t)c->xyz_floats * sizeof(float)));
+  HSG_TRY(dev_alloc(c, &c->d_xyz_off, c->xyz_off.size() * sizeof(long long)));
+  HSG_CUDA(c, cudaMemcpy(c->d_xyz_off, c->xyz_off.data(), c->xyz_off.size() * sizeof(long long),
+                         cudaMemcpyHostToDevice));
+  return HSG_OK;
+}
+
+bool finite_all(const float* a, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double* temps,
+                       int n_temps, int n_replicas, const float* const* J,
+                       const float* const* H, uint64_t seed, const hsg_options* optp) {
+  if (!out) return bad_arg(nullptr, "out is NULL");
+  *out = nullptr;
+  hsg_options opt;
+  hsg_default_options(&opt);
+  if (optp) opt = *optp;
+  if (n_samples < 1) return bad_arg(nullptr, "n_samples < 1");
+  if (!L || !temps || !J) return bad_arg(nullptr, "L, temps and J must not be NULL");
+  if (n_temps < 1 || n_temps > 256) return bad_arg(nullptr, "n_temps must be in [1, 256]");
+  if (n_replicas < 1) return bad_arg(nullptr, "n_replicas < 1");
+  if (opt.precision < HSG_FP32 || opt.precision > HSG_OCT16)
+    return bad_arg(nullptr, "unknown precision");
+  if (opt.n_hb_per_step < 0 || opt.n_or_per_step < 0)
+    return bad_arg(nullptr, "negative sweeps per step");
+  const int W = n_temps * n_replicas;
+  if (W > 1024) return bad_arg(nullptr, "n_temps * n_replicas must be <= 1024");
+  const int Wp = (W + 7) / 8 * 8;
+  const int fmt = opt.precision;
+  const int VEC = fmt_vec(fmt), G = Wp / VEC;
+  for (int s = 0; s < n_samples; ++s) {
+    if (L[s] < 4 || (L[s] & 1) || L[s] > 512)
+      return bad_arg(nullptr, "L must be even and in [4, 512]");
+    const long long N = (long long)L[s] * L[s] * L[s];
+    if (N * G >= (1ll << 31)) return bad_arg(nullptr, "lattice too large for the system count");
+    if (!J[s]) return bad_arg(nullptr, "J[s] is NULL");
+    if (!finite_all(J[s], (size_t)N * 3)) return bad_arg(nullptr, "J has a non-finite value");
+    if (H && H[s] && !finite_all(H[s], (size_t)N * 3))
+      return bad_arg(nullptr, "H has a non-finite value");
+    for (int t = 0; t < n_temps; ++t) {
+      const double T = temps[(size_t)s * n_temps + t];
+      if (!std::isfinite(T) || T <= 0.0) return bad_arg(nullptr, "temperatures must be positive");
+      if (t > 0 && !(T > temps[(size_t)s * n_temps + t - 1]))
+        return bad_arg(nullptr, "temperatures must be strictly increasing");
+    }
+  }
+
+  hsg_ctx* c = new hsg_ctx();
+  c->opt = opt;
+  c->device = opt.device;
+  c->fmt = fmt;
+  c->VEC = VEC;
+  c->PL = fmt_planes(fmt);
+  c->ELEM = fmt_elem(fmt);
+  c->j16 = opt.j_fp16 != 0;
+  c->ns = n_samples;
+  c->R_T = n_temps;
+  c->R_O = n_replicas;
+  c->W = W;
+  c->Wp = Wp;
+  c->G = G;
+  c->seed_lo = (uint32_t)(seed & 0xffffffffu);
+  c->seed_hi = (uint32_t)(seed >> 32);
+  fastdiv((uint32_t)G, &c->fdG_m, &c->fdG_s);
+  c->L.assign(L, L + n_samples);
+
+  auto cleanup_fail = [&](hsg_status st) {
+    g_create_error = c->msg;
+    hsg_destroy(c);
+    return st;
+  };
+
+  cudaError_t e = cudaSetDevice(opt.device);
+  if (e != cudaSuccess) {
+    c->msg = std::string("cudaSetDevice: ") + cudaGetErrorString(e);
+    return cleanup_fail(HSG_ECUDA);
+  }
+  if (opt.stream) {
+    c->stream = (cudaStream_t)opt.stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      c->msg = std::string("cudaStreamCreate: ") + cudaGetErrorString(e);
+      return cleanup_fail(HSG_ECUDA);
+    }
+    c->own_stream = true;
+  }
+
+  // layout
+  std::vector<int2> sweep_blocks, conv_blocks;
+  std::vector<int4> energy_blocks;
+  size_t spin_off = 0, rec_off = 0;
+  long long xyz = 0;
+  for (int s = 0; s < n_samples; ++s) {
+    SampleDev d{};
+    d.L = L[s];
+    d.N = L[s] * L[s] * L[s];
+    d.Lh = L[s] / 2;
+    fastdiv((uint32_t)d.Lh, &d.fdLh_m, &d.fdLh_s);
+    fastdiv((uint32_t)d.L, &d.fdL_m, &d.fdL_s);
+    d.spin_off = (long long)spin_off;
+    d.plane_stride = (long long)d.N * Wp * c->ELEM;
+    d.rec_off = (long long)rec_off;
+    d.sys_base = s * Wp;
+    const long long half_items = (long long)(d.N / 2) * G;
+    for (long long it = 0; it < half_items; it += SWEEP_BS)
+      sweep_blocks.push_back(make_int2(s, (int)it));
+    const long long all_items = (long long)d.N * G;
+    for (long long it = 0; it < all_items; it += 256) conv_blocks.push_back(make_int2(s, (int)it));
+    const int per_block = RED_BS * RED_SITES;
+    d.e_nsb = (d.N / 2 + per_block - 1) / per_block;
+    d.e_block0 = (int)energy_blocks.size();
+    for (int sb = 0; sb < d.e_nsb; ++sb)
+      for (int g = 0; g < G; ++g) energy_blocks.push_back(make_int4(s, g, sb, 0));
+    size_t sb = (size_t)c->PL * d.plane_stride;
+    spin_off += (sb + 255) / 256 * 256;
+    rec_off += (size_t)d.N;
+    c->sd.push_back(d);
+    c->xyz_off.push_back(xyz);
+    xyz += (long long)W * d.N * 3;
+    c->total_sites += d.N;
+    c->Lmax = std::max(c->Lmax, d.L);
+  }
+  c->xyz_floats = xyz;
+  c->spin_bytes = spin_off;
+  c->rec_bytes = rec_off * (c->j16 ? 24 : 48);
+  c->n_sweep_blocks = (int)sweep_blocks.size();
+  c->n_conv_blocks = (int)conv_blocks.size();
+  c->n_energy_blocks = (int)energy_blocks.size();
+
+  // records: six bonds and the field of every storage site
+  std::vector<float> recf;
+  std::vector<__half> rech;
+  if (c->j16) rech.resize(rec_off * 12);
+  else recf.resize(rec_off * 12);
+  for (int s = 0; s < n_samples; ++s) {
+    const SampleDev& d = c->sd[s];
+    const int Ls = d.L, Lh = d.Lh;
+    const long long half_n = d.N / 2;
+    const float* Js = J[s];
+    const float* Hs = (H && H[s]) ? H[s] : nullptr;
+    for (long long ss = 0; ss < d.N; ++ss) {
+      const int par = ss >= half_n ? 1 : 0;
+      const long long h = ss - par * half_n;
+      const long long r = h / Lh;
+      const int hx = (int)(h % Lh);
+      const int y = (int)(r % Ls), z = (int)(r / Ls);
+      const int x = 2 * hx + ((par + y + z) & 1);
+      auto idx = [&](int xx, int yy, int zz) {
+        return (long long)((xx + Ls) % Ls) + (long long)Ls * (((yy + Ls) % Ls) + (long long)Ls * ((zz + Ls) % Ls));
+      };
+      const long long i = idx(x, y, z);
+      float v[12];
+      v[0] = Js[i * 3 + 0];
+      v[1] = Js[idx(x - 1, y, z) * 3 + 0];
+      v[2] = Js[i * 3 + 1];
+      v[3] = Js[idx(x, y - 1, z) * 3 + 1];
+      v[4] = Js[i * 3 + 2];
+      v[5] = Js[idx(x, y, z - 1) * 3 + 2];
+      v[6] = Hs ? Hs[i * 3 + 0] : 0.0f;
+      v[7] = Hs ? Hs[i * 3 + 1] : 0.0f;
+      v[8] = Hs ? Hs[i * 3 + 2] : 0.0f;
+      v[9] = v[10] = v[11] = 0.0f;
+      const size_t o = (size_t)(d.rec_off + ss) * 12;
+      for (int k = 0; k < 12; ++k) {
+        if (c->j16) rech[o + k] = __float2half_rn(v[k]);
+        else recf[o + k] = v[k];
+      }
+    }
+  }
+
+  // device allocations
+  hsg_status st;
+#define HSG_ALLOC(ptr, bytes)                   \
+  st = dev_alloc(c, &(ptr), (bytes));           \
+  if (st != HSG_OK) return cleanup_fail(st);
+  HSG_ALLOC(c->spins, c->spin_bytes);
+  HSG_ALLOC(c->rec, c->rec_bytes);
+  HSG_ALLOC(c->d_sd, sizeof(SampleDev) * n_samples);
+  HSG_ALLOC(c->d_sweep_blocks, sizeof(int2) * sweep_blocks.size());
+  HSG_ALLOC(c->d_conv_blocks, sizeof(int2) * conv_blocks.size());
+  HSG_ALLOC(c->d_energy_blocks, sizeof(int4) * energy_blocks.size());
+  HSG_ALLOC(c->d_epart, sizeof(double) * 8 * energy_blocks.size());
+  HSG_ALLOC(c->d_beta, sizeof(float) * n_samples * Wp);
+  HSG_ALLOC(c->d_temps, sizeof(double) * n_samples * n_temps);
+  HSG_ALLOC(c->d_inv_temps, sizeof(double) * n_samples * n_temps);
+  HSG_ALLOC(c->d_perm, sizeof(int) * n_samples * n_replicas * n_temps);
+  HSG_ALLOC(c->d_E, sizeof(double) * n_samples * Wp);
+  HSG_ALLOC(c->d_acc, sizeof(unsigned long long) * n_samples * n_replicas * std::max(1, n_temps - 1));
+  HSG_ALLOC(c->d_counters, sizeof(unsigned long long) * 2);
+#undef HSG_ALLOC
+
+  std::vector<double> inv(n_samples * (size_t)n_temps);
+  std::vector<float> beta(n_samples * (size_t)Wp, 1.0f);
+  std::vector<int> perm(n_samples * (size_t)n_replicas * n_temps);
+  for (int s = 0; s < n_samples; ++s) {
+    for (int t = 0; t < n_temps; ++t) inv[(size_t)s * n_temps + t] = 1.0 / temps[(size_t)s * n_temps + t];
+    for (int r = 0; r < n_replicas; ++r)
+      for (int t = 0; t < n_temps; ++t) {
+        perm[((size_t)s * n_replicas + r) * n_temps + t] = t;
+        beta[(size_t)s * Wp + r * n_temps + t] = (float)inv[(size_t)s * n_temps + t];
+      }
+  }
+  const unsigned long long zero2[2] = {0ull, 0ull};
+#define HSG_UP(dst, src, bytes)                                                     \
+  e = cudaMemcpy((dst), (src), (bytes), cudaMemcpyHostToDevice);                   \
+  if (e != cudaSuccess) {                                                          \
+    c->msg = std::string("cudaMemcpy: ") + cudaGetErrorString(e);                  \
+    return cleanup_fail(HSG_ECUDA);                                                \
+  }
+  HSG_UP(c->rec, c->j16 ? (const void*)rech.data() : (const void*)recf.data(), c->rec_bytes);
+  HSG_UP(c->d_sd, c->sd.data(), sizeof(SampleDev) * n_samples);
+  HSG_UP(c->d_sweep_blocks, sweep_blocks.data(), sizeof(int2) * sweep_blocks.size());
+  HSG_UP(c->d_conv_blocks, conv_blocks.data(), sizeof(int2) * conv_blocks.size());
+  HSG_UP(c->d_energy_blocks, energy_blocks.data(), sizeof(int4) * energy_blocks.size());
+  HSG_UP(c->d_temps, temps, sizeof(double) * n_samples * n_temps);
+  HSG_UP(c->d_inv_temps, inv.data(), sizeof(double) * inv.size());
+  HSG_UP(c->d_perm, perm.data(), sizeof(int) * perm.size());
+  HSG_UP(c->d_beta, beta.data(), sizeof(float) * beta.size());
+  HSG_UP(c->d_counters, zero2, sizeof(zero2));
+#undef HSG_UP
+  e = cudaMemset(c->d_acc, 0, sizeof(unsigned long long) * n_samples * n_replicas * std::max(1, n_temps - 1));
+  if (e == cudaSuccess) e = cudaMemset(c->d_E, 0, sizeof(double) * n_samples * Wp);
+  if (e == cudaSuccess) e = cudaMemset(c->spins, 0, c->spin_bytes);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    c->msg = std::string("device init: ") + cudaGetErrorString(e);
+    return cleanup_fail(HSG_ECUDA);
+  }
+  ConvParams cp = conv_params(c, nullptr, nullptr);
+  e = launch_init(c->fmt, cp, c->n_conv_blocks, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    c->msg = std::string("init kernel: ") + cudaGetErrorString(e);
+    return cleanup_fail(HSG_ECUDA);
+  }
+  *out = c;
+  return HSG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hsg_default_options(hsg_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->precision = HSG_FP32;
+  opt->n_hb_per_step = 1;
+  opt->n_or_per_step = 5;
+}
+
+hsg_status hsg_create(hsg_ctx** out, int L, const double* temps, int n_temps, int n_replicas,
+                      const float* J, const float* H, uint64_t seed, const hsg_options* opt) {
+  const float* Jp[1] = {J};
+  const float* Hp[1] = {H};
+  return create_impl(out, 1, &L, temps, n_temps, n_replicas, Jp, Hp, seed, opt);
+}
+
+hsg_status hsg_create_batch(hsg_ctx** out, int n_samples, const int* L, const double* temps,
+                            int n_temps, int n_replicas, const float* const* J,
+                            const float* const* H, uint64_t seed, const hsg_options* opt) {
+  return create_impl(out, n_samples, L, temps, n_temps, n_replicas, J, H, seed, opt);
+}
+
+hsg_status hsg_sweep_or(hsg_ctx* c, int n) {
+  HSG_CHECK_CTX(c);
+  if (n < 0) return bad_arg(c, "n_sweeps < 0");
+  if (n == 0) return HSG_OK;
+  HSG_CUDA(c, cudaSetDevice(c->device));
+  for (int k = 0; k < n; ++k) HSG_TRY(half_sweeps(c, false, k));
+  HSG_CUDA(c, launch_bump(c->d_counters, n, 0, c->stream));
+  return HSG_OK;
+}
+
+hsg_status hsg_sweep_hb(hsg_ctx* c, int n) {
+  HSG_CHECK_CTX(c);
+  if (n < 0) return bad_arg(c, "n_sweeps < 0");
+  if (n == 0) return HSG_OK;
+  HSG_CUDA(c, cudaSetDevice(c->device));
+  for (int k = 0; k < n; ++k) HSG_TRY(half_sweeps(c, true, k));
+  HSG_CUDA(c, launch_bump(c->d_counters, n, 0, c->stream));
+  return HSG_OK;
+}
+
+hsg_status hsg_pt_exchange(hsg_ctx* c) {
+  HSG_CHECK_CTX(c);
+  HSG_CUDA(c, cudaSetDevice(c->device));
+  HSG_TRY(enqueue_energy(c));
+  HSG_CUDA(c, launch_pt(pt_params(c, 0, 1), c->stream));
+  return HSG_OK;
+}
+
+hsg_status hsg_pt_exchange_energies(hsg_ctx* c, const double* E_sys) {
+  HSG_CHECK_CTX(c);
+  if (!E_sys) return bad_arg(c, "E_sys is NULL");
+  HSG_CUDA(c, cudaSetDevice(c->device));
+  HSG_CUDA(c, cudaMemcpy2DAsync(c->d_E, sizeof(double) * c->Wp, E_sys, sizeof(double) * c->W,
+                                sizeof(double) * c->W, c->ns, cudaMemcpyHostToDevice, c->stream));
+  HSG_CUDA(c, launch_pt(pt_params(c, 0, 1), c->stream));
+  // the host array may be released by the caller on return
+  HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return HSG_OK;
+}
+
+hsg_status hsg_step(hsg_ctx* c, int n_steps) {
+  HSG_CHECK_CTX(c);
+  if (n_steps < 0) return bad_arg(c, "n_steps < 0");
+  if (n_steps == 0) return HSG_OK;
+  HSG_CUDA(c, cudaSetDevice(c->device));
+  if (!c->graph_exec) {
+    HSG_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    hsg_status st = enqueue_step(c);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (st != HSG_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    HSG_CUDA(c, e);
+    c->graph = g;
+    HSG_CUDA(c, cudaGraphInstantiate(&c->graph_exec, c->graph, 0));
+  }
+  for (int k = 0; k < n_steps; ++k) HSG_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream));
+  return HSG_OK;
+}
+
+hsg_status hsg_energies(hsg_ctx* c, double* E_sys) {
+  HSG_CHECK_CTX(c);
+  if (!E_sys) return bad_arg(c, "E_sys is NULL");
+  HSG_CUDA(c, cudaSetDevice(c->device));
+  HSG_TRY(enqueue_energy(c));
+  HSG_CUDA(c, cudaMemcpy2DAsync(E_sys, sizeof(double) * c->W, c->d_E, sizeof(double) * c->Wp,
+                                sizeof(double) * c->W, c->ns, cudaMemcpyDeviceToHost, c->stream));
+  HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return HSG_OK;
+}
+
+hsg_status hsg_measure(hsg_ctx* c, hsg_obs* o) {
+  HSG_CHECK_CTX(c);
+  if (!o) return bad_arg(c, "obs is NULL");
+  HSG_CUDA(c, cudaSetDevice(c->device));
+  HSG_TRY(enqueue_energy(c));
+  const bool pairs = c->R_O >= 2 && (o->q || o->qk);
+  if (pairs) {
+    if (!c->d_mpart) {
+      HSG_TRY(dev_alloc(c, &c->d_mpart, sizeof(double) * c->ns * (size_t)c->Lmax * c->R_T * 45));
+      HSG_TRY(dev_alloc(c, &c->d_q, sizeof(double) * c->ns * (size_t)c->R_T * 9));
+      HSG_TRY(dev_alloc(c, &c->d_qk, sizeof(double) * c->ns * (size_t)c->R_T * 54));
+    }
+    MeasureParams p;
+    p.spins = c->spins;
+    p.samples = c->d_sd;
+    p.perm = c->d_perm;
+    p.partials = c->d_mpart;
+    p.q = c->d_q;
+    p.qk = c->d_qk;
+    p.n_samples = c->ns;
+    p.R_O = c->R_O;
+    p.R_T = c->R_T;
+    p.Wp = c->Wp;
+    p.Lmax = c->Lmax;
+    HSG_CUDA(c, launch_measure(c->fmt, p, c->Lmax, c->stream));
+  }
+  std::vector<double> E((size_t)c->ns * c->Wp);
+  std::vector<int> perm((size_t)c->ns * c->R_O * c->R_T);
+  HSG_CUDA(c, cudaMemcpyAsync(E.data(), c->d_E, sizeof(double) * E.size(), cudaMemcpyDeviceToHost,
+                              c->stream));
+  HSG_CUDA(c, cudaMemcpyAsync(perm.data(), c->d_perm, sizeof(int) * perm.size(),
+                              cudaMemcpyDeviceToHost, c->stream));
+  if (pairs && o->q)
+    HSG_CUDA(c, cudaMemcpyAsync(o->q, c->d_q, sizeof(double) * c->ns * c->R_T * 9,
+                                cudaMemcpyDeviceToHost, c->stream));
+  if (pairs && o->qk)
+    HSG_CUDA(c, cudaMemcpyAsync(o->qk, c->d_qk, sizeof(double) * c->ns * c->R_T * 54,
+                                cudaMemcpyDeviceToHost, c->stream));
+  HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (int s = 0; s < c->ns; ++s)
+    for (int r = 0; r < c->R_O; ++r)
+      for (int t = 0; t < c->R_T; ++t) {
+        const size_t pi = ((size_t)s * c->R_O + r) * c->R_T + t;
+        if (o->E) o->E[pi] = E[(size_t)s * c->Wp + r * c->R_T + perm[pi]];
+        if (o->perm) o->perm[pi] = perm[pi];
+      }
+  return HSG_OK;
+}
+
+hsg_status hsg_get_spins_dev(hsg_ctx* c, float* xyz_dev) {
+  HSG_CHECK_CTX(c);
+  if (!xyz_dev) return bad_arg(c, "xyz is NULL");
+  HSG_CUDA(c, cudaSetDevice(c->device));
+  HSG_TRY(ensure_xyz(c));
+  HSG_CUDA(c, launch_get(c->fmt, conv_params(c, xyz_dev, c->d_xyz_off), c->n_conv_blocks, c->stream));
+  return HSG_OK;
+}
+
+hsg_status hsg_set_spins_dev(hsg_ctx* c, const float* xyz_dev) {
+  HSG_CHECK_CTX(c);
+  if (!xyz_dev) return bad_arg(c, "xyz is NULL");
+  HSG_CUDA(c, cudaSetDevice(c->device));
+  HSG_TRY(ensure_xyz(c));
+  HSG_CUDA(c, launch_set(c->fmt, conv_params(c, const_cast<float*>(xyz_dev), c->d_xyz_off),
+                         c->n_conv_blocks, c->stream));
+  return HSG_OK;
+}
+
+hsg_status hsg_get_spins(hsg_ctx* c, float* xyz) {
+  HSG_CHECK_CTX(c);
+  if (!xyz) return bad_arg(c, "xyz is NULL");
+  HSG_CUDA(c, cudaSetDevice(c->device));
+  HSG_TRY(ensure_xyz(c));
+  HSG_CUDA(c, launch_get(c->fmt, conv_params(c, c->d_xyz, c->d_xyz_off), c->n_conv_blocks, c->stream));
+  HSG_CUDA(c, cudaMemcpyAsync(xyz, c->d_xyz, sizeof(float) * c->xyz_floats, cudaMemcpyDeviceToHost,
+                              c->stream));
+  HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return HSG_OK;
+}
+
+hsg_status hsg_set_spins(hsg_ctx* c, const float* xyz) {
+  HSG_CHECK_CTX(c);
+  if (!xyz) return bad_arg(c, "xyz is NULL");
+  HSG_CUDA(c, cudaSetDevice(c->device));
+  HSG_TRY(ensure_xyz(c));
+  HSG_CUDA(c, cudaMemcpyAsync(c->d_xyz, xyz, sizeof(float) * c->xyz_floats, cudaMemcpyHostToDevice,
+                              c->stream));
+  HSG_CUDA(c, launch_set(c->fmt, conv_params(c, c->d_xyz, c->d_xyz_off), c->n_conv_blocks, c->stream));
+  // the host buffer has been read once the copy is done
+  HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return HSG_OK;
+}
+
+hsg_status hsg_get_perm(hsg_ctx* c, int32_t* perm) {
+  HSG_CHECK_CTX(c);
+  if (!perm) return bad_arg(c, "perm is NULL");
+  HSG_CUDA(c, cudaSetDevice(c->device));
+  HSG_CUDA(c, cudaMemcpyAsync(perm, c->d_perm, sizeof(int) * c->ns * c->R_O * c->R_T,
+                              cudaMemcpyDeviceToHost, c->stream));
+  HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return HSG_OK;
+}
+
+hsg_status hsg_get_pt_stats(hsg_ctx* c, uint64_t* accepted, uint64_t* n_calls) {
+  HSG_CHECK_CTX(c);
+  HSG_CUDA(c, cudaSetDevice(c->device));
+  unsigned long long cnt[2];
+  if (accepted && c->R_T > 1)
+    HSG_CUDA(c, cudaMemcpyAsync(accepted, c->d_acc,
+                                sizeof(unsigned long long) * c->ns * c->R_O * (c->R_T - 1),
+                                cudaMemcpyDeviceToHost, c->stream));
+  HSG_CUDA(c, cudaMemcpyAsync(cnt, c->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+  HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (n_calls) *n_calls = cnt[1];
+  return HSG_OK;
+}
+
+hsg_status hsg_get_info(hsg_ctx* c, hsg_info* info) {
+  HSG_CHECK_CTX(c);
+  if (!info) return bad_arg(c, "info is NULL");
+  HSG_CUDA(c, cudaSetDevice(c->device));
+  unsigned long long cnt[2];
+  HSG_CUDA(c, cudaMemcpyAsync(cnt, c->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+  HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  info->n_samples = c->ns;
+  info->n_temps = c->R_T;
+  info->n_replicas = c->R_O;
+  info->W = c->W;
+  info->Wp = c->Wp;
+  info->precision = c->fmt;
+  info->j_fp16 = c->j16 ? 1 : 0;
+  info->variant = HSG_VARIANT_TWO_PASS;
+  info->total_sites = c->total_sites;
+  info->total_spins = c->total_sites * c->W;
+  info->spin_bytes = (long long)c->spin_bytes;
+  info->rec_bytes = (long long)c->rec_bytes;
+  info->sweep_count = cnt[0];
+  info->pt_count = cnt[1];
+  info->stream = (void*)c->stream;
+  return HSG_OK;
+}
+
+hsg_status hsg_sync(hsg_ctx* c) {
+  HSG_CHECK_CTX(c);
+  HSG_CUDA(c, cudaSetDevice(c->device));
+  HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  HSG_CUDA(c, cudaGetLastError());
+  return HSG_OK;
+}
+
+const char* hsg_last_error(const hsg_ctx* c) {
+  if (!c) return g_create_error.c_str();
+  return c->msg.c_str();
+}
+
+const char* hsg_status_string(hsg_status st) {
+  switch (st) {
+    case HSG_OK: return "ok";
+    case HSG_EINVAL: return "invalid argument";
+    case HSG_ENOMEM: return "out of memory";
+    case HSG_ECUDA: return "CUDA error";
+    case HSG_ETIMEOUT: return "device wait timed out";
+    case HSG_ESTATE: return "invalid state";
+  }
+  return "unknown status";
+}
+
+void hsg_destroy(hsg_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  for (void* p : c->allocations) cudaFree(p);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,536 @@
+// Reductions and bookkeeping kernels: FP64 energies (Eq. 1), the parallel
+// tempering pass (Eq. 4), the overlap measurements (Eq. 5 and its
+// k-dependent form), the random initial state and the conversions between
+// the stored spin formats and FP32 (x, y, z).
+//
+// Every reduction is deterministic: per-thread partial sums, a fixed-order
+// shuffle/shared-memory tree inside a block, and a second kernel that adds the
+// block partials in a fixed order.  Two runs give bit-identical results.
+#include "hsg_device.cuh"
+#include "hsg_internal.h"
+
+namespace hsg {
+
+// ---------------------------------------------------------------------------
+// Energies.  Every bond joins an odd and an even site, so
+//   E = - sum_{odd i} s_i . h_i  - sum_{even j} H_j . s_j
+// with h_i the full local field (bonds + field) of the odd site i.
+// ---------------------------------------------------------------------------
+template <bool J16>
+__device__ __forceinline__ void load_rec(const void* rec, long long idx, float* j6, float* h3) {
+  if (J16) {
+    const uint2* r = reinterpret_cast<const uint2*>(rec) + idx * 3;
+    const uint2 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2);
+    float2 t;
+    t = h2f(a.x); j6[0] = t.x; j6[1] = t.y;
+    t = h2f(a.y); j6[2] = t.x; j6[3] = t.y;
+    t = h2f(b.x); j6[4] = t.x; j6[5] = t.y;
+    t = h2f(b.y); h3[0] = t.x; h3[1] = t.y;
+    t = h2f(c.x); h3[2] = t.x;
+  } else {
+    const float4* r = reinterpret_cast<const float4*>(rec) + idx * 3;
+    const float4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2);
+    j6[0] = a.x; j6[1] = a.y; j6[2] = a.z; j6[3] = a.w;
+    j6[4] = b.x; j6[5] = b.y; h3[0] = b.z; h3[1] = b.w;
+    h3[2] = c.x;
+  }
+}
+
+template <int F>
+__device__ __forceinline__ void load_site(const unsigned char* p, long long ps,
+                                          Spins<FmtInfo<F>::VEC>& s) {
+  uint4 c[FmtInfo<F>::PLANES];
+#pragma unroll
+  for (int pl = 0; pl < FmtInfo<F>::PLANES; ++pl)
+    c[pl] = __ldg(reinterpret_cast<const uint4*>(p + pl * ps));
+  decode<F>(c, s);
+}
+
+template <int F, bool J16>
+__global__ void __launch_bounds__(RED_BS) k_energy(const EnergyParams p) {
+  constexpr int VEC = FmtInfo<F>::VEC, ELEM = FmtInfo<F>::ELEM;
+  const int4 blk = p.blocks[blockIdx.x];
+  const SampleDev& sd = p.samples[blk.x];
+  const int g = blk.y;
+  const uint32_t half_n = (uint32_t)sd.N >> 1;
+  const uint32_t L = sd.L, Lh = sd.Lh;
+  const long long site_stride = (long long)p.Wp * ELEM;
+  const unsigned char* base = p.spins + sd.spin_off + (long long)g * 16;
+  const long long ps = sd.plane_stride;
+
+  float acc[VEC];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) acc[v] = 0.0f;
+
+  for (int k = 0; k < RED_SITES; ++k) {
+    const uint32_t h = ((uint32_t)blk.z * RED_SITES + k) * RED_BS + threadIdx.x;
+    if (h >= half_n) break;
+    // odd site with half-index h and its even neighbours
+    const uint32_t r = (__umulhi(h, sd.fdLh_m) + h) >> sd.fdLh_s;
+    const uint32_t hx = h - r * Lh;
+    const uint32_t z = (__umulhi(r, sd.fdL_m) + r) >> sd.fdL_s;
+    const uint32_t y = r - z * L;
+    const uint32_t x = 2u * hx + ((1u + y + z) & 1u);
+    const uint32_t xp = (x + 1 == L) ? 0u : x + 1, xm = (x == 0) ? L - 1 : x - 1;
+    const uint32_t yp = (y + 1 == L) ? 0u : y + 1, ym = (y == 0) ? L - 1 : y - 1;
+    const uint32_t zp = (z + 1 == L) ? 0u : z + 1, zm = (z == 0) ? L - 1 : z - 1;
+    const uint32_t xh = x >> 1;
+    uint32_t nb[6];
+    nb[0] = (xp >> 1) + r * Lh;
+    nb[1] = (xm >> 1) + r * Lh;
+    nb[2] = xh + (yp + L * z) * Lh;
+    nb[3] = xh + (ym + L * z) * Lh;
+    nb[4] = xh + (y + L * zp) * Lh;
+    nb[5] = xh + (y + L * zm) * Lh;
+    const uint32_t own = half_n + h;
+    float j6[6], h3[3];
+    load_rec<J16>(p.rec, sd.rec_off + own, j6, h3);
+    Spins<VEC> hf, t;
+    load_site<F>(base + nb[0] * site_stride, ps, t);
+#pragma unroll
+    for (int q = 0; q < VEC / 2; ++q) {
+      hf.x[q] = mul2(f2(j6[0]), t.x[q]);
+      hf.y[q] = mul2(f2(j6[0]), t.y[q]);
+      hf.z[q] = mul2(f2(j6[0]), t.z[q]);
+    }
+#pragma unroll
+    for (int n = 1; n < 6; ++n) {
+      load_site<F>(base + nb[n] * site_stride, ps, t);
+#pragma unroll
+      for (int q = 0; q < VEC / 2; ++q) {
+        hf.x[q] = add2(hf.x[q], mul2(f2(j6[n]), t.x[q]));
+        hf.y[q] = add2(hf.y[q], mul2(f2(j6[n]), t.y[q]));
+        hf.z[q] = add2(hf.z[q], mul2(f2(j6[n]), t.z[q]));
+      }
+    }
+    Spins<VEC> so, se;
+    load_site<F>(base + own * site_stride, ps, so);
+    load_site<F>(base + h * site_stride, ps, se);       // even site with the same half-index
+    float je[6], he[3];
+    load_rec<J16>(p.rec, sd.rec_off + h, je, he);
+#pragma unroll
+    for (int q = 0; q < VEC / 2; ++q) {
+      const float2 hx2 = add2(hf.x[q], f2(h3[0]));
+      const float2 hy2 = add2(hf.y[q], f2(h3[1]));
+      const float2 hz2 = add2(hf.z[q], f2(h3[2]));
+      const float2 eo = add2(add2(mul2(so.x[q], hx2), mul2(so.y[q], hy2)), mul2(so.z[q], hz2));
+      const float2 ee = add2(add2(mul2(se.x[q], f2(he[0])), mul2(se.y[q], f2(he[1]))),
+                             mul2(se.z[q], f2(he[2])));
+      acc[2 * q] -= eo.x + ee.x;
+      acc[2 * q + 1] -= eo.y + ee.y;
+    }
+  }
+
+  // block reduction in FP64, fixed order
+  __shared__ double red[RED_BS / 32][8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) {
+    double d = (double)acc[v];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+    if (lane == 0) red[warp][v] = d;
+  }
+  __syncthreads();
+  if (threadIdx.x < VEC) {
+    double d = 0.0;
+    for (int w = 0; w < RED_BS / 32; ++w) d += red[w][threadIdx.x];
+    p.partials[(long long)blockIdx.x * 8 + threadIdx.x] = d;
+  }
+}
+
+template <int VEC>
+__global__ void k_energy_final(const EnergyParams p) {
+  const int s = blockIdx.x;
+  const int w = threadIdx.x;
+  if (w >= p.Wp) return;
+  const SampleDev& sd = p.samples[s];
+  const int g = w / VEC, v = w % VEC;
+  double e = 0.0;
+  for (int sb = 0; sb < sd.e_nsb; ++sb)
+    e += p.partials[(long long)(sd.e_block0 + sb * p.G + g) * 8 + v];
+  p.E[(long long)s * p.Wp + w] = e;
+}
+
+template <int F, bool J16>
+static cudaError_t energy_fmt(const EnergyParams& p, int nb, cudaStream_t st) {
+  k_energy<F, J16><<<nb, RED_BS, 0, st>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_energy_final<FmtInfo<F>::VEC><<<p.n_samples, ((p.Wp + 31) / 32) * 32, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy(int fmt, bool j16, const EnergyParams& p, int nb, cudaStream_t st) {
+  switch (fmt) {
+    case FMT_F32: return j16 ? energy_fmt<FMT_F32, true>(p, nb, st) : energy_fmt<FMT_F32, false>(p, nb, st);
+    case FMT_F16: return j16 ? energy_fmt<FMT_F16, true>(p, nb, st) : energy_fmt<FMT_F16, false>(p, nb, st);
+    case FMT_BF16: return j16 ? energy_fmt<FMT_BF16, true>(p, nb, st) : energy_fmt<FMT_BF16, false>(p, nb, st);
+    case FMT_ANG16: return j16 ? energy_fmt<FMT_ANG16, true>(p, nb, st) : energy_fmt<FMT_ANG16, false>(p, nb, st);
+    case FMT_OCT16: return j16 ? energy_fmt<FMT_OCT16, true>(p, nb, st) : energy_fmt<FMT_OCT16, false>(p, nb, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Parallel tempering, Eq. (4): one thread per (sample, replica) chain walks the
+// pairs (k, k+1) upwards from the lowest temperature; an accepted exchange
+// swaps the temperatures of the two configurations.  Runs as one block so that
+// the counters can be advanced after every chain is done.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_pt(const PTParams p) {
+  const int n_chains = p.n_samples * p.R_O;
+  for (int c = threadIdx.x; c < n_chains; c += blockDim.x) {
+    const int s = c / p.R_O, r = c - s * p.R_O;
+    int* perm = p.perm + (long long)c * p.R_T;
+    const double* E = p.E + (long long)s * p.Wp + r * p.R_T;
+    const double* ib = p.inv_temps + (long long)s * p.R_T;
+    const uint32_t step = (uint32_t)p.counters[1];
+    if (p.bump_pt) {
+      for (int k = 0; k + 1 < p.R_T; ++k) {
+        const int a = perm[k], b = perm[k + 1];
+        const double dbeta = ib[k + 1] - ib[k];
+        const double dE = E[b] - E[a];
+        const double x = dbeta * dE;
+        const uint4 rnd = philox4x32_10(make_uint4((uint32_t)k, (uint32_t)c, step, TAG_PT),
+                                        p.seed_lo, p.seed_hi);
+        const double u = (double)u01(rnd.x);
+        const bool acc = (x >= 0.0) || (u < exp(x));
+        if (acc) {
+          perm[k] = b;
+          perm[k + 1] = a;
+          p.accepted[(long long)c * (p.R_T - 1) + k] += 1ull;
+        }
+      }
+    }
+    float* beta = p.beta + (long long)s * p.Wp + r * p.R_T;
+    for (int t = 0; t < p.R_T; ++t) beta[perm[t]] = (float)ib[t];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    p.counters[0] += (unsigned long long)p.sweeps_per_call;
+    p.counters[1] += (unsigned long long)p.bump_pt;
+  }
+}
+
+cudaError_t launch_pt(const PTParams& p, cudaStream_t st) {
+  int n = p.n_samples * p.R_O;
+  int bs = n >= 1024 ? 1024 : ((n + 31) / 32) * 32;
+  k_pt<<<1, bs, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+__global__ void k_bump(unsigned long long* counters, int sweeps, int pts) {
+  counters[0] += (unsigned long long)sweeps;
+  counters[1] += (unsigned long long)pts;
+}
+
+cudaError_t launch_bump(unsigned long long* counters, int sweeps, int pts, cudaStream_t st) {
+  k_bump<<<1, 1, 0, st>>>(counters, sweeps, pts);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Overlaps: q^{mu nu} = (1/N) sum_i s_i^mu(A) s_i^nu(B) and the modes
+// k = (2 pi/L) e_a, between the configurations A, B of replicas 0 and 1 that
+// hold temperature t.  A block handles one z-plane of one sample; a thread one
+// slot t and every YL-th row.  Per row the x-sums (with the e^{i kx x} twiddle)
+// run in FP32; rows are added in FP64 with the e^{i ky y} twiddle; the z twiddle
+// is applied in the final kernel.
+// ---------------------------------------------------------------------------
+template <int F>
+__global__ void __launch_bounds__(MEAS_BS) k_measure_planes(const MeasureParams p) {
+  constexpr int ELEM = FmtInfo<F>::ELEM;
+  const int s = blockIdx.y, z = blockIdx.x;
+  const SampleDev& sd = p.samples[s];
+  const int L = sd.L;
+  if (z >= L) return;
+  __shared__ float tw[2][512];
+  __shared__ double red[MEAS_BS][15];
+  for (int x = threadIdx.x; x < L; x += blockDim.x) {
+    float sx, cx;
+    sincospif(2.0f * (float)x / (float)L, &sx, &cx);
+    tw[0][x] = cx;
+    tw[1][x] = sx;
+  }
+  __syncthreads();
+  const int R_T = p.R_T;
+  const int YL = MEAS_BS / R_T;
+  const int t = threadIdx.x % R_T, yl = threadIdx.x / R_T;
+  const bool active = yl < YL;
+  double Q[9], QX[18], QY[18];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) Q[i] = 0.0;
+#pragma unroll
+  for (int i = 0; i < 18; ++i) { QX[i] = 0.0; QY[i] = 0.0; }
+  if (active) {
+    const int* perm = p.perm + (long long)s * p.R_O * R_T;
+    const int wA = perm[t], wB = R_T + perm[R_T + t];
+    const uint32_t half_n = (uint32_t)sd.N >> 1;
+    const long long site_stride = (long long)p.Wp * ELEM;
+    const unsigned char* base = p.spins + sd.spin_off;
+    for (int y = yl; y < L; y += YL) {
+      float R0[9], RX[18];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) R0[i] = 0.0f;
+#pragma unroll
+      for (int i = 0; i < 18; ++i) RX[i] = 0.0f;
+      const uint32_t row = (uint32_t)(y + L * z) * (uint32_t)L;
+      for (int x = 0; x < L; ++x) {
+        const uint32_t site = row + (uint32_t)x;
+        const uint32_t ss = (((uint32_t)(x + y + z)) & 1u) * half_n + (site >> 1);
+        const unsigned char* pl = base + ss * site_stride;
+        float a[3], b[3];
+        decode_one<F>(pl, sd.plane_stride, wA, a[0], a[1], a[2]);
+        decode_one<F>(pl, sd.plane_stride, wB, b[0], b[1], b[2]);
+        const float cx = tw[0][x], sx = tw[1][x];
+#pragma unroll
+        for (int mu = 0; mu < 3; ++mu)
+#pragma unroll
+          for (int nu = 0; nu < 3; ++nu) {
+            const float pr = a[mu] * b[nu];
+            R0[mu * 3 + nu] += pr;
+            RX[(mu * 3 + nu) * 2] += pr * cx;
+            RX[(mu * 3 + nu) * 2 + 1] += pr * sx;
+          }
+      }
+      double sy, cy;
+      sincospi(2.0 * (double)y / (double)L, &sy, &cy);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        Q[i] += (double)R0[i];
+        QX[2 * i] += (double)RX[2 * i];
+        QX[2 * i + 1] += (double)RX[2 * i + 1];
+        QY[2 * i] += (double)R0[i] * cy;
+        QY[2 * i + 1] += (double)R0[i] * sy;
+      }
+    }
+  }
+  // reduce over the YL row-lanes of each slot in three passes of 15 values
+  double* out = p.partials + (((long long)s * p.Lmax + z) * R_T) * 45;
+  for (int pass = 0; pass < 3; ++pass) {
+#pragma unroll
+    for (int i = 0; i < 15; ++i) {
+      const int v = pass * 15 + i;
+      red[threadIdx.x][i] = v < 9 ? Q[v] : (v < 27 ? QX[v - 9] : QY[v - 27]);
+    }
+    __syncthreads();
+    if (threadIdx.x < R_T) {
+      for (int i = 0; i < 15; ++i) {
+        double acc = 0.0;
+        for (int k = 0; k < YL; ++k) acc += red[k * R_T + threadIdx.x][i];
+        out[threadIdx.x * 45 + pass * 15 + i] = acc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_measure_final(const MeasureParams p) {
+  const int s = blockIdx.x;
+  const SampleDev& sd = p.samples[s];
+  const int L = sd.L;
+  const double invN = 1.0 / (double)sd.N;
+  for (int idx = threadIdx.x; idx < p.R_T * 9; idx += blockDim.x) {
+    const int t = idx / 9, mn = idx % 9;
+    double q = 0, xr = 0, xi = 0, yr = 0, yi = 0, zr = 0, zi = 0;
+    for (int z = 0; z < L; ++z) {
+      const double* v = p.partials + (((long long)s * p.Lmax + z) * p.R_T + t) * 45;
+      q += v[mn];
+      xr += v[9 + 2 * mn];
+      xi += v[9 + 2 * mn + 1];
+      yr += v[27 + 2 * mn];
+      yi += v[27 + 2 * mn + 1];
+      double sz, cz;
+      sincospi(2.0 * (double)z / (double)L, &sz, &cz);
+      zr += v[mn] * cz;
+      zi += v[mn] * sz;
+    }
+    p.q[((long long)s * p.R_T + t) * 9 + mn] = q * invN;
+    double* k = p.qk + ((long long)s * p.R_T + t) * 54;
+    k[(0 * 9 + mn) * 2] = xr * invN;
+    k[(0 * 9 + mn) * 2 + 1] = xi * invN;
+    k[(1 * 9 + mn) * 2] = yr * invN;
+    k[(1 * 9 + mn) * 2 + 1] = yi * invN;
+    k[(2 * 9 + mn) * 2] = zr * invN;
+    k[(2 * 9 + mn) * 2 + 1] = zi * invN;
+  }
+}
+
+template <int F>
+static cudaError_t measure_fmt(const MeasureParams& p, int lmax, cudaStream_t st) {
+  k_measure_planes<F><<<dim3(lmax, p.n_samples), MEAS_BS, 0, st>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_measure_final<<<p.n_samples, 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_measure(int fmt, const MeasureParams& p, int lmax, cudaStream_t st) {
+  switch (fmt) {
+    case FMT_F32: return measure_fmt<FMT_F32>(p, lmax, st);
+    case FMT_F16: return measure_fmt<FMT_F16>(p, lmax, st);
+    case FMT_BF16: return measure_fmt<FMT_BF16>(p, lmax, st);
+    case FMT_ANG16: return measure_fmt<FMT_ANG16>(p, lmax, st);
+    case FMT_OCT16: return measure_fmt<FMT_OCT16>(p, lmax, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Initial state and conversions.  One thread per (site, chunk), all sites.
+// ---------------------------------------------------------------------------
+struct ConvItem {
+  const SampleDev* sd;
+  uint32_t site, g, ss;
+  bool ok;
+};
+
+__device__ __forceinline__ ConvItem conv_item(const ConvParams& p) {
+  ConvItem it;
+  const int2 blk = p.blocks[blockIdx.x];
+  it.sd = &p.samples[blk.x];
+  const uint32_t item = (uint32_t)blk.y + threadIdx.x;
+  const uint32_t N = (uint32_t)it.sd->N;
+  it.ok = item < N * (uint32_t)p.G;
+  if (!it.ok) return it;
+  it.site = (__umulhi(item, p.fdG_m) + item) >> p.fdG_s;
+  it.g = item - it.site * (uint32_t)p.G;
+  const uint32_t L = it.sd->L;
+  const uint32_t r = (__umulhi(it.site, it.sd->fdL_m) + it.site) >> it.sd->fdL_s;
+  const uint32_t x = it.site - r * L;
+  const uint32_t z = (__umulhi(r, it.sd->fdL_m) + r) >> it.sd->fdL_s;
+  const uint32_t y = r - z * L;
+  it.ss = ((x + y + z) & 1u) * (N >> 1) + (it.site >> 1);
+  return it;
+}
+
+template <int F>
+__global__ void k_init(const ConvParams p) {
+  constexpr int VEC = FmtInfo<F>::VEC, PL = FmtInfo<F>::PLANES, ELEM = FmtInfo<F>::ELEM;
+  const ConvItem it = conv_item(p);
+  if (!it.ok) return;
+  Spins<VEC> s;
+  const uint32_t sys0 = (uint32_t)it.sd->sys_base + it.g * VEC;
+#pragma unroll
+  for (int k = 0; k < VEC / 2; ++k) {
+    const uint4 r = philox4x32_10(make_uint4(it.site, (sys0 >> 1) + k, 0u, TAG_INIT),
+                                  p.seed_lo, p.seed_hi);
+    double v[2][3];
+    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const double u1 = (double)u01(w[2 * b]), u2 = (double)u01(w[2 * b + 1]);
+      const double zc = 2.0 * u1 - 1.0;
+      const double rho = 2.0 * sqrt(u1 * (1.0 - u1));
+      double sp, cp;
+      sincospi(2.0 * u2, &sp, &cp);
+      v[b][0] = rho * cp;
+      v[b][1] = rho * sp;
+      v[b][2] = zc;
+    }
+    s.x[k] = make_float2((float)v[0][0], (float)v[1][0]);
+    s.y[k] = make_float2((float)v[0][1], (float)v[1][1]);
+    s.z[k] = make_float2((float)v[0][2], (float)v[1][2]);
+  }
+  uint4 c[PL];
+  encode<F>(s, c);
+  unsigned char* o = p.spins + it.sd->spin_off + (long long)it.g * 16 +
+                     (long long)it.ss * p.Wp * ELEM;
+#pragma unroll
+  for (int pl = 0; pl < PL; ++pl)
+    *reinterpret_cast<uint4*>(o + pl * it.sd->plane_stride) = c[pl];
+}
+
+template <int F>
+__global__ void k_get(const ConvParams p) {
+  constexpr int VEC = FmtInfo<F>::VEC, PL = FmtInfo<F>::PLANES, ELEM = FmtInfo<F>::ELEM;
+  const ConvItem it = conv_item(p);
+  if (!it.ok) return;
+  const int sidx = p.blocks[blockIdx.x].x;
+  const unsigned char* o = p.spins + it.sd->spin_off + (long long)it.g * 16 +
+                           (long long)it.ss * p.Wp * ELEM;
+  uint4 c[PL];
+#pragma unroll
+  for (int pl = 0; pl < PL; ++pl)
+    c[pl] = *reinterpret_cast<const uint4*>(o + pl * it.sd->plane_stride);
+  Spins<VEC> s;
+  decode<F>(c, s);
+  float* out = p.xyz + p.xyz_off[sidx];
+  const long long N = it.sd->N;
+#pragma unroll
+  for (int k = 0; k < VEC / 2; ++k) {
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int w = (int)it.g * VEC + 2 * k + b;
+      if (w < p.W) {
+        float* q = out + ((long long)w * N + it.site) * 3;
+        q[0] = b ? s.x[k].y : s.x[k].x;
+        q[1] = b ? s.y[k].y : s.y[k].x;
+        q[2] = b ? s.z[k].y : s.z[k].x;
+      }
+    }
+  }
+}
+
+template <int F>
+__global__ void k_set(const ConvParams p) {
+  constexpr int VEC = FmtInfo<F>::VEC, PL = FmtInfo<F>::PLANES, ELEM = FmtInfo<F>::ELEM;
+  const ConvItem it = conv_item(p);
+  if (!it.ok) return;
+  const int sidx = p.blocks[blockIdx.x].x;
+  const float* in = p.xyz + p.xyz_off[sidx];
+  const long long N = it.sd->N;
+  Spins<VEC> s;
+#pragma unroll
+  for (int k = 0; k < VEC / 2; ++k) {
+    float v[2][3];
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int w = (int)it.g * VEC + 2 * k + b;
+      if (w < p.W) {
+        const float* q = in + ((long long)w * N + it.site) * 3;
+        v[b][0] = q[0];
+        v[b][1] = q[1];
+        v[b][2] = q[2];
+      } else {
+        v[b][0] = 0.0f;
+        v[b][1] = 0.0f;
+        v[b][2] = 1.0f;
+      }
+    }
+    s.x[k] = make_float2(v[0][0], v[1][0]);
+    s.y[k] = make_float2(v[0][1], v[1][1]);
+    s.z[k] = make_float2(v[0][2], v[1][2]);
+  }
+  uint4 c[PL];
+  encode<F>(s, c);
+  unsigned char* o = p.spins + it.sd->spin_off + (long long)it.g * 16 +
+                     (long long)it.ss * p.Wp * ELEM;
+#pragma unroll
+  for (int pl = 0; pl < PL; ++pl)
+    *reinterpret_cast<uint4*>(o + pl * it.sd->plane_stride) = c[pl];
+}
+
+#define HSG_CONV_SWITCH(KERNEL)                                                          \
+  switch (fmt) {                                                                        \
+    case FMT_F32: KERNEL<FMT_F32><<<nb, 256, 0, st>>>(p); break;                        \
+    case FMT_F16: KERNEL<FMT_F16><<<nb, 256, 0, st>>>(p); break;                        \
+    case FMT_BF16: KERNEL<FMT_BF16><<<nb, 256, 0, st>>>(p); break;                      \
+    case FMT_ANG16: KERNEL<FMT_ANG16><<<nb, 256, 0, st>>>(p); break;                    \
+    case FMT_OCT16: KERNEL<FMT_OCT16><<<nb, 256, 0, st>>>(p); break;                    \
+    default: return cudaErrorInvalidValue;                                              \
+  }                                                                                     \
+  return cudaGetLastError();
+
+cudaError_t launch_init(int fmt, const ConvParams& p, int nb, cudaStream_t st) {
+  HSG_CONV_SWITCH(k_init)
+}
+cudaError_t launch_get(int fmt, const ConvParams& p, int nb, cudaStream_t st) {
+  HSG_CONV_SWITCH(k_get)
+}
+cudaError_t launch_set(int fmt, const ConvParams& p, int nb, cudaStream_t st) {
+  HSG_CONV_SWITCH(k_set)
+}
+
+}  // namespace hsg

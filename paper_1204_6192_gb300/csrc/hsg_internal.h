@@ -1,0 +1,117 @@
+// Internal layout and kernel-launch interface of libhsg (not part of the C ABI).
+//
+// Device data layout (all samples of a context in one allocation each):
+//   spins   per sample, sites in parity-split order: storage site
+//           ss(i) = p(i) * N/2 + (i >> 1), so each half-sweep touches one
+//           contiguous half of the array.  Component formats keep three planes
+//           [c][ss][Wp]; packed formats one plane [ss][Wp] of 32-bit words.
+//           The system index is innermost: one 16-byte chunk holds VEC
+//           systems of one site, so a warp reads 512 contiguous bytes.
+//   records per storage site 12 scalars (FP32 or FP16):
+//           [J+x, J-x, J+y, J-y], [J+z, J-z, Hx, Hy], [Hz, 0, 0, 0]
+//           i.e. the six bonds of the site and its field, shared by all Wp
+//           systems of the sample (the paper's reuse of J and H across
+//           temperatures and replicas, Sec. 3.3).
+//   beta    float [n_samples][Wp]: inverse temperature of each system.
+//   perm    int32 [n_samples][R_O][R_T]; temps/inv_temps double [n_samples][R_T].
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hsg {
+
+// spin storage formats (values of hsg_precision)
+enum Fmt { FMT_F32 = 0, FMT_F16 = 1, FMT_BF16 = 2, FMT_ANG16 = 3, FMT_OCT16 = 4 };
+
+constexpr int SWEEP_BS = 256;     // threads per block, streaming sweep kernels
+constexpr int RED_BS = 256;       // threads per block, energy reduction
+constexpr int RED_SITES = 8;      // odd sites per thread in the energy kernel
+constexpr int MEAS_BS = 256;      // threads per block, measurement partials
+
+struct FastDivH {
+  uint32_t d, m, s;
+};
+
+struct SampleDev {
+  int L, N, Lh;
+  uint32_t fdLh_m, fdLh_s, fdL_m, fdL_s;
+  long long spin_off;       // byte offset of the sample's spin block
+  long long plane_stride;   // bytes between component planes (N * Wp * ELEM)
+  long long rec_off;        // record index of storage site 0
+  int sys_base;             // global id of system 0 = sample * Wp
+  int e_block0;             // first energy block of the sample
+  int e_nsb;                // energy site-blocks per chunk
+};
+
+struct SweepParams {
+  unsigned char* spins;
+  const void* rec;
+  const SampleDev* samples;
+  const int2* blocks;       // (sample, first item) per block
+  const float* beta;        // [n_samples][Wp]
+  const unsigned long long* counters;   // [0] sweeps done, [1] PT passes done
+  int G, Wp;
+  uint32_t fdG_m, fdG_s;
+  uint32_t seed_lo, seed_hi;
+  int parity;
+  int sweep_offset;
+};
+
+struct EnergyParams {
+  const unsigned char* spins;
+  const void* rec;
+  const SampleDev* samples;
+  const int4* blocks;       // (sample, g, site-block, 0)
+  double* partials;         // [n_blocks][8]
+  double* E;                // [n_samples][Wp]
+  int G, Wp, n_samples;
+};
+
+struct PTParams {
+  const double* E;          // [n_samples][Wp]
+  const double* inv_temps;  // [n_samples][R_T]
+  int* perm;                // [n_samples][R_O][R_T]
+  float* beta;              // [n_samples][Wp]
+  unsigned long long* accepted;   // [n_samples][R_O][R_T-1]
+  unsigned long long* counters;
+  int n_samples, R_O, R_T, Wp;
+  uint32_t seed_lo, seed_hi;
+  int sweeps_per_call;      // added to counters[0] after the pass
+  int bump_pt;              // 1: this is a PT pass (counters[1] += 1)
+};
+
+struct MeasureParams {
+  const unsigned char* spins;
+  const SampleDev* samples;
+  const int* perm;
+  double* partials;         // [n_samples][Lmax][R_T][45]
+  double* q;                // [n_samples][R_T][9]
+  double* qk;               // [n_samples][R_T][3][9][2]
+  int n_samples, R_O, R_T, Wp, Lmax;
+};
+
+struct ConvParams {
+  unsigned char* spins;
+  const SampleDev* samples;
+  const int2* blocks;       // same as the sweep table with parity ignored (both halves)
+  float* xyz;               // [sum_s W * N_s * 3]
+  const long long* xyz_off; // per sample, float offset of its block
+  int G, Wp, W;
+  uint32_t fdG_m, fdG_s;
+  uint32_t seed_lo, seed_hi;
+};
+
+// launchers (hsg_kernels*.cu)
+cudaError_t launch_half_sweep(int fmt, bool hb, bool j16, bool fast, const SweepParams& p,
+                              int n_blocks, cudaStream_t st);
+cudaError_t launch_energy(int fmt, bool j16, const EnergyParams& p, int n_blocks,
+                          cudaStream_t st);
+cudaError_t launch_pt(const PTParams& p, cudaStream_t st);
+cudaError_t launch_bump(unsigned long long* counters, int sweeps, int pts, cudaStream_t st);
+cudaError_t launch_measure(int fmt, const MeasureParams& p, int lmax, cudaStream_t st);
+cudaError_t launch_init(int fmt, const ConvParams& p, int n_blocks, cudaStream_t st);
+cudaError_t launch_get(int fmt, const ConvParams& p, int n_blocks, cudaStream_t st);
+cudaError_t launch_set(int fmt, const ConvParams& p, int n_blocks, cudaStream_t st);
+
+}  // namespace hsg

@@ -1,0 +1,295 @@
+"""Python binding of libhsg (include/hsg.h): argument marshalling only.
+
+Every step of the Monte Carlo path runs inside the CUDA library; this module
+converts numpy arrays to plain pointers and C status codes to exceptions.
+There is no fallback: if libhsg.so is missing or cannot be loaded, every call
+raises.  Method names follow the C entry points (``hsg_sweep_or`` ->
+``Context.sweep_or`` and so on); the module-level ``hsg_*`` functions are the
+C names themselves.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhsg.so")
+
+PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2, "angle16": 3, "oct16": 4}
+STATUS = {0: "HSG_OK", 1: "HSG_EINVAL", 2: "HSG_ENOMEM", 3: "HSG_ECUDA", 4: "HSG_ETIMEOUT",
+          5: "HSG_ESTATE"}
+VARIANT_AUTO, VARIANT_TWO_PASS, VARIANT_RESIDENT = 0, 1, 2
+
+
+class HsgError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("j_fp16", ctypes.c_int), ("fast_math", ctypes.c_int),
+                ("n_hb_per_step", ctypes.c_int), ("n_or_per_step", ctypes.c_int),
+                ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("variant", ctypes.c_int)]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [("E", ctypes.POINTER(ctypes.c_double)), ("q", ctypes.POINTER(ctypes.c_double)),
+                ("qk", ctypes.POINTER(ctypes.c_double)), ("perm", ctypes.POINTER(ctypes.c_int32))]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_samples", ctypes.c_int), ("n_temps", ctypes.c_int), ("n_replicas", ctypes.c_int),
+                ("W", ctypes.c_int), ("Wp", ctypes.c_int), ("precision", ctypes.c_int),
+                ("j_fp16", ctypes.c_int), ("variant", ctypes.c_int),
+                ("total_sites", ctypes.c_longlong), ("total_spins", ctypes.c_longlong),
+                ("spin_bytes", ctypes.c_longlong), ("rec_bytes", ctypes.c_longlong),
+                ("sweep_count", ctypes.c_uint64), ("pt_count", ctypes.c_uint64),
+                ("stream", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libhsg.so; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libhsg.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
+    fp = ctypes.POINTER(ctypes.c_float)
+    ctxpp = ctypes.POINTER(ctypes.c_void_p)
+    fpp = ctypes.POINTER(fp)
+    sigs = {
+        "hsg_default_options": (None, [ctypes.POINTER(Options)]),
+        "hsg_create": (ip, [ctxpp, ip, dp, ip, ip, fp, fp, ctypes.c_uint64, ctypes.POINTER(Options)]),
+        "hsg_create_batch": (ip, [ctxpp, ip, ctypes.POINTER(ctypes.c_int), dp, ip, ip, fpp, fpp,
+                                  ctypes.c_uint64, ctypes.POINTER(Options)]),
+        "hsg_sweep_or": (ip, [vp, ip]),
+        "hsg_sweep_hb": (ip, [vp, ip]),
+        "hsg_pt_exchange": (ip, [vp]),
+        "hsg_pt_exchange_energies": (ip, [vp, dp]),
+        "hsg_step": (ip, [vp, ip]),
+        "hsg_energies": (ip, [vp, dp]),
+        "hsg_measure": (ip, [vp, ctypes.POINTER(Obs)]),
+        "hsg_get_spins": (ip, [vp, fp]),
+        "hsg_set_spins": (ip, [vp, fp]),
+        "hsg_get_spins_dev": (ip, [vp, vp]),
+        "hsg_set_spins_dev": (ip, [vp, vp]),
+        "hsg_get_perm": (ip, [vp, ctypes.POINTER(ctypes.c_int32)]),
+        "hsg_get_pt_stats": (ip, [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+        "hsg_get_info": (ip, [vp, ctypes.POINTER(Info)]),
+        "hsg_sync": (ip, [vp]),
+        "hsg_last_error": (ctypes.c_char_p, [vp]),
+        "hsg_status_string": (ctypes.c_char_p, [ip]),
+        "hsg_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(a: np.ndarray, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def default_options() -> Options:
+    o = Options()
+    lib().hsg_default_options(ctypes.byref(o))
+    return o
+
+
+class Context:
+    """One hsg_ctx: a batch of disorder samples updated together on one GPU.
+
+    ``samples``: objects with L, J [N,3], H [N,3] or None, temps [n_temps].
+    """
+
+    def __init__(self, samples: Sequence, n_replicas: int, seed: int, precision: str = "fp32",
+                 j_fp16: bool = False, fast_math: bool = False, n_hb: int = 1, n_or: int = 5,
+                 device: int = 0, stream: Optional[int] = None, variant: int = VARIANT_AUTO):
+        L = lib()
+        self._ctx = ctypes.c_void_p()
+        opt = default_options()
+        opt.precision = PRECISIONS[precision]
+        opt.j_fp16 = int(bool(j_fp16))
+        opt.fast_math = int(bool(fast_math))
+        opt.n_hb_per_step = n_hb
+        opt.n_or_per_step = n_or
+        opt.device = device
+        opt.stream = stream
+        opt.variant = variant
+        self.samples = list(samples)
+        self.n_samples = len(self.samples)
+        self.n_temps = len(self.samples[0].temps)
+        self.n_replicas = n_replicas
+        self.W = self.n_temps * n_replicas
+        self.Ls = [int(s.L) for s in self.samples]
+        self.Ns = [l ** 3 for l in self.Ls]
+        self.precision = precision
+        # keep the float32 copies alive for the call
+        Js = [np.ascontiguousarray(s.J, dtype=np.float32) for s in self.samples]
+        Hs = [None if s.H is None else np.ascontiguousarray(s.H, dtype=np.float32) for s in self.samples]
+        temps = np.ascontiguousarray(np.concatenate([np.asarray(s.temps, dtype=np.float64)
+                                                     for s in self.samples]))
+        fptr = ctypes.POINTER(ctypes.c_float)
+        Jp = (fptr * self.n_samples)(*[_ptr(j, ctypes.c_float) for j in Js])
+        Hp = (fptr * self.n_samples)(*[(_ptr(h, ctypes.c_float) if h is not None else fptr())
+                                       for h in Hs])
+        Ls = (ctypes.c_int * self.n_samples)(*self.Ls)
+        st = L.hsg_create_batch(ctypes.byref(self._ctx), self.n_samples, Ls, _ptr(temps, ctypes.c_double),
+                                self.n_temps, n_replicas, Jp, Hp, ctypes.c_uint64(seed),
+                                ctypes.byref(opt))
+        if st != 0:
+            raise HsgError(st, (L.hsg_last_error(None) or b"").decode())
+
+    # -- helpers ----------------------------------------------------------------
+    def _check(self, st: int):
+        if st != 0:
+            raise HsgError(st, (lib().hsg_last_error(self._ctx) or b"").decode())
+
+    @property
+    def handle(self):
+        return self._ctx
+
+    def close(self):
+        if self._ctx:
+            lib().hsg_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- the C entry points -----------------------------------------------------
+    def sweep_or(self, n: int = 1):
+        self._check(lib().hsg_sweep_or(self._ctx, n))
+
+    def sweep_hb(self, n: int = 1):
+        self._check(lib().hsg_sweep_hb(self._ctx, n))
+
+    def pt_exchange(self):
+        self._check(lib().hsg_pt_exchange(self._ctx))
+
+    def pt_exchange_energies(self, E_sys: np.ndarray):
+        E = np.ascontiguousarray(E_sys, dtype=np.float64).reshape(self.n_samples, self.W)
+        self._check(lib().hsg_pt_exchange_energies(self._ctx, _ptr(E, ctypes.c_double)))
+
+    def step(self, n: int = 1):
+        self._check(lib().hsg_step(self._ctx, n))
+
+    def energies(self) -> np.ndarray:
+        E = np.zeros((self.n_samples, self.W))
+        self._check(lib().hsg_energies(self._ctx, _ptr(E, ctypes.c_double)))
+        return E
+
+    def measure(self, q: bool = True):
+        ns, R_O, R_T = self.n_samples, self.n_replicas, self.n_temps
+        E = np.zeros((ns, R_O, R_T))
+        perm = np.zeros((ns, R_O, R_T), dtype=np.int32)
+        qa = np.zeros((ns, R_T, 3, 3))
+        qk = np.zeros((ns, R_T, 3, 3, 3, 2))
+        o = Obs()
+        o.E = _ptr(E, ctypes.c_double)
+        o.perm = _ptr(perm, ctypes.c_int32)
+        if q:
+            o.q = _ptr(qa, ctypes.c_double)
+            o.qk = _ptr(qk, ctypes.c_double)
+        self._check(lib().hsg_measure(self._ctx, ctypes.byref(o)))
+        return {"E": E, "perm": perm, "q": qa, "qk": qk}
+
+    def spin_shapes(self):
+        return [(self.W, n, 3) for n in self.Ns]
+
+    def _split(self, flat: np.ndarray):
+        out, o = [], 0
+        for n in self.Ns:
+            k = self.W * n * 3
+            out.append(flat[o:o + k].reshape(self.W, n, 3))
+            o += k
+        return out
+
+    def get_spins(self, out: Optional[np.ndarray] = None):
+        """Per-sample float32 arrays [W, N, 3] (memory-slot order)."""
+        total = sum(self.W * n * 3 for n in self.Ns)
+        flat = out if out is not None else np.empty(total, dtype=np.float32)
+        self._check(lib().hsg_get_spins(self._ctx, _ptr(flat, ctypes.c_float)))
+        return self._split(flat)
+
+    def set_spins(self, spins):
+        if isinstance(spins, np.ndarray) and spins.ndim == 1:
+            flat = np.ascontiguousarray(spins, dtype=np.float32)
+        else:
+            flat = np.ascontiguousarray(np.concatenate([np.asarray(s, dtype=np.float32).ravel()
+                                                        for s in spins]))
+        self._check(lib().hsg_set_spins(self._ctx, _ptr(flat, ctypes.c_float)))
+
+    def get_spins_dev(self, dev_ptr: int):
+        self._check(lib().hsg_get_spins_dev(self._ctx, ctypes.c_void_p(dev_ptr)))
+
+    def set_spins_dev(self, dev_ptr: int):
+        self._check(lib().hsg_set_spins_dev(self._ctx, ctypes.c_void_p(dev_ptr)))
+
+    def get_perm(self) -> np.ndarray:
+        perm = np.zeros((self.n_samples, self.n_replicas, self.n_temps), dtype=np.int32)
+        self._check(lib().hsg_get_perm(self._ctx, _ptr(perm, ctypes.c_int32)))
+        return perm
+
+    def pt_stats(self):
+        acc = np.zeros((self.n_samples, self.n_replicas, max(self.n_temps - 1, 1)), dtype=np.uint64)
+        n = ctypes.c_uint64()
+        self._check(lib().hsg_get_pt_stats(self._ctx, _ptr(acc, ctypes.c_uint64), ctypes.byref(n)))
+        return acc, int(n.value)
+
+    def info(self) -> Info:
+        i = Info()
+        self._check(lib().hsg_get_info(self._ctx, ctypes.byref(i)))
+        return i
+
+    def sync(self):
+        self._check(lib().hsg_sync(self._ctx))
+
+
+# C names -----------------------------------------------------------------------
+def hsg_create(L: int, temps, n_replicas: int, J, H, seed: int, **kw) -> Context:
+    from types import SimpleNamespace
+    return Context([SimpleNamespace(L=L, J=J, H=H, temps=np.asarray(temps))], n_replicas, seed, **kw)
+
+
+def hsg_create_batch(samples, n_replicas: int, seed: int, **kw) -> Context:
+    return Context(samples, n_replicas, seed, **kw)
+
+
+hsg_sweep_or = Context.sweep_or
+hsg_sweep_hb = Context.sweep_hb
+hsg_pt_exchange = Context.pt_exchange
+hsg_pt_exchange_energies = Context.pt_exchange_energies
+hsg_step = Context.step
+hsg_energies = Context.energies
+hsg_measure = Context.measure
+hsg_get_spins = Context.get_spins
+hsg_set_spins = Context.set_spins
+hsg_get_spins_dev = Context.get_spins_dev
+hsg_set_spins_dev = Context.set_spins_dev
+hsg_get_perm = Context.get_perm
+hsg_get_pt_stats = Context.pt_stats
+hsg_get_info = Context.info
+hsg_sync = Context.sync
+hsg_destroy = Context.close
