@@ -142,6 +142,13 @@ hsg_status hsg_step(hsg_ctx* ctx, int n_steps);
    double[n_samples][W].  Synchronises. */
 hsg_status hsg_energies(hsg_ctx* ctx, double* E_sys);
 
+/* The energies the last PT pass used (or the last hsg_energies result), host
+   double[n_samples][W], memory-slot order, without recomputing them.  After
+   hsg_step they are the energies of the state the step ended in, summed from
+   per-block partials that the last OR sweep of the step leaves behind.
+   Synchronises. */
+hsg_status hsg_last_energies(hsg_ctx* ctx, double* E_sys);
+
 /* Observables, caller-owned host buffers (any pointer may be NULL to skip):
  *   E    double[n_samples][n_replicas][n_temps]   energy by temperature slot
  *   q    double[n_samples][n_temps][3][3]         q^{mu nu} of replicas 0 and 1 (Eq. 5)

@@ -113,6 +113,10 @@ void orc_codec_roundtrip(double v[3], int codec) {
     case ORC_CODEC_BF16:
       for (int c = 0; c < 3; ++c) v[c] = orc_round_bf16(v[c]);
       return;
+    case ORC_CODEC_FP32:
+      /* binary32 storage: nearest float, ties to even (C's double -> float conversion) */
+      for (int c = 0; c < 3; ++c) v[c] = (double)(float)v[c];
+      return;
     case ORC_CODEC_ANGLE16: {
       /* polar angle theta in [0, pi] on 65536 levels, azimuth on a 2^16 ring */
       double z = v[2];

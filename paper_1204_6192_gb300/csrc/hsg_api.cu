@@ -47,9 +47,7 @@ struct hsg_ctx {
   int n_sweep_blocks = 0;
   int2* d_conv_blocks = nullptr;
   int n_conv_blocks = 0;
-  int4* d_energy_blocks = nullptr;
-  int n_energy_blocks = 0;
-  double* d_epart = nullptr;
+  double* d_epart = nullptr;        // energy partials [2][n_sweep_blocks][Wp]
   float* d_beta = nullptr;
   double* d_temps = nullptr;
   double* d_inv_temps = nullptr;
@@ -154,6 +152,8 @@ SweepParams sweep_params(hsg_ctx* c, int parity, int sweep_offset) {
   p.seed_hi = c->seed_hi;
   p.parity = parity;
   p.sweep_offset = sweep_offset;
+  p.epart = c->d_epart;
+  p.n_blocks = c->n_sweep_blocks;
   return p;
 }
 
@@ -162,12 +162,15 @@ EnergyParams energy_params(hsg_ctx* c) {
   p.spins = c->spins;
   p.rec = c->rec;
   p.samples = c->d_sd;
-  p.blocks = c->d_energy_blocks;
+  p.blocks = c->d_sweep_blocks;
   p.partials = c->d_epart;
   p.E = c->d_E;
   p.G = c->G;
   p.Wp = c->Wp;
   p.n_samples = c->ns;
+  p.n_blocks = c->n_sweep_blocks;
+  p.fdG_m = c->fdG_m;
+  p.fdG_s = c->fdG_s;
   return p;
 }
 
@@ -207,10 +210,12 @@ ConvParams conv_params(hsg_ctx* c, float* xyz, const long long* xyz_off) {
   return p;
 }
 
-hsg_status half_sweeps(hsg_ctx* c, bool hb, int sweep_offset) {
+// One sweep: the even half-sweep, then the odd one.  With `energy`, both
+// launches also leave the per-block energy partials of the new state.
+hsg_status half_sweeps(hsg_ctx* c, bool hb, int sweep_offset, bool energy = false) {
   for (int parity = 0; parity < 2; ++parity) {
     SweepParams p = sweep_params(c, parity, sweep_offset);
-    HSG_CUDA(c, launch_half_sweep(c->fmt, hb, c->j16, c->opt.fast_math != 0, p,
+    HSG_CUDA(c, launch_half_sweep(c->fmt, hb, c->j16, c->opt.fast_math != 0, energy, p,
                                   c->n_sweep_blocks, c->stream));
   }
   return HSG_OK;
@@ -218,15 +223,21 @@ hsg_status half_sweeps(hsg_ctx* c, bool hb, int sweep_offset) {
 
 hsg_status enqueue_energy(hsg_ctx* c) {
   EnergyParams p = energy_params(c);
-  HSG_CUDA(c, launch_energy(c->fmt, c->j16, p, c->n_energy_blocks, c->stream));
+  HSG_CUDA(c, launch_energy(c->fmt, c->j16, p, c->stream));
   return HSG_OK;
 }
 
+// A step: n_hb HB sweeps, n_or OR sweeps (the last one also produces the
+// energy partials of the final state), the energy sums and one PT pass.
 hsg_status enqueue_step(hsg_ctx* c) {
   const int nhb = c->opt.n_hb_per_step, nor = c->opt.n_or_per_step;
   for (int k = 0; k < nhb; ++k) HSG_TRY(half_sweeps(c, true, k));
-  for (int k = 0; k < nor; ++k) HSG_TRY(half_sweeps(c, false, nhb + k));
-  HSG_TRY(enqueue_energy(c));
+  for (int k = 0; k < nor; ++k) HSG_TRY(half_sweeps(c, false, nhb + k, k == nor - 1));
+  if (nor > 0) {
+    HSG_CUDA(c, launch_energy_final(energy_params(c), c->stream));
+  } else {
+    HSG_TRY(enqueue_energy(c));
+  }
   HSG_CUDA(c, launch_pt(pt_params(c, nhb + nor, 1), c->stream));
   return HSG_OK;
 }
@@ -327,7 +338,6 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
 
   // layout
   std::vector<int2> sweep_blocks, conv_blocks;
-  std::vector<int4> energy_blocks;
   size_t spin_off = 0, rec_off = 0;
   long long xyz = 0;
   for (int s = 0; s < n_samples; ++s) {
@@ -342,15 +352,12 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
     d.rec_off = (long long)rec_off;
     d.sys_base = s * Wp;
     const long long half_items = (long long)(d.N / 2) * G;
+    d.blk0 = (int)sweep_blocks.size();
     for (long long it = 0; it < half_items; it += SWEEP_BS)
       sweep_blocks.push_back(make_int2(s, (int)it));
+    d.blk1 = (int)sweep_blocks.size();
     const long long all_items = (long long)d.N * G;
     for (long long it = 0; it < all_items; it += 256) conv_blocks.push_back(make_int2(s, (int)it));
-    const int per_block = RED_BS * RED_SITES;
-    d.e_nsb = (d.N / 2 + per_block - 1) / per_block;
-    d.e_block0 = (int)energy_blocks.size();
-    for (int sb = 0; sb < d.e_nsb; ++sb)
-      for (int g = 0; g < G; ++g) energy_blocks.push_back(make_int4(s, g, sb, 0));
     size_t sb = (size_t)c->PL * d.plane_stride;
     spin_off += (sb + 255) / 256 * 256;
     rec_off += (size_t)d.N;
@@ -365,7 +372,6 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   c->rec_bytes = rec_off * (c->j16 ? 24 : 48);
   c->n_sweep_blocks = (int)sweep_blocks.size();
   c->n_conv_blocks = (int)conv_blocks.size();
-  c->n_energy_blocks = (int)energy_blocks.size();
 
   // records: six bonds and the field of every storage site
   std::vector<float> recf;
@@ -418,8 +424,7 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   HSG_ALLOC(c->d_sd, sizeof(SampleDev) * n_samples);
   HSG_ALLOC(c->d_sweep_blocks, sizeof(int2) * sweep_blocks.size());
   HSG_ALLOC(c->d_conv_blocks, sizeof(int2) * conv_blocks.size());
-  HSG_ALLOC(c->d_energy_blocks, sizeof(int4) * energy_blocks.size());
-  HSG_ALLOC(c->d_epart, sizeof(double) * 8 * energy_blocks.size());
+  HSG_ALLOC(c->d_epart, sizeof(double) * 2 * sweep_blocks.size() * Wp);
   HSG_ALLOC(c->d_beta, sizeof(float) * n_samples * Wp);
   HSG_ALLOC(c->d_temps, sizeof(double) * n_samples * n_temps);
   HSG_ALLOC(c->d_inv_temps, sizeof(double) * n_samples * n_temps);
@@ -451,7 +456,6 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   HSG_UP(c->d_sd, c->sd.data(), sizeof(SampleDev) * n_samples);
   HSG_UP(c->d_sweep_blocks, sweep_blocks.data(), sizeof(int2) * sweep_blocks.size());
   HSG_UP(c->d_conv_blocks, conv_blocks.data(), sizeof(int2) * conv_blocks.size());
-  HSG_UP(c->d_energy_blocks, energy_blocks.data(), sizeof(int4) * energy_blocks.size());
   HSG_UP(c->d_temps, temps, sizeof(double) * n_samples * n_temps);
   HSG_UP(c->d_inv_temps, inv.data(), sizeof(double) * inv.size());
   HSG_UP(c->d_perm, perm.data(), sizeof(int) * perm.size());
@@ -569,6 +573,16 @@ hsg_status hsg_energies(hsg_ctx* c, double* E_sys) {
   if (!E_sys) return bad_arg(c, "E_sys is NULL");
   HSG_CUDA(c, cudaSetDevice(c->device));
   HSG_TRY(enqueue_energy(c));
+  HSG_CUDA(c, cudaMemcpy2DAsync(E_sys, sizeof(double) * c->W, c->d_E, sizeof(double) * c->Wp,
+                                sizeof(double) * c->W, c->ns, cudaMemcpyDeviceToHost, c->stream));
+  HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return HSG_OK;
+}
+
+hsg_status hsg_last_energies(hsg_ctx* c, double* E_sys) {
+  HSG_CHECK_CTX(c);
+  if (!E_sys) return bad_arg(c, "E_sys is NULL");
+  HSG_CUDA(c, cudaSetDevice(c->device));
   HSG_CUDA(c, cudaMemcpy2DAsync(E_sys, sizeof(double) * c->W, c->d_E, sizeof(double) * c->Wp,
                                 sizeof(double) * c->W, c->ns, cudaMemcpyDeviceToHost, c->stream));
   HSG_CUDA(c, cudaStreamSynchronize(c->stream));

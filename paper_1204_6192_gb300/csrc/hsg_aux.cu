@@ -49,22 +49,20 @@ __device__ __forceinline__ void load_site(const unsigned char* p, long long ps,
 template <int F, bool J16>
 __global__ void __launch_bounds__(RED_BS) k_energy(const EnergyParams p) {
   constexpr int VEC = FmtInfo<F>::VEC, ELEM = FmtInfo<F>::ELEM;
-  const int4 blk = p.blocks[blockIdx.x];
+  const int2 blk = p.blocks[blockIdx.x];
   const SampleDev& sd = p.samples[blk.x];
-  const int g = blk.y;
+  const uint32_t item = (uint32_t)blk.y + threadIdx.x;
   const uint32_t half_n = (uint32_t)sd.N >> 1;
-  const uint32_t L = sd.L, Lh = sd.Lh;
-  const long long site_stride = (long long)p.Wp * ELEM;
-  const unsigned char* base = p.spins + sd.spin_off + (long long)g * 16;
-  const long long ps = sd.plane_stride;
-
-  float acc[VEC];
+  float eo[VEC], ee[VEC];
 #pragma unroll
-  for (int v = 0; v < VEC; ++v) acc[v] = 0.0f;
-
-  for (int k = 0; k < RED_SITES; ++k) {
-    const uint32_t h = ((uint32_t)blk.z * RED_SITES + k) * RED_BS + threadIdx.x;
-    if (h >= half_n) break;
+  for (int v = 0; v < VEC; ++v) { eo[v] = 0.0f; ee[v] = 0.0f; }
+  if (item < half_n * (uint32_t)p.G) {
+    const uint32_t h = (__umulhi(item, p.fdG_m) + item) >> p.fdG_s;
+    const uint32_t g = item - h * (uint32_t)p.G;
+    const uint32_t L = sd.L, Lh = sd.Lh;
+    const long long site_stride = (long long)p.Wp * ELEM;
+    const unsigned char* base = p.spins + sd.spin_off + (long long)g * 16;
+    const long long ps = sd.plane_stride;
     // odd site with half-index h and its even neighbours
     const uint32_t r = (__umulhi(h, sd.fdLh_m) + h) >> sd.fdLh_s;
     const uint32_t hx = h - r * Lh;
@@ -113,61 +111,62 @@ __global__ void __launch_bounds__(RED_BS) k_energy(const EnergyParams p) {
       const float2 hx2 = add2(hf.x[q], f2(h3[0]));
       const float2 hy2 = add2(hf.y[q], f2(h3[1]));
       const float2 hz2 = add2(hf.z[q], f2(h3[2]));
-      const float2 eo = add2(add2(mul2(so.x[q], hx2), mul2(so.y[q], hy2)), mul2(so.z[q], hz2));
-      const float2 ee = add2(add2(mul2(se.x[q], f2(he[0])), mul2(se.y[q], f2(he[1]))),
-                             mul2(se.z[q], f2(he[2])));
-      acc[2 * q] -= eo.x + ee.x;
-      acc[2 * q + 1] -= eo.y + ee.y;
+      const float2 o = add2(add2(mul2(so.x[q], hx2), mul2(so.y[q], hy2)), mul2(so.z[q], hz2));
+      const float2 e = add2(add2(mul2(se.x[q], f2(he[0])), mul2(se.y[q], f2(he[1]))),
+                            mul2(se.z[q], f2(he[2])));
+      eo[2 * q] = -o.x;
+      eo[2 * q + 1] = -o.y;
+      ee[2 * q] = -e.x;
+      ee[2 * q + 1] = -e.y;
     }
   }
-
-  // block reduction in FP64, fixed order
-  __shared__ double red[RED_BS / 32][8];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int v = 0; v < VEC; ++v) {
-    double d = (double)acc[v];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
-    if (lane == 0) red[warp][v] = d;
-  }
-  __syncthreads();
-  if (threadIdx.x < VEC) {
-    double d = 0.0;
-    for (int w = 0; w < RED_BS / 32; ++w) d += red[w][threadIdx.x];
-    p.partials[(long long)blockIdx.x * 8 + threadIdx.x] = d;
-  }
+  __shared__ float red[RED_BS][VEC];
+  block_system_sums<VEC, RED_BS>(ee, (uint32_t)blk.y, p.G, p.Wp,
+                                 p.partials + (long long)blockIdx.x * p.Wp, red);
+  block_system_sums<VEC, RED_BS>(eo, (uint32_t)blk.y, p.G, p.Wp,
+                                 p.partials + ((long long)p.n_blocks + blockIdx.x) * p.Wp, red);
 }
 
-template <int VEC>
-__global__ void k_energy_final(const EnergyParams p) {
-  const int s = blockIdx.x;
-  const int w = threadIdx.x;
-  if (w >= p.Wp) return;
+// E[s][w] = sum over the sample's blocks of the even-site and odd-site partials,
+// one block per system, fixed order.
+__global__ void __launch_bounds__(256) k_energy_final(const EnergyParams p) {
+  const int s = blockIdx.x / p.Wp, w = blockIdx.x - (blockIdx.x / p.Wp) * p.Wp;
   const SampleDev& sd = p.samples[s];
-  const int g = w / VEC, v = w % VEC;
-  double e = 0.0;
-  for (int sb = 0; sb < sd.e_nsb; ++sb)
-    e += p.partials[(long long)(sd.e_block0 + sb * p.G + g) * 8 + v];
-  p.E[(long long)s * p.Wp + w] = e;
+  double acc = 0.0;
+  for (int b = sd.blk0 + threadIdx.x; b < sd.blk1; b += blockDim.x) {
+    acc += p.partials[(long long)b * p.Wp + w];
+    acc += p.partials[((long long)p.n_blocks + b) * p.Wp + w];
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) p.E[(long long)s * p.Wp + w] = red[0];
 }
 
-template <int F, bool J16>
-static cudaError_t energy_fmt(const EnergyParams& p, int nb, cudaStream_t st) {
-  k_energy<F, J16><<<nb, RED_BS, 0, st>>>(p);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_energy_final<FmtInfo<F>::VEC><<<p.n_samples, ((p.Wp + 31) / 32) * 32, 0, st>>>(p);
+cudaError_t launch_energy_final(const EnergyParams& p, cudaStream_t st) {
+  k_energy_final<<<p.n_samples * p.Wp, 256, 0, st>>>(p);
   return cudaGetLastError();
 }
 
-cudaError_t launch_energy(int fmt, bool j16, const EnergyParams& p, int nb, cudaStream_t st) {
+template <int F, bool J16>
+static cudaError_t energy_fmt(const EnergyParams& p, cudaStream_t st) {
+  k_energy<F, J16><<<p.n_blocks, RED_BS, 0, st>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_energy_final(p, st);
+}
+
+cudaError_t launch_energy(int fmt, bool j16, const EnergyParams& p, cudaStream_t st) {
   switch (fmt) {
-    case FMT_F32: return j16 ? energy_fmt<FMT_F32, true>(p, nb, st) : energy_fmt<FMT_F32, false>(p, nb, st);
-    case FMT_F16: return j16 ? energy_fmt<FMT_F16, true>(p, nb, st) : energy_fmt<FMT_F16, false>(p, nb, st);
-    case FMT_BF16: return j16 ? energy_fmt<FMT_BF16, true>(p, nb, st) : energy_fmt<FMT_BF16, false>(p, nb, st);
-    case FMT_ANG16: return j16 ? energy_fmt<FMT_ANG16, true>(p, nb, st) : energy_fmt<FMT_ANG16, false>(p, nb, st);
-    case FMT_OCT16: return j16 ? energy_fmt<FMT_OCT16, true>(p, nb, st) : energy_fmt<FMT_OCT16, false>(p, nb, st);
+    case FMT_F32: return j16 ? energy_fmt<FMT_F32, true>(p, st) : energy_fmt<FMT_F32, false>(p, st);
+    case FMT_F16: return j16 ? energy_fmt<FMT_F16, true>(p, st) : energy_fmt<FMT_F16, false>(p, st);
+    case FMT_BF16: return j16 ? energy_fmt<FMT_BF16, true>(p, st) : energy_fmt<FMT_BF16, false>(p, st);
+    case FMT_ANG16: return j16 ? energy_fmt<FMT_ANG16, true>(p, st) : energy_fmt<FMT_ANG16, false>(p, st);
+    case FMT_OCT16: return j16 ? energy_fmt<FMT_OCT16, true>(p, st) : energy_fmt<FMT_OCT16, false>(p, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -288,7 +288,8 @@ __device__ __forceinline__ void hb_move(float& sx, float& sy, float& sz, float h
     } else {
       const float inv_a = 1.0f / a;
       dm = -log1pf((1.0f - u1) * expm1f(-2.0f * a)) * inv_a;
-      dp = (a < 40.0f) ? log1pf(u1 * expm1f(2.0f * a)) * inv_a : 2.0f - dm;
+      dp = 2.0f - dm;                   // accurate while cos t >= 0
+      if (dm > 1.0f && a < 40.0f) dp = log1pf(u1 * expm1f(2.0f * a)) * inv_a;
     }
   } else {
     dm = 2.0f * (1.0f - u1);
@@ -322,6 +323,27 @@ __device__ __forceinline__ void hb_move(float& sx, float& sy, float& sz, float h
   sx = ox * inv;
   sy = oy * inv;
   sz = oz * inv;
+}
+
+// Per-block, per-system sums of the per-thread values e[VEC] of a block whose
+// thread t holds item item0 + t (item = site * G + chunk g): out[g * VEC + v]
+// is the sum over the threads of chunk g, added in thread order in FP64, so
+// the result is independent of scheduling.  Every thread of the block calls it.
+template <int VEC, int BS>
+__device__ __forceinline__ void block_system_sums(const float* e, uint32_t item0, int G, int Wp,
+                                                  double* out, float (*red)[VEC]) {
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) red[threadIdx.x][v] = e[v];
+  __syncthreads();
+  const int r0 = (int)(item0 % (uint32_t)G);
+  for (int j = threadIdx.x; j < Wp; j += BS) {
+    const int g = j / VEC, v = j - (j / VEC) * VEC;
+    const int t0 = (g - r0 + G) % G;
+    double acc = 0.0;
+    for (int t = t0; t < BS; t += G) acc += (double)red[t][v];
+    out[j] = acc;
+  }
+  __syncthreads();
 }
 
 // Fast unsigned division by a runtime constant (Granlund & Montgomery, 1994):

@@ -25,8 +25,7 @@ namespace hsg {
 enum Fmt { FMT_F32 = 0, FMT_F16 = 1, FMT_BF16 = 2, FMT_ANG16 = 3, FMT_OCT16 = 4 };
 
 constexpr int SWEEP_BS = 256;     // threads per block, streaming sweep kernels
-constexpr int RED_BS = 256;       // threads per block, energy reduction
-constexpr int RED_SITES = 8;      // odd sites per thread in the energy kernel
+constexpr int RED_BS = SWEEP_BS;  // energy kernel: same blocks as the sweep
 constexpr int MEAS_BS = 256;      // threads per block, measurement partials
 
 struct FastDivH {
@@ -40,8 +39,7 @@ struct SampleDev {
   long long plane_stride;   // bytes between component planes (N * Wp * ELEM)
   long long rec_off;        // record index of storage site 0
   int sys_base;             // global id of system 0 = sample * Wp
-  int e_block0;             // first energy block of the sample
-  int e_nsb;                // energy site-blocks per chunk
+  int blk0, blk1;           // the sample's blocks in the sweep block table
 };
 
 struct SweepParams {
@@ -56,16 +54,19 @@ struct SweepParams {
   uint32_t seed_lo, seed_hi;
   int parity;
   int sweep_offset;
+  double* epart;            // energy partials [2][n_blocks][Wp] (energy variant only)
+  int n_blocks;
 };
 
 struct EnergyParams {
   const unsigned char* spins;
   const void* rec;
   const SampleDev* samples;
-  const int4* blocks;       // (sample, g, site-block, 0)
-  double* partials;         // [n_blocks][8]
+  const int2* blocks;       // the sweep block table: (sample, first item)
+  double* partials;         // [2][n_blocks][Wp]: even-site and odd-site terms per block
   double* E;                // [n_samples][Wp]
-  int G, Wp, n_samples;
+  int G, Wp, n_samples, n_blocks;
+  uint32_t fdG_m, fdG_s;
 };
 
 struct PTParams {
@@ -103,10 +104,10 @@ struct ConvParams {
 };
 
 // launchers (hsg_kernels*.cu)
-cudaError_t launch_half_sweep(int fmt, bool hb, bool j16, bool fast, const SweepParams& p,
-                              int n_blocks, cudaStream_t st);
-cudaError_t launch_energy(int fmt, bool j16, const EnergyParams& p, int n_blocks,
-                          cudaStream_t st);
+cudaError_t launch_half_sweep(int fmt, bool hb, bool j16, bool fast, bool energy,
+                              const SweepParams& p, int n_blocks, cudaStream_t st);
+cudaError_t launch_energy(int fmt, bool j16, const EnergyParams& p, cudaStream_t st);
+cudaError_t launch_energy_final(const EnergyParams& p, cudaStream_t st);
 cudaError_t launch_pt(const PTParams& p, cudaStream_t st);
 cudaError_t launch_bump(unsigned long long* counters, int sweeps, int pts, cudaStream_t st);
 cudaError_t launch_measure(int fmt, const MeasureParams& p, int lmax, cudaStream_t st);

@@ -90,119 +90,153 @@ __device__ __forceinline__ SiteGeom site_geom(const SampleDev& sd, uint32_t h, i
   return gm;
 }
 
-template <int F, bool HB, bool J16, bool FAST>
+template <int F, bool HB, bool J16, bool FAST, bool EN>
 __global__ void __launch_bounds__(SWEEP_BS) k_half_sweep(const SweepParams p) {
   constexpr int VEC = FmtInfo<F>::VEC, PL = FmtInfo<F>::PLANES, ELEM = FmtInfo<F>::ELEM;
   const int2 blk = p.blocks[blockIdx.x];
   const SampleDev& sd = p.samples[blk.x];
   const uint32_t item = (uint32_t)blk.y + threadIdx.x;
   const uint32_t half_n = (uint32_t)sd.N >> 1;
-  if (item >= half_n * (uint32_t)p.G) return;
-  const uint32_t h = (__umulhi(item, p.fdG_m) + item) >> p.fdG_s;
-  const uint32_t g = item - h * (uint32_t)p.G;
-  const SiteGeom gm = site_geom(sd, h, p.parity);
+  const bool active = item < half_n * (uint32_t)p.G;
+  if (!EN && !active) return;
+  float e[VEC];
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) e[v] = 0.0f;
 
-  const long long site_stride = (long long)p.Wp * ELEM;
-  const unsigned char* base = p.spins + sd.spin_off + (long long)g * 16;
-  const long long ps = sd.plane_stride;
+  if (active) {
+    const uint32_t h = (__umulhi(item, p.fdG_m) + item) >> p.fdG_s;
+    const uint32_t g = item - h * (uint32_t)p.G;
+    const SiteGeom gm = site_geom(sd, h, p.parity);
 
-  float j6[6], h3[3];
-  load_record<J16>(p.rec, sd.rec_off + gm.own, j6, h3);
+    const long long site_stride = (long long)p.Wp * ELEM;
+    const unsigned char* base = p.spins + sd.spin_off + (long long)g * 16;
+    const long long ps = sd.plane_stride;
 
-  // local field h = sum_n J_n s_n + H, summed in the order +x, -x, +y, -y, +z, -z
-  Spins<VEC> hf;
-  {
+    float j6[6], h3[3];
+    load_record<J16>(p.rec, sd.rec_off + gm.own, j6, h3);
+
+    // local field h = sum_n J_n s_n + H, summed in the order +x, -x, +y, -y, +z, -z
+    Spins<VEC> hf;
+    {
+      uint4 c[PL];
+      Spins<VEC> nb;
+      load_chunks_ro<F>(base + gm.nb[0] * site_stride, ps, c);
+      decode<F>(c, nb);
+      const float2 jj = f2(j6[0]);
+#pragma unroll
+      for (int k = 0; k < VEC / 2; ++k) {
+        hf.x[k] = mul2(jj, nb.x[k]);
+        hf.y[k] = mul2(jj, nb.y[k]);
+        hf.z[k] = mul2(jj, nb.z[k]);
+      }
+    }
+#pragma unroll
+    for (int n = 1; n < 6; ++n) {
+      uint4 c[PL];
+      Spins<VEC> nb;
+      load_chunks_ro<F>(base + gm.nb[n] * site_stride, ps, c);
+      decode<F>(c, nb);
+      const float2 jj = f2(j6[n]);
+#pragma unroll
+      for (int k = 0; k < VEC / 2; ++k) {
+        hf.x[k] = add2(hf.x[k], mul2(jj, nb.x[k]));
+        hf.y[k] = add2(hf.y[k], mul2(jj, nb.y[k]));
+        hf.z[k] = add2(hf.z[k], mul2(jj, nb.z[k]));
+      }
+    }
+    {
+      const float2 hx = f2(h3[0]), hy = f2(h3[1]), hz = f2(h3[2]);
+#pragma unroll
+      for (int k = 0; k < VEC / 2; ++k) {
+        hf.x[k] = add2(hf.x[k], hx);
+        hf.y[k] = add2(hf.y[k], hy);
+        hf.z[k] = add2(hf.z[k], hz);
+      }
+    }
+
+    unsigned char* own_p = p.spins + sd.spin_off + (long long)g * 16 + gm.own * site_stride;
     uint4 c[PL];
-    Spins<VEC> nb;
-    load_chunks_ro<F>(base + gm.nb[0] * site_stride, ps, c);
-    decode<F>(c, nb);
-    const float2 jj = f2(j6[0]);
-#pragma unroll
-    for (int k = 0; k < VEC / 2; ++k) {
-      hf.x[k] = mul2(jj, nb.x[k]);
-      hf.y[k] = mul2(jj, nb.y[k]);
-      hf.z[k] = mul2(jj, nb.z[k]);
-    }
-  }
-#pragma unroll
-  for (int n = 1; n < 6; ++n) {
-    uint4 c[PL];
-    Spins<VEC> nb;
-    load_chunks_ro<F>(base + gm.nb[n] * site_stride, ps, c);
-    decode<F>(c, nb);
-    const float2 jj = f2(j6[n]);
-#pragma unroll
-    for (int k = 0; k < VEC / 2; ++k) {
-      hf.x[k] = add2(hf.x[k], mul2(jj, nb.x[k]));
-      hf.y[k] = add2(hf.y[k], mul2(jj, nb.y[k]));
-      hf.z[k] = add2(hf.z[k], mul2(jj, nb.z[k]));
-    }
-  }
-  {
-    const float2 hx = f2(h3[0]), hy = f2(h3[1]), hz = f2(h3[2]);
-#pragma unroll
-    for (int k = 0; k < VEC / 2; ++k) {
-      hf.x[k] = add2(hf.x[k], hx);
-      hf.y[k] = add2(hf.y[k], hy);
-      hf.z[k] = add2(hf.z[k], hz);
-    }
-  }
+    Spins<VEC> s;
+    load_chunks<F>(own_p, ps, c);
+    decode<F>(c, s);
 
-  unsigned char* own_p = p.spins + sd.spin_off + (long long)g * 16 + gm.own * site_stride;
-  uint4 c[PL];
-  Spins<VEC> s;
-  load_chunks<F>(own_p, ps, c);
-  decode<F>(c, s);
-
-  if (HB) {
-    const uint32_t sweep = (uint32_t)(p.counters[0] + (unsigned long long)p.sweep_offset);
-    const uint32_t sys0 = (uint32_t)sd.sys_base + g * VEC;   // even
-    const float* beta = p.beta + (long long)blk.x * p.Wp + g * VEC;
+    if (HB) {
+      const uint32_t sweep = (uint32_t)(p.counters[0] + (unsigned long long)p.sweep_offset);
+      const uint32_t sys0 = (uint32_t)sd.sys_base + g * VEC;   // even
+      const float* beta = p.beta + (long long)blk.x * p.Wp + g * VEC;
 #pragma unroll
-    for (int k = 0; k < VEC / 2; ++k) {
-      const uint4 r = philox4x32_10(make_uint4(gm.site, (sys0 >> 1) + k, sweep, TAG_HB),
-                                    p.seed_lo, p.seed_hi);
-      hb_move<FAST>(s.x[k].x, s.y[k].x, s.z[k].x, hf.x[k].x, hf.y[k].x, hf.z[k].x,
-                    beta[2 * k], u01(r.x), u01(r.y));
-      hb_move<FAST>(s.x[k].y, s.y[k].y, s.z[k].y, hf.x[k].y, hf.y[k].y, hf.z[k].y,
-                    beta[2 * k + 1], u01(r.z), u01(r.w));
+      for (int k = 0; k < VEC / 2; ++k) {
+        const uint4 r = philox4x32_10(make_uint4(gm.site, (sys0 >> 1) + k, sweep, TAG_HB),
+                                      p.seed_lo, p.seed_hi);
+        hb_move<FAST>(s.x[k].x, s.y[k].x, s.z[k].x, hf.x[k].x, hf.y[k].x, hf.z[k].x,
+                      beta[2 * k], u01(r.x), u01(r.y));
+        hb_move<FAST>(s.x[k].y, s.y[k].y, s.z[k].y, hf.x[k].y, hf.y[k].y, hf.z[k].y,
+                      beta[2 * k + 1], u01(r.z), u01(r.w));
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < VEC / 2; ++k) or_move2(s.x[k], s.y[k], s.z[k], hf.x[k], hf.y[k], hf.z[k]);
     }
-  } else {
+    encode<F>(s, c);
+    store_chunks<F>(own_p, ps, c);
+
+    if (EN) {
+      // energy of the new state from the stored values: every bond joins one odd
+      // and one even site, E = - sum_odd s_i.h_i - sum_even H_j.s_j
+      Spins<VEC> st;
+      decode<F>(c, st);
 #pragma unroll
-    for (int k = 0; k < VEC / 2; ++k) or_move2(s.x[k], s.y[k], s.z[k], hf.x[k], hf.y[k], hf.z[k]);
+      for (int k = 0; k < VEC / 2; ++k) {
+        float2 d;
+        if (p.parity == 1) {
+          d = add2(add2(mul2(st.x[k], hf.x[k]), mul2(st.y[k], hf.y[k])), mul2(st.z[k], hf.z[k]));
+        } else {
+          d = add2(add2(mul2(st.x[k], f2(h3[0])), mul2(st.y[k], f2(h3[1]))),
+                   mul2(st.z[k], f2(h3[2])));
+        }
+        e[2 * k] = -d.x;
+        e[2 * k + 1] = -d.y;
+      }
+    }
   }
-  encode<F>(s, c);
-  store_chunks<F>(own_p, ps, c);
+  if (EN) {
+    __shared__ float red[SWEEP_BS][VEC];
+    double* out = p.epart + ((long long)p.parity * p.n_blocks + blockIdx.x) * p.Wp;
+    block_system_sums<VEC, SWEEP_BS>(e, (uint32_t)blk.y, p.G, p.Wp, out, red);
+  }
 }
 
 template <int F>
-static cudaError_t launch_fmt(bool hb, bool j16, bool fast, const SweepParams& p, int nb,
+static cudaError_t launch_fmt(bool hb, bool j16, bool fast, bool en, const SweepParams& p, int nb,
                               cudaStream_t st) {
   dim3 grid(nb), block(SWEEP_BS);
   if (hb) {
     if (j16) {
-      if (fast) k_half_sweep<F, true, true, true><<<grid, block, 0, st>>>(p);
-      else k_half_sweep<F, true, true, false><<<grid, block, 0, st>>>(p);
+      if (fast) k_half_sweep<F, true, true, true, false><<<grid, block, 0, st>>>(p);
+      else k_half_sweep<F, true, true, false, false><<<grid, block, 0, st>>>(p);
     } else {
-      if (fast) k_half_sweep<F, true, false, true><<<grid, block, 0, st>>>(p);
-      else k_half_sweep<F, true, false, false><<<grid, block, 0, st>>>(p);
+      if (fast) k_half_sweep<F, true, false, true, false><<<grid, block, 0, st>>>(p);
+      else k_half_sweep<F, true, false, false, false><<<grid, block, 0, st>>>(p);
     }
+  } else if (en) {
+    if (j16) k_half_sweep<F, false, true, false, true><<<grid, block, 0, st>>>(p);
+    else k_half_sweep<F, false, false, false, true><<<grid, block, 0, st>>>(p);
   } else {
-    if (j16) k_half_sweep<F, false, true, false><<<grid, block, 0, st>>>(p);
-    else k_half_sweep<F, false, false, false><<<grid, block, 0, st>>>(p);
+    if (j16) k_half_sweep<F, false, true, false, false><<<grid, block, 0, st>>>(p);
+    else k_half_sweep<F, false, false, false, false><<<grid, block, 0, st>>>(p);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_half_sweep(int fmt, bool hb, bool j16, bool fast, const SweepParams& p,
-                              int n_blocks, cudaStream_t st) {
+cudaError_t launch_half_sweep(int fmt, bool hb, bool j16, bool fast, bool en,
+                              const SweepParams& p, int n_blocks, cudaStream_t st) {
   if (n_blocks <= 0) return cudaSuccess;
   switch (fmt) {
-    case FMT_F32: return launch_fmt<FMT_F32>(hb, j16, fast, p, n_blocks, st);
-    case FMT_F16: return launch_fmt<FMT_F16>(hb, j16, fast, p, n_blocks, st);
-    case FMT_BF16: return launch_fmt<FMT_BF16>(hb, j16, fast, p, n_blocks, st);
-    case FMT_ANG16: return launch_fmt<FMT_ANG16>(hb, j16, fast, p, n_blocks, st);
-    case FMT_OCT16: return launch_fmt<FMT_OCT16>(hb, j16, fast, p, n_blocks, st);
+    case FMT_F32: return launch_fmt<FMT_F32>(hb, j16, fast, en, p, n_blocks, st);
+    case FMT_F16: return launch_fmt<FMT_F16>(hb, j16, fast, en, p, n_blocks, st);
+    case FMT_BF16: return launch_fmt<FMT_BF16>(hb, j16, fast, en, p, n_blocks, st);
+    case FMT_ANG16: return launch_fmt<FMT_ANG16>(hb, j16, fast, en, p, n_blocks, st);
+    case FMT_OCT16: return launch_fmt<FMT_OCT16>(hb, j16, fast, en, p, n_blocks, st);
   }
   return cudaErrorInvalidValue;
 }

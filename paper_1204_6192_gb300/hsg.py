@@ -77,6 +77,7 @@ def lib() -> ctypes.CDLL:
         "hsg_pt_exchange_energies": (ip, [vp, dp]),
         "hsg_step": (ip, [vp, ip]),
         "hsg_energies": (ip, [vp, dp]),
+        "hsg_last_energies": (ip, [vp, dp]),
         "hsg_measure": (ip, [vp, ctypes.POINTER(Obs)]),
         "hsg_get_spins": (ip, [vp, fp]),
         "hsg_set_spins": (ip, [vp, fp]),
@@ -200,6 +201,11 @@ class Context:
         self._check(lib().hsg_energies(self._ctx, _ptr(E, ctypes.c_double)))
         return E
 
+    def last_energies(self) -> np.ndarray:
+        E = np.zeros((self.n_samples, self.W))
+        self._check(lib().hsg_last_energies(self._ctx, _ptr(E, ctypes.c_double)))
+        return E
+
     def measure(self, q: bool = True):
         ns, R_O, R_T = self.n_samples, self.n_replicas, self.n_temps
         E = np.zeros((ns, R_O, R_T))
@@ -283,6 +289,7 @@ hsg_pt_exchange = Context.pt_exchange
 hsg_pt_exchange_energies = Context.pt_exchange_energies
 hsg_step = Context.step
 hsg_energies = Context.energies
+hsg_last_energies = Context.last_energies
 hsg_measure = Context.measure
 hsg_get_spins = Context.get_spins
 hsg_set_spins = Context.set_spins

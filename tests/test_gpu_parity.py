@@ -93,20 +93,31 @@ def test_one_sweep_fp32_strict(L, op):
     assert d.max() < TOL_FP32, d.max()
 
 
-def oracle_self_chaos(samples, n_rep, seed, schedule, eps=3e-8):
-    """Deviation of the FP64 oracle from itself when its initial state is moved
-    by eps (the FP32 rounding level): the spread any FP32 implementation must
-    show after the same sweeps, because the dynamics amplify small differences."""
+def fp32_storage_reference(samples, n_rep, seed, schedule):
+    """|FP64 oracle - FP64 oracle with binary32 spin storage| after the schedule.
+
+    The dynamics amplify small differences (the FP64 oracle moved by 3e-8
+    deviates by ~1e-3 after 9 sweeps at L = 8), so no FP32 implementation can
+    follow the FP64 trajectory to a fixed max-norm over many sweeps; this is the
+    spread that FP32 storage alone produces, the scale GPU differences are
+    measured against."""
     a = oracle.OracleSim(samples, n_rep, seed)
-    b = oracle.OracleSim(samples, n_rep, seed)
-    rng = np.random.default_rng(123)
-    for o in b.samples:
-        o.s += rng.uniform(-eps, eps, o.s.shape)
-        o.s /= np.linalg.norm(o.s, axis=2, keepdims=True)
+    b = oracle.OracleSim(samples, n_rep, seed, codec="fp32")
     for op, n in schedule:
         getattr(a, op)(n)
         getattr(b, op)(n)
-    return max(np.abs(x - y).max() for x, y in zip(a.spins(), b.spins()))
+    return np.concatenate([np.abs(x - y).ravel() for x, y in zip(a.spins(), b.spins())])
+
+
+# FP32 arithmetic adds a few ulp per update on top of the half-ulp storage
+# rounding; the maximum is one outlier of a chaotic map and gets a wider margin
+CHAOS_FACTOR = {0.5: 10.0, 0.9: 10.0, 0.99: 10.0, 1.0: 30.0}
+
+
+def assert_within_fp32_spread(d, ref):
+    for q, k in CHAOS_FACTOR.items():
+        lim = k * np.quantile(ref, q) + 1e-6
+        assert np.quantile(d, q) <= lim, (q, np.quantile(d, q), lim)
 
 
 def trajectory_check(samples, n_rep, seed, sched):
@@ -118,11 +129,7 @@ def trajectory_check(samples, n_rep, seed, sched):
         getattr(orc, op)(n)
     d = np.concatenate([np.abs(g - o).ravel() for g, o in zip(ctx.get_spins(), orc.spins())])
     ctx.close()
-    chaos = oracle_self_chaos(samples, n_rep, seed, sched)
-    # bulk within 1e-5 after 10 sweeps; the tail bounded by the chaos of the dynamics
-    assert np.median(d) < 2e-6, np.median(d)
-    assert np.quantile(d, 0.99) < TOL_FP32, np.quantile(d, 0.99)
-    assert d.max() < max(TOL_FP32, 50 * chaos), (d.max(), chaos)
+    assert_within_fp32_spread(d, fp32_storage_reference(samples, n_rep, seed, sched))
     return d
 
 
@@ -162,6 +169,20 @@ def test_energies_match_oracle_on_seeded_state():
     ctx.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "oct16"])
+def test_step_energies_equal_recomputed(precision):
+    """The energies the step's PT pass used (summed from the partials of the
+    last OR sweep) equal a fresh FP64 energy evaluation of the same state."""
+    samples = [inputs.small_sample(L, n_temps=4, h_r=0.2, disorder_seed=L) for L in (6, 8)]
+    ctx = hsg.Context(samples, 2, 4, precision=precision, j_fp16=precision != "fp32")
+    for _ in range(3):
+        ctx.step(1)
+        E_step = ctx.last_energies()
+        E_new = ctx.energies()
+        np.testing.assert_allclose(E_step, E_new, rtol=1e-6, atol=1e-6)
+    ctx.close()
+
+
 def test_pt_with_injected_energies_bit_exact():
     rng = np.random.default_rng(2)
     samples = [inputs.small_sample(4, n_temps=8, disorder_seed=k) for k in range(3)]
@@ -181,7 +202,7 @@ def test_pt_with_injected_energies_bit_exact():
 
 def test_step_with_pt_matches_oracle():
     """hsg_step (graph: HB, 5 OR, energies, PT) against the oracle's step: the
-    permutations agree exactly, the spins in bulk (the dynamics are chaotic)."""
+    permutations agree exactly, the spins within the FP32 spread."""
     w = inputs.workload("L8_plain")
     samples = [f32(x) for x in w.samples]
     ctx = hsg.Context(samples, 2, 1)
@@ -190,8 +211,9 @@ def test_step_with_pt_matches_oracle():
         ctx.step(1)
         orc.step(1)
         np.testing.assert_array_equal(ctx.get_perm()[0], orc.samples[0].perm)
-        d = np.abs(ctx.get_spins()[0] - orc.spins()[0])
-        assert np.median(d) < 2e-6 and np.quantile(d, 0.9) < TOL_FP32, (k, np.median(d))
+    d = np.abs(ctx.get_spins()[0] - orc.spins()[0]).ravel()
+    ref = fp32_storage_reference(samples, 2, 1, [("step", 3)])
+    assert_within_fp32_spread(d, ref)
     info = ctx.info()
     assert info.sweep_count == 18 and info.pt_count == 3
     ctx.close()

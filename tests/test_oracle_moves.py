@@ -149,6 +149,13 @@ def test_angle_codecs(orc, codec, bound):
     np.testing.assert_allclose(orc.codec_roundtrip(r, codec), r, atol=1e-12)
 
 
+def test_fp32_storage_matches_numpy(orc):
+    rng = np.random.default_rng(10)
+    v = np.concatenate([unit(rng, 5000), rng.uniform(-1, 1, (100, 3))])
+    np.testing.assert_array_equal(orc.codec_roundtrip(v, "fp32"),
+                                  v.astype(np.float32).astype(np.float64))
+
+
 def test_component_codecs_bound(orc):
     rng = np.random.default_rng(9)
     v = unit(rng, 20000)
