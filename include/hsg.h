@@ -194,6 +194,35 @@ typedef struct {
 } hsg_info;
 hsg_status hsg_get_info(hsg_ctx* ctx, hsg_info* info);
 
+/*
+ * FP64 energies of W systems given as caller-owned device arrays, computed
+ * without allocating any device memory.  The paper has no counterpart; this
+ * entry point exists for callers that must not let a library allocate: code
+ * that runs while a CUDA graph is being captured (cudaMalloc is not allowed
+ * there), programs whose device memory belongs to their own pool allocator,
+ * and loops that cannot afford the device synchronisation cudaMalloc/cudaFree
+ * can cause.
+ *   spins_dev  float[W][L^3][3], (x, y, z) per site (the hsg_get_spins layout)
+ *   J_dev      float[L^3][3] bonds (i, i + e_a); H_dev float[L^3][3] or NULL
+ *   E_dev      double[W] output, E_w = -sum_bonds J s.s - sum_i H.s (Eq. 1)
+ *   stream     cudaStream_t, NULL for the default stream; the call is
+ *              asynchronous on it
+ * Scratch: block partial sums go to one static __device__ array of 524288
+ * doubles (4 MiB) that every GPU loading the library keeps until the process
+ * exits.  Sizes with W * ceil(L^3 / 2048) > 524288 are rejected with
+ * HSG_EINVAL (e.g. L = 128 allows W <= 512).  All calls share the array:
+ * calls that overlap on the GPU (other streams, other host threads) race on
+ * it, so serialise them.  Each call overwrites every partial it reads, so
+ * nothing needs clearing between calls.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Errors: HSG_EINVAL for bad
+ * sizes or NULL pointers, HSG_ECUDA for a failed launch; the text is in
+ * hsg_last_error(NULL).
+ */
+hsg_status hsg_energies_xyz_noalloc(const float* spins_dev, const float* J_dev,
+                                    const float* H_dev, int L, int W, double* E_dev,
+                                    void* stream);
+
 /* Wait for all work of the context; returns any pending device error. */
 hsg_status hsg_sync(hsg_ctx* ctx);
 

@@ -483,6 +483,11 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
 
 }  // namespace
 
+namespace hsg {
+// error text for calls that have no context (reported by hsg_last_error(NULL))
+void set_global_error(const char* msg) { g_create_error = msg ? msg : ""; }
+}  // namespace hsg
+
 extern "C" {
 
 void hsg_default_options(hsg_options* opt) {

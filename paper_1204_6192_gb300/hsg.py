@@ -90,6 +90,7 @@ def lib() -> ctypes.CDLL:
         "hsg_last_error": (ctypes.c_char_p, [vp]),
         "hsg_status_string": (ctypes.c_char_p, [ip]),
         "hsg_destroy": (None, [vp]),
+        "hsg_energies_xyz_noalloc": (ip, [vp, vp, vp, ip, ip, vp, vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
@@ -271,6 +272,16 @@ class Context:
 
     def sync(self):
         self._check(lib().hsg_sync(self._ctx))
+
+
+def hsg_energies_xyz_noalloc(spins_dev: int, J_dev: int, H_dev: int, L: int, W: int, E_dev: int,
+                             stream: int = 0) -> int:
+    """FP64 energies of W systems held in caller-owned device buffers (raw
+    device addresses), with no device allocation (scratch is a static array
+    inside the library).  Returns the C status code; 0 on success."""
+    return lib().hsg_energies_xyz_noalloc(ctypes.c_void_p(spins_dev), ctypes.c_void_p(J_dev),
+                                          ctypes.c_void_p(H_dev or None), L, W,
+                                          ctypes.c_void_p(E_dev), ctypes.c_void_p(stream or None))
 
 
 # C names -----------------------------------------------------------------------
