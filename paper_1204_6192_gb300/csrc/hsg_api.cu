@@ -43,11 +43,14 @@ struct hsg_ctx {
   void* rec = nullptr;
   size_t rec_bytes = 0;
   SampleDev* d_sd = nullptr;
-  int2* d_sweep_blocks = nullptr;
+  int4* d_sweep_blocks = nullptr;     // (sample, chunk group, first half-site)
   int n_sweep_blocks = 0;
-  int2* d_conv_blocks = nullptr;
+  int GPT = 1;                        // chunks per thread in the sweep kernels
+  int4* d_conv_blocks = nullptr;      // (sample, chunk, first site)
   int n_conv_blocks = 0;
   double* d_epart = nullptr;        // energy partials [2][n_sweep_blocks][Wp]
+  double* d_epart2 = nullptr;       // second level [n_samples][e_splits][Wp]
+  int e_splits = 1;
   float* d_beta = nullptr;
   double* d_temps = nullptr;
   double* d_inv_temps = nullptr;
@@ -132,7 +135,7 @@ hsg_status dev_alloc(hsg_ctx* c, T** p, size_t bytes) {
     if (s_ != HSG_OK) return s_;       \
   } while (0)
 
-int fmt_vec(int f) { return (f == FMT_F16 || f == FMT_BF16) ? 8 : 4; }
+int fmt_vec(int) { return 4; }
 int fmt_planes(int f) { return (f == FMT_ANG16 || f == FMT_OCT16) ? 1 : 3; }
 int fmt_elem(int f) { return (f == FMT_F16 || f == FMT_BF16) ? 2 : 4; }
 
@@ -146,8 +149,7 @@ SweepParams sweep_params(hsg_ctx* c, int parity, int sweep_offset) {
   p.counters = c->d_counters;
   p.G = c->G;
   p.Wp = c->Wp;
-  p.fdG_m = c->fdG_m;
-  p.fdG_s = c->fdG_s;
+  p.GPT = c->GPT;
   p.seed_lo = c->seed_lo;
   p.seed_hi = c->seed_hi;
   p.parity = parity;
@@ -164,13 +166,14 @@ EnergyParams energy_params(hsg_ctx* c) {
   p.samples = c->d_sd;
   p.blocks = c->d_sweep_blocks;
   p.partials = c->d_epart;
+  p.partials2 = c->d_epart2;
+  p.splits = c->e_splits;
   p.E = c->d_E;
   p.G = c->G;
   p.Wp = c->Wp;
   p.n_samples = c->ns;
   p.n_blocks = c->n_sweep_blocks;
-  p.fdG_m = c->fdG_m;
-  p.fdG_s = c->fdG_s;
+  p.GPT = c->GPT;
   return p;
 }
 
@@ -337,7 +340,18 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   }
 
   // layout
-  std::vector<int2> sweep_blocks, conv_blocks;
+  std::vector<int4> sweep_blocks, conv_blocks;
+  // chunks per thread: enough threads to fill the GPU (~152 SMs x 2048), the
+  // rest of the chunks walked by each thread so site geometry and couplings
+  // are computed once per site
+  {
+    long long half_sites = 0;
+    for (int s = 0; s < n_samples; ++s) half_sites += (long long)L[s] * L[s] * L[s] / 2;
+    const long long target = 152ll * 2048;
+    long long gpt = half_sites * G / target;
+    c->GPT = (int)std::max(1ll, std::min((long long)G, gpt));
+  }
+  const int n_gg = (G + c->GPT - 1) / c->GPT;
   size_t spin_off = 0, rec_off = 0;
   long long xyz = 0;
   for (int s = 0; s < n_samples; ++s) {
@@ -351,13 +365,12 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
     d.plane_stride = (long long)d.N * Wp * c->ELEM;
     d.rec_off = (long long)rec_off;
     d.sys_base = s * Wp;
-    const long long half_items = (long long)(d.N / 2) * G;
     d.blk0 = (int)sweep_blocks.size();
-    for (long long it = 0; it < half_items; it += SWEEP_BS)
-      sweep_blocks.push_back(make_int2(s, (int)it));
+    for (int gg = 0; gg < n_gg; ++gg)
+      for (int h0 = 0; h0 < d.N / 2; h0 += SWEEP_BS) sweep_blocks.push_back(make_int4(s, gg, h0, 0));
     d.blk1 = (int)sweep_blocks.size();
-    const long long all_items = (long long)d.N * G;
-    for (long long it = 0; it < all_items; it += 256) conv_blocks.push_back(make_int2(s, (int)it));
+    for (int g = 0; g < G; ++g)
+      for (int s0 = 0; s0 < d.N; s0 += 256) conv_blocks.push_back(make_int4(s, g, s0, 0));
     size_t sb = (size_t)c->PL * d.plane_stride;
     spin_off += (sb + 255) / 256 * 256;
     rec_off += (size_t)d.N;
@@ -371,6 +384,11 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   c->spin_bytes = spin_off;
   c->rec_bytes = rec_off * (c->j16 ? 24 : 48);
   c->n_sweep_blocks = (int)sweep_blocks.size();
+  {
+    int max_rows = 1;
+    for (const SampleDev& d : c->sd) max_rows = std::max(max_rows, d.blk1 - d.blk0);
+    c->e_splits = std::min(64, std::max(1, max_rows / 256));
+  }
   c->n_conv_blocks = (int)conv_blocks.size();
 
   // records: six bonds and the field of every storage site
@@ -422,9 +440,10 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   HSG_ALLOC(c->spins, c->spin_bytes);
   HSG_ALLOC(c->rec, c->rec_bytes);
   HSG_ALLOC(c->d_sd, sizeof(SampleDev) * n_samples);
-  HSG_ALLOC(c->d_sweep_blocks, sizeof(int2) * sweep_blocks.size());
-  HSG_ALLOC(c->d_conv_blocks, sizeof(int2) * conv_blocks.size());
+  HSG_ALLOC(c->d_sweep_blocks, sizeof(int4) * sweep_blocks.size());
+  HSG_ALLOC(c->d_conv_blocks, sizeof(int4) * conv_blocks.size());
   HSG_ALLOC(c->d_epart, sizeof(double) * 2 * sweep_blocks.size() * Wp);
+  HSG_ALLOC(c->d_epart2, sizeof(double) * n_samples * c->e_splits * Wp);
   HSG_ALLOC(c->d_beta, sizeof(float) * n_samples * Wp);
   HSG_ALLOC(c->d_temps, sizeof(double) * n_samples * n_temps);
   HSG_ALLOC(c->d_inv_temps, sizeof(double) * n_samples * n_temps);
@@ -454,8 +473,8 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   }
   HSG_UP(c->rec, c->j16 ? (const void*)rech.data() : (const void*)recf.data(), c->rec_bytes);
   HSG_UP(c->d_sd, c->sd.data(), sizeof(SampleDev) * n_samples);
-  HSG_UP(c->d_sweep_blocks, sweep_blocks.data(), sizeof(int2) * sweep_blocks.size());
-  HSG_UP(c->d_conv_blocks, conv_blocks.data(), sizeof(int2) * conv_blocks.size());
+  HSG_UP(c->d_sweep_blocks, sweep_blocks.data(), sizeof(int4) * sweep_blocks.size());
+  HSG_UP(c->d_conv_blocks, conv_blocks.data(), sizeof(int4) * conv_blocks.size());
   HSG_UP(c->d_temps, temps, sizeof(double) * n_samples * n_temps);
   HSG_UP(c->d_inv_temps, inv.data(), sizeof(double) * inv.size());
   HSG_UP(c->d_perm, perm.data(), sizeof(int) * perm.size());

@@ -16,145 +16,158 @@ namespace hsg {
 //   E = - sum_{odd i} s_i . h_i  - sum_{even j} H_j . s_j
 // with h_i the full local field (bonds + field) of the odd site i.
 // ---------------------------------------------------------------------------
-template <bool J16>
-__device__ __forceinline__ void load_rec(const void* rec, long long idx, float* j6, float* h3) {
-  if (J16) {
-    const uint2* r = reinterpret_cast<const uint2*>(rec) + idx * 3;
-    const uint2 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2);
-    float2 t;
-    t = h2f(a.x); j6[0] = t.x; j6[1] = t.y;
-    t = h2f(a.y); j6[2] = t.x; j6[3] = t.y;
-    t = h2f(b.x); j6[4] = t.x; j6[5] = t.y;
-    t = h2f(b.y); h3[0] = t.x; h3[1] = t.y;
-    t = h2f(c.x); h3[2] = t.x;
-  } else {
-    const float4* r = reinterpret_cast<const float4*>(rec) + idx * 3;
-    const float4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2);
-    j6[0] = a.x; j6[1] = a.y; j6[2] = a.z; j6[3] = a.w;
-    j6[4] = b.x; j6[5] = b.y; h3[0] = b.z; h3[1] = b.w;
-    h3[2] = c.x;
-  }
-}
-
-template <int F>
-__device__ __forceinline__ void load_site(const unsigned char* p, long long ps,
-                                          Spins<FmtInfo<F>::VEC>& s) {
-  uint4 c[FmtInfo<F>::PLANES];
-#pragma unroll
-  for (int pl = 0; pl < FmtInfo<F>::PLANES; ++pl)
-    c[pl] = __ldg(reinterpret_cast<const uint4*>(p + pl * ps));
-  decode<F>(c, s);
-}
-
 template <int F, bool J16>
 __global__ void __launch_bounds__(RED_BS) k_energy(const EnergyParams p) {
-  constexpr int VEC = FmtInfo<F>::VEC, ELEM = FmtInfo<F>::ELEM;
-  const int2 blk = p.blocks[blockIdx.x];
+  constexpr int VEC = FmtInfo<F>::VEC, PL = FmtInfo<F>::PLANES;
+  using Chunk = typename FmtInfo<F>::Chunk;
+  extern __shared__ float esum[];                 // [2][RED_BS / 32][GPT * VEC]
+  const int4 blk = p.blocks[blockIdx.x];
   const SampleDev& sd = p.samples[blk.x];
-  const uint32_t item = (uint32_t)blk.y + threadIdx.x;
+  const uint32_t h = (uint32_t)blk.z + threadIdx.x;
   const uint32_t half_n = (uint32_t)sd.N >> 1;
-  float eo[VEC], ee[VEC];
+  const bool active = h < half_n;
+  const int g0 = blk.y * p.GPT;
+  const int g1 = min(p.G, g0 + p.GPT);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int stride = p.GPT * VEC;
+  float* esum_even = esum;
+  float* esum_odd = esum + (RED_BS / 32) * stride;
+
+  SiteGeom gm;                                   // the odd site with half-index h
+  float j6[6], h3[3], je[6], he[3];
+  long long nb_off[6], odd_off = 0, even_off = 0;
+  const unsigned char* base = p.spins + sd.spin_off;
+  const long long ps = sd.plane_stride;
+  const long long gstride = (long long)sd.N * FmtInfo<F>::CHUNK;
+  if (active) {
+    gm = site_geom(sd, h, 1);
+    load_record<J16>(p.rec, sd.rec_off + gm.own, j6, h3);
+    load_record<J16>(p.rec, sd.rec_off + h, je, he);   // even site with the same half-index
 #pragma unroll
-  for (int v = 0; v < VEC; ++v) { eo[v] = 0.0f; ee[v] = 0.0f; }
-  if (item < half_n * (uint32_t)p.G) {
-    const uint32_t h = (__umulhi(item, p.fdG_m) + item) >> p.fdG_s;
-    const uint32_t g = item - h * (uint32_t)p.G;
-    const uint32_t L = sd.L, Lh = sd.Lh;
-    const long long site_stride = (long long)p.Wp * ELEM;
-    const unsigned char* base = p.spins + sd.spin_off + (long long)g * 16;
-    const long long ps = sd.plane_stride;
-    // odd site with half-index h and its even neighbours
-    const uint32_t r = (__umulhi(h, sd.fdLh_m) + h) >> sd.fdLh_s;
-    const uint32_t hx = h - r * Lh;
-    const uint32_t z = (__umulhi(r, sd.fdL_m) + r) >> sd.fdL_s;
-    const uint32_t y = r - z * L;
-    const uint32_t x = 2u * hx + ((1u + y + z) & 1u);
-    const uint32_t xp = (x + 1 == L) ? 0u : x + 1, xm = (x == 0) ? L - 1 : x - 1;
-    const uint32_t yp = (y + 1 == L) ? 0u : y + 1, ym = (y == 0) ? L - 1 : y - 1;
-    const uint32_t zp = (z + 1 == L) ? 0u : z + 1, zm = (z == 0) ? L - 1 : z - 1;
-    const uint32_t xh = x >> 1;
-    uint32_t nb[6];
-    nb[0] = (xp >> 1) + r * Lh;
-    nb[1] = (xm >> 1) + r * Lh;
-    nb[2] = xh + (yp + L * z) * Lh;
-    nb[3] = xh + (ym + L * z) * Lh;
-    nb[4] = xh + (y + L * zp) * Lh;
-    nb[5] = xh + (y + L * zm) * Lh;
-    const uint32_t own = half_n + h;
-    float j6[6], h3[3];
-    load_rec<J16>(p.rec, sd.rec_off + own, j6, h3);
-    Spins<VEC> hf, t;
-    load_site<F>(base + nb[0] * site_stride, ps, t);
+    for (int n = 0; n < 6; ++n) nb_off[n] = chunk_offset<F>(sd, g0, gm.nb[n]);
+    odd_off = chunk_offset<F>(sd, g0, gm.own);
+    even_off = chunk_offset<F>(sd, g0, h);
+  }
+  for (int g = g0; g < g1; ++g) {
+    float eo[VEC], ee[VEC];
 #pragma unroll
-    for (int q = 0; q < VEC / 2; ++q) {
-      hf.x[q] = mul2(f2(j6[0]), t.x[q]);
-      hf.y[q] = mul2(f2(j6[0]), t.y[q]);
-      hf.z[q] = mul2(f2(j6[0]), t.z[q]);
-    }
+    for (int v = 0; v < VEC; ++v) { eo[v] = 0.0f; ee[v] = 0.0f; }
+    if (active) {
+      const long long dg = (long long)(g - g0) * gstride;
+      Chunk nc[6][PL], co[PL], ce[PL];
 #pragma unroll
-    for (int n = 1; n < 6; ++n) {
-      load_site<F>(base + nb[n] * site_stride, ps, t);
+      for (int n = 0; n < 6; ++n) load_chunks<F, true>(base + nb_off[n] + dg, ps, nc[n]);
+      load_chunks<F, true>(base + odd_off + dg, ps, co);
+      load_chunks<F, true>(base + even_off + dg, ps, ce);
+      Spins<VEC> hf, t;
+      decode<F>(nc[0], t);
 #pragma unroll
       for (int q = 0; q < VEC / 2; ++q) {
-        hf.x[q] = add2(hf.x[q], mul2(f2(j6[n]), t.x[q]));
-        hf.y[q] = add2(hf.y[q], mul2(f2(j6[n]), t.y[q]));
-        hf.z[q] = add2(hf.z[q], mul2(f2(j6[n]), t.z[q]));
+        hf.x[q] = mul2(f2(j6[0]), t.x[q]);
+        hf.y[q] = mul2(f2(j6[0]), t.y[q]);
+        hf.z[q] = mul2(f2(j6[0]), t.z[q]);
+      }
+#pragma unroll
+      for (int n = 1; n < 6; ++n) {
+        decode<F>(nc[n], t);
+#pragma unroll
+        for (int q = 0; q < VEC / 2; ++q) {
+          hf.x[q] = add2(hf.x[q], mul2(f2(j6[n]), t.x[q]));
+          hf.y[q] = add2(hf.y[q], mul2(f2(j6[n]), t.y[q]));
+          hf.z[q] = add2(hf.z[q], mul2(f2(j6[n]), t.z[q]));
+        }
+      }
+      Spins<VEC> so, se;
+      decode<F>(co, so);
+      decode<F>(ce, se);
+#pragma unroll
+      for (int q = 0; q < VEC / 2; ++q) {
+        const float2 hx2 = add2(hf.x[q], f2(h3[0]));
+        const float2 hy2 = add2(hf.y[q], f2(h3[1]));
+        const float2 hz2 = add2(hf.z[q], f2(h3[2]));
+        const float2 o = add2(add2(mul2(so.x[q], hx2), mul2(so.y[q], hy2)), mul2(so.z[q], hz2));
+        const float2 e = add2(add2(mul2(se.x[q], f2(he[0])), mul2(se.y[q], f2(he[1]))),
+                              mul2(se.z[q], f2(he[2])));
+        eo[2 * q] = -o.x;
+        eo[2 * q + 1] = -o.y;
+        ee[2 * q] = -e.x;
+        ee[2 * q + 1] = -e.y;
       }
     }
-    Spins<VEC> so, se;
-    load_site<F>(base + own * site_stride, ps, so);
-    load_site<F>(base + h * site_stride, ps, se);       // even site with the same half-index
-    float je[6], he[3];
-    load_rec<J16>(p.rec, sd.rec_off + h, je, he);
 #pragma unroll
-    for (int q = 0; q < VEC / 2; ++q) {
-      const float2 hx2 = add2(hf.x[q], f2(h3[0]));
-      const float2 hy2 = add2(hf.y[q], f2(h3[1]));
-      const float2 hz2 = add2(hf.z[q], f2(h3[2]));
-      const float2 o = add2(add2(mul2(so.x[q], hx2), mul2(so.y[q], hy2)), mul2(so.z[q], hz2));
-      const float2 e = add2(add2(mul2(se.x[q], f2(he[0])), mul2(se.y[q], f2(he[1]))),
-                            mul2(se.z[q], f2(he[2])));
-      eo[2 * q] = -o.x;
-      eo[2 * q + 1] = -o.y;
-      ee[2 * q] = -e.x;
-      ee[2 * q + 1] = -e.y;
+    for (int v = 0; v < VEC; ++v) {
+      const float to = warp_sum(eo[v]);
+      const float te = warp_sum(ee[v]);
+      if (lane == 0) {
+        esum_odd[warp * stride + (g - g0) * VEC + v] = to;
+        esum_even[warp * stride + (g - g0) * VEC + v] = te;
+      }
     }
   }
-  __shared__ float red[RED_BS][VEC];
-  block_system_sums<VEC, RED_BS>(ee, (uint32_t)blk.y, p.G, p.Wp,
-                                 p.partials + (long long)blockIdx.x * p.Wp, red);
-  block_system_sums<VEC, RED_BS>(eo, (uint32_t)blk.y, p.G, p.Wp,
-                                 p.partials + ((long long)p.n_blocks + blockIdx.x) * p.Wp, red);
+  __syncthreads();
+  for (int j = threadIdx.x; j < p.Wp; j += RED_BS) {
+    double ae = 0.0, ao = 0.0;
+    const int jj = j - g0 * VEC;
+    if (jj >= 0 && jj < (g1 - g0) * VEC) {
+      for (int w = 0; w < RED_BS / 32; ++w) {
+        ae += (double)esum_even[w * stride + jj];
+        ao += (double)esum_odd[w * stride + jj];
+      }
+    }
+    p.partials[(long long)blockIdx.x * p.Wp + j] = ae;
+    p.partials[((long long)p.n_blocks + blockIdx.x) * p.Wp + j] = ao;
+  }
 }
 
 // E[s][w] = sum over the sample's blocks of the even-site and odd-site partials,
-// one block per system, fixed order.
-__global__ void __launch_bounds__(256) k_energy_final(const EnergyParams p) {
-  const int s = blockIdx.x / p.Wp, w = blockIdx.x - (blockIdx.x / p.Wp) * p.Wp;
+// in two fixed-order levels: split k of the sample's rows is added by a block
+// of 32 systems x 8 row lanes (coalesced rows of Wp doubles), then the splits.
+__global__ void __launch_bounds__(256) k_energy_final1(const EnergyParams p) {
+  const int s = blockIdx.z, split = blockIdx.x;
+  const int w = blockIdx.y * 32 + threadIdx.x;
   const SampleDev& sd = p.samples[s];
+  const int nrows = sd.blk1 - sd.blk0;
+  const int per = (nrows + p.splits - 1) / p.splits;
+  const int r0 = sd.blk0 + split * per;
+  const int r1 = min(r0 + per, sd.blk1);
   double acc = 0.0;
-  for (int b = sd.blk0 + threadIdx.x; b < sd.blk1; b += blockDim.x) {
-    acc += p.partials[(long long)b * p.Wp + w];
-    acc += p.partials[((long long)p.n_blocks + b) * p.Wp + w];
+  if (w < p.Wp) {
+    for (int r = r0 + (int)threadIdx.y; r < r1; r += 8) {
+      acc += p.partials[(long long)r * p.Wp + w];
+      acc += p.partials[((long long)p.n_blocks + r) * p.Wp + w];
+    }
   }
-  __shared__ double red[256];
-  red[threadIdx.x] = acc;
+  __shared__ double red[8][32];
+  red[threadIdx.y][threadIdx.x] = acc;
   __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
+  if (threadIdx.y == 0 && w < p.Wp) {
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += red[k][threadIdx.x];
+    p.partials2[((long long)s * p.splits + split) * p.Wp + w] = t;
   }
-  if (threadIdx.x == 0) p.E[(long long)s * p.Wp + w] = red[0];
+}
+
+__global__ void k_energy_final2(const EnergyParams p) {
+  const int s = blockIdx.x;
+  for (int w = threadIdx.x; w < p.Wp; w += blockDim.x) {
+    double e = 0.0;
+    for (int k = 0; k < p.splits; ++k) e += p.partials2[((long long)s * p.splits + k) * p.Wp + w];
+    p.E[(long long)s * p.Wp + w] = e;
+  }
 }
 
 cudaError_t launch_energy_final(const EnergyParams& p, cudaStream_t st) {
-  k_energy_final<<<p.n_samples * p.Wp, 256, 0, st>>>(p);
+  k_energy_final1<<<dim3(p.splits, (p.Wp + 31) / 32, p.n_samples), dim3(32, 8), 0, st>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_energy_final2<<<p.n_samples, 128, 0, st>>>(p);
   return cudaGetLastError();
 }
 
 template <int F, bool J16>
 static cudaError_t energy_fmt(const EnergyParams& p, cudaStream_t st) {
-  k_energy<F, J16><<<p.n_blocks, RED_BS, 0, st>>>(p);
+  const size_t smem = sizeof(float) * 2 * (RED_BS / 32) * p.GPT * FmtInfo<F>::VEC;
+  k_energy<F, J16><<<p.n_blocks, RED_BS, smem, st>>>(p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_energy_final(p, st);
@@ -239,7 +252,6 @@ cudaError_t launch_bump(unsigned long long* counters, int sweeps, int pts, cudaS
 // ---------------------------------------------------------------------------
 template <int F>
 __global__ void __launch_bounds__(MEAS_BS) k_measure_planes(const MeasureParams p) {
-  constexpr int ELEM = FmtInfo<F>::ELEM;
   const int s = blockIdx.y, z = blockIdx.x;
   const SampleDev& sd = p.samples[s];
   const int L = sd.L;
@@ -266,7 +278,6 @@ __global__ void __launch_bounds__(MEAS_BS) k_measure_planes(const MeasureParams 
     const int* perm = p.perm + (long long)s * p.R_O * R_T;
     const int wA = perm[t], wB = R_T + perm[R_T + t];
     const uint32_t half_n = (uint32_t)sd.N >> 1;
-    const long long site_stride = (long long)p.Wp * ELEM;
     const unsigned char* base = p.spins + sd.spin_off;
     for (int y = yl; y < L; y += YL) {
       float R0[9], RX[18];
@@ -278,10 +289,11 @@ __global__ void __launch_bounds__(MEAS_BS) k_measure_planes(const MeasureParams 
       for (int x = 0; x < L; ++x) {
         const uint32_t site = row + (uint32_t)x;
         const uint32_t ss = (((uint32_t)(x + y + z)) & 1u) * half_n + (site >> 1);
-        const unsigned char* pl = base + ss * site_stride;
         float a[3], b[3];
-        decode_one<F>(pl, sd.plane_stride, wA, a[0], a[1], a[2]);
-        decode_one<F>(pl, sd.plane_stride, wB, b[0], b[1], b[2]);
+        decode_one<F>(base + chunk_offset<F>(sd, wA >> 2, ss), sd.plane_stride, wA & 3,
+                      a[0], a[1], a[2]);
+        decode_one<F>(base + chunk_offset<F>(sd, wB >> 2, ss), sd.plane_stride, wB & 3,
+                      b[0], b[1], b[2]);
         const float cx = tw[0][x], sx = tw[1][x];
 #pragma unroll
         for (int mu = 0; mu < 3; ++mu)
@@ -385,16 +397,16 @@ struct ConvItem {
   bool ok;
 };
 
+// Block (sample, chunk g, first site): one thread per site of chunk g.
 __device__ __forceinline__ ConvItem conv_item(const ConvParams& p) {
   ConvItem it;
-  const int2 blk = p.blocks[blockIdx.x];
+  const int4 blk = p.blocks[blockIdx.x];
   it.sd = &p.samples[blk.x];
-  const uint32_t item = (uint32_t)blk.y + threadIdx.x;
+  it.g = (uint32_t)blk.y;
+  it.site = (uint32_t)blk.z + threadIdx.x;
   const uint32_t N = (uint32_t)it.sd->N;
-  it.ok = item < N * (uint32_t)p.G;
+  it.ok = it.site < N;
   if (!it.ok) return it;
-  it.site = (__umulhi(item, p.fdG_m) + item) >> p.fdG_s;
-  it.g = item - it.site * (uint32_t)p.G;
   const uint32_t L = it.sd->L;
   const uint32_t r = (__umulhi(it.site, it.sd->fdL_m) + it.site) >> it.sd->fdL_s;
   const uint32_t x = it.site - r * L;
@@ -406,7 +418,7 @@ __device__ __forceinline__ ConvItem conv_item(const ConvParams& p) {
 
 template <int F>
 __global__ void k_init(const ConvParams p) {
-  constexpr int VEC = FmtInfo<F>::VEC, PL = FmtInfo<F>::PLANES, ELEM = FmtInfo<F>::ELEM;
+  constexpr int VEC = FmtInfo<F>::VEC, PL = FmtInfo<F>::PLANES;
   const ConvItem it = conv_item(p);
   if (!it.ok) return;
   Spins<VEC> s;
@@ -432,27 +444,21 @@ __global__ void k_init(const ConvParams p) {
     s.y[k] = make_float2((float)v[0][1], (float)v[1][1]);
     s.z[k] = make_float2((float)v[0][2], (float)v[1][2]);
   }
-  uint4 c[PL];
+  typename FmtInfo<F>::Chunk c[PL];
   encode<F>(s, c);
-  unsigned char* o = p.spins + it.sd->spin_off + (long long)it.g * 16 +
-                     (long long)it.ss * p.Wp * ELEM;
-#pragma unroll
-  for (int pl = 0; pl < PL; ++pl)
-    *reinterpret_cast<uint4*>(o + pl * it.sd->plane_stride) = c[pl];
+  unsigned char* o = p.spins + it.sd->spin_off + chunk_offset<F>(*it.sd, it.g, it.ss);
+  store_chunks<F>(o, it.sd->plane_stride, c);
 }
 
 template <int F>
 __global__ void k_get(const ConvParams p) {
-  constexpr int VEC = FmtInfo<F>::VEC, PL = FmtInfo<F>::PLANES, ELEM = FmtInfo<F>::ELEM;
+  constexpr int VEC = FmtInfo<F>::VEC, PL = FmtInfo<F>::PLANES;
   const ConvItem it = conv_item(p);
   if (!it.ok) return;
   const int sidx = p.blocks[blockIdx.x].x;
-  const unsigned char* o = p.spins + it.sd->spin_off + (long long)it.g * 16 +
-                           (long long)it.ss * p.Wp * ELEM;
-  uint4 c[PL];
-#pragma unroll
-  for (int pl = 0; pl < PL; ++pl)
-    c[pl] = *reinterpret_cast<const uint4*>(o + pl * it.sd->plane_stride);
+  const unsigned char* o = p.spins + it.sd->spin_off + chunk_offset<F>(*it.sd, it.g, it.ss);
+  typename FmtInfo<F>::Chunk c[PL];
+  load_chunks<F, false>(o, it.sd->plane_stride, c);
   Spins<VEC> s;
   decode<F>(c, s);
   float* out = p.xyz + p.xyz_off[sidx];
@@ -474,7 +480,7 @@ __global__ void k_get(const ConvParams p) {
 
 template <int F>
 __global__ void k_set(const ConvParams p) {
-  constexpr int VEC = FmtInfo<F>::VEC, PL = FmtInfo<F>::PLANES, ELEM = FmtInfo<F>::ELEM;
+  constexpr int VEC = FmtInfo<F>::VEC, PL = FmtInfo<F>::PLANES;
   const ConvItem it = conv_item(p);
   if (!it.ok) return;
   const int sidx = p.blocks[blockIdx.x].x;
@@ -502,13 +508,10 @@ __global__ void k_set(const ConvParams p) {
     s.y[k] = make_float2(v[0][1], v[1][1]);
     s.z[k] = make_float2(v[0][2], v[1][2]);
   }
-  uint4 c[PL];
+  typename FmtInfo<F>::Chunk c[PL];
   encode<F>(s, c);
-  unsigned char* o = p.spins + it.sd->spin_off + (long long)it.g * 16 +
-                     (long long)it.ss * p.Wp * ELEM;
-#pragma unroll
-  for (int pl = 0; pl < PL; ++pl)
-    *reinterpret_cast<uint4*>(o + pl * it.sd->plane_stride) = c[pl];
+  unsigned char* o = p.spins + it.sd->spin_off + chunk_offset<F>(*it.sd, it.g, it.ss);
+  store_chunks<F>(o, it.sd->plane_stride, c);
 }
 
 #define HSG_CONV_SWITCH(KERNEL)                                                          \

@@ -24,11 +24,11 @@ namespace hsg {
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    // one 32x32 -> 64-bit multiply per half (high and low words together)
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1,
+                   (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
     k0 += 0x9E3779B9u;
     k1 += 0xBB67AE85u;
   }
@@ -49,31 +49,32 @@ __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
-  return __fadd2_rn(a, make_float2(-b.x, -b.y));
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;"
+      : "=l"(r)
+      : "l"(*reinterpret_cast<unsigned long long*>(&a)),
+        "l"(*reinterpret_cast<unsigned long long*>(&b)));
+  return *reinterpret_cast<float2*>(&r);
 }
 
 // ----------------------------------------------------------------------------
-// Storage formats.  A chunk is 16 bytes of one "plane" holding VEC systems of
-// one site; component formats store 3 planes (x, y, z), packed formats 1.
+// Storage formats.  A chunk holds VEC = 4 systems of one site in one "plane":
+// 16 bytes (uint4) for FP32 components and for the packed 32-bit formats,
+// 8 bytes (uint2) for FP16/BF16 components.  Component formats store three
+// planes (x, y, z), packed formats one.
 // ----------------------------------------------------------------------------
 template <int F> struct FmtInfo;
-template <> struct FmtInfo<FMT_F32>   { static constexpr int VEC = 4, PLANES = 3, ELEM = 4; };
-template <> struct FmtInfo<FMT_F16>   { static constexpr int VEC = 8, PLANES = 3, ELEM = 2; };
-template <> struct FmtInfo<FMT_BF16>  { static constexpr int VEC = 8, PLANES = 3, ELEM = 2; };
-template <> struct FmtInfo<FMT_ANG16> { static constexpr int VEC = 4, PLANES = 1, ELEM = 4; };
-template <> struct FmtInfo<FMT_OCT16> { static constexpr int VEC = 4, PLANES = 1, ELEM = 4; };
+template <> struct FmtInfo<FMT_F32>   { static constexpr int VEC = 4, PLANES = 3, ELEM = 4, CHUNK = 16; using Chunk = uint4; };
+template <> struct FmtInfo<FMT_F16>   { static constexpr int VEC = 4, PLANES = 3, ELEM = 2, CHUNK = 8;  using Chunk = uint2; };
+template <> struct FmtInfo<FMT_BF16>  { static constexpr int VEC = 4, PLANES = 3, ELEM = 2, CHUNK = 8;  using Chunk = uint2; };
+template <> struct FmtInfo<FMT_ANG16> { static constexpr int VEC = 4, PLANES = 1, ELEM = 4, CHUNK = 16; using Chunk = uint4; };
+template <> struct FmtInfo<FMT_OCT16> { static constexpr int VEC = 4, PLANES = 1, ELEM = 4, CHUNK = 16; using Chunk = uint4; };
 
 // VEC systems of one site as FP32 pairs.
 template <int VEC> struct Spins {
   float2 x[VEC / 2], y[VEC / 2], z[VEC / 2];
 };
 
-__device__ __forceinline__ float2 as_f2_lo(uint4 v) {
-  return make_float2(__uint_as_float(v.x), __uint_as_float(v.y));
-}
-__device__ __forceinline__ float2 as_f2_hi(uint4 v) {
-  return make_float2(__uint_as_float(v.z), __uint_as_float(v.w));
-}
 __device__ __forceinline__ float2 h2f(uint32_t w) {
   __half2 h = *reinterpret_cast<__half2*>(&w);
   return __half22float2(h);
@@ -89,6 +90,9 @@ __device__ __forceinline__ float2 b2f(uint32_t w) {
 __device__ __forceinline__ uint32_t f2b(float2 v) {
   __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
   return *reinterpret_cast<uint32_t*>(&h);
+}
+__device__ __forceinline__ float2 u2f2(uint32_t a, uint32_t b) {
+  return make_float2(__uint_as_float(a), __uint_as_float(b));
 }
 
 // --- angle pair: theta on 65536 levels of [0, pi], phi on a 2^16 ring -----
@@ -144,27 +148,23 @@ __device__ __forceinline__ uint32_t oct16_encode(float x, float y, float z) {
   return ((uint32_t)qx & 0xffffu) | (((uint32_t)qy & 0xffffu) << 16);
 }
 
-// Decode the PLANES chunks of one site into VEC FP32 spins.
+// Decode the PLANES chunks of one site into VEC = 4 FP32 spins.
 template <int F>
-__device__ __forceinline__ void decode(const uint4* c, Spins<FmtInfo<F>::VEC>& s) {
+__device__ __forceinline__ void decode(const typename FmtInfo<F>::Chunk* c, Spins<4>& s) {
   if constexpr (F == FMT_F32) {
-    s.x[0] = as_f2_lo(c[0]); s.x[1] = as_f2_hi(c[0]);
-    s.y[0] = as_f2_lo(c[1]); s.y[1] = as_f2_hi(c[1]);
-    s.z[0] = as_f2_lo(c[2]); s.z[1] = as_f2_hi(c[2]);
-  } else if constexpr (F == FMT_F16 || F == FMT_BF16) {
-    const uint32_t* px = reinterpret_cast<const uint32_t*>(&c[0]);
-    const uint32_t* py = reinterpret_cast<const uint32_t*>(&c[1]);
-    const uint32_t* pz = reinterpret_cast<const uint32_t*>(&c[2]);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if constexpr (F == FMT_F16) {
-        s.x[k] = h2f(px[k]); s.y[k] = h2f(py[k]); s.z[k] = h2f(pz[k]);
-      } else {
-        s.x[k] = b2f(px[k]); s.y[k] = b2f(py[k]); s.z[k] = b2f(pz[k]);
-      }
-    }
+    s.x[0] = u2f2(c[0].x, c[0].y); s.x[1] = u2f2(c[0].z, c[0].w);
+    s.y[0] = u2f2(c[1].x, c[1].y); s.y[1] = u2f2(c[1].z, c[1].w);
+    s.z[0] = u2f2(c[2].x, c[2].y); s.z[1] = u2f2(c[2].z, c[2].w);
+  } else if constexpr (F == FMT_F16) {
+    s.x[0] = h2f(c[0].x); s.x[1] = h2f(c[0].y);
+    s.y[0] = h2f(c[1].x); s.y[1] = h2f(c[1].y);
+    s.z[0] = h2f(c[2].x); s.z[1] = h2f(c[2].y);
+  } else if constexpr (F == FMT_BF16) {
+    s.x[0] = b2f(c[0].x); s.x[1] = b2f(c[0].y);
+    s.y[0] = b2f(c[1].x); s.y[1] = b2f(c[1].y);
+    s.z[0] = b2f(c[2].x); s.z[1] = b2f(c[2].y);
   } else {
-    const uint32_t* p = reinterpret_cast<const uint32_t*>(&c[0]);
+    const uint32_t p[4] = {c[0].x, c[0].y, c[0].z, c[0].w};
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       float x0, y0, z0, x1, y1, z1;
@@ -183,7 +183,7 @@ __device__ __forceinline__ void decode(const uint4* c, Spins<FmtInfo<F>::VEC>& s
 }
 
 template <int F>
-__device__ __forceinline__ void encode(const Spins<FmtInfo<F>::VEC>& s, uint4* c) {
+__device__ __forceinline__ void encode(const Spins<4>& s, typename FmtInfo<F>::Chunk* c) {
   if constexpr (F == FMT_F32) {
     c[0] = make_uint4(__float_as_uint(s.x[0].x), __float_as_uint(s.x[0].y),
                       __float_as_uint(s.x[1].x), __float_as_uint(s.x[1].y));
@@ -192,13 +192,13 @@ __device__ __forceinline__ void encode(const Spins<FmtInfo<F>::VEC>& s, uint4* c
     c[2] = make_uint4(__float_as_uint(s.z[0].x), __float_as_uint(s.z[0].y),
                       __float_as_uint(s.z[1].x), __float_as_uint(s.z[1].y));
   } else if constexpr (F == FMT_F16) {
-    c[0] = make_uint4(f2h(s.x[0]), f2h(s.x[1]), f2h(s.x[2]), f2h(s.x[3]));
-    c[1] = make_uint4(f2h(s.y[0]), f2h(s.y[1]), f2h(s.y[2]), f2h(s.y[3]));
-    c[2] = make_uint4(f2h(s.z[0]), f2h(s.z[1]), f2h(s.z[2]), f2h(s.z[3]));
+    c[0] = make_uint2(f2h(s.x[0]), f2h(s.x[1]));
+    c[1] = make_uint2(f2h(s.y[0]), f2h(s.y[1]));
+    c[2] = make_uint2(f2h(s.z[0]), f2h(s.z[1]));
   } else if constexpr (F == FMT_BF16) {
-    c[0] = make_uint4(f2b(s.x[0]), f2b(s.x[1]), f2b(s.x[2]), f2b(s.x[3]));
-    c[1] = make_uint4(f2b(s.y[0]), f2b(s.y[1]), f2b(s.y[2]), f2b(s.y[3]));
-    c[2] = make_uint4(f2b(s.z[0]), f2b(s.z[1]), f2b(s.z[2]), f2b(s.z[3]));
+    c[0] = make_uint2(f2b(s.x[0]), f2b(s.x[1]));
+    c[1] = make_uint2(f2b(s.y[0]), f2b(s.y[1]));
+    c[2] = make_uint2(f2b(s.z[0]), f2b(s.z[1]));
   } else {
     uint32_t w[4];
 #pragma unroll
@@ -213,6 +213,28 @@ __device__ __forceinline__ void encode(const Spins<FmtInfo<F>::VEC>& s, uint4* c
     }
     c[0] = make_uint4(w[0], w[1], w[2], w[3]);
   }
+}
+
+// Chunk loads and stores of one site (PLANES chunks, plane_stride bytes apart).
+// ro: through the read-only path (data not written during the launch).
+template <int F, bool RO>
+__device__ __forceinline__ void load_chunks(const unsigned char* p, long long plane_stride,
+                                            typename FmtInfo<F>::Chunk* c) {
+  using C = typename FmtInfo<F>::Chunk;
+#pragma unroll
+  for (int pl = 0; pl < FmtInfo<F>::PLANES; ++pl) {
+    const C* q = reinterpret_cast<const C*>(p + pl * plane_stride);
+    c[pl] = RO ? __ldg(q) : *q;
+  }
+}
+
+template <int F>
+__device__ __forceinline__ void store_chunks(unsigned char* p, long long plane_stride,
+                                             const typename FmtInfo<F>::Chunk* c) {
+  using C = typename FmtInfo<F>::Chunk;
+#pragma unroll
+  for (int pl = 0; pl < FmtInfo<F>::PLANES; ++pl)
+    *reinterpret_cast<C*>(p + pl * plane_stride) = c[pl];
 }
 
 // Decode one system (lane w of the site's plane data) from raw storage.
@@ -267,6 +289,32 @@ __device__ __forceinline__ void or_move2(float2& sx, float2& sy, float2& sz, flo
   if (hh.y > 0.0f) { sx.y = nx.y; sy.y = ny.y; sz.y = nz.y; }
 }
 
+// (sin, cos) of 2 pi u for a uniform u in (0, 1).  4u is exact in binary32,
+// so the reduction to the nearest quadrant, f = 4u - q in [-1/2, 1/2], is exact;
+// r = f pi/2 lies in [-pi/4, pi/4], where the Taylor series of sin (to r^9) and
+// cos (to r^10) are truncated below 3e-9; the quadrant rotation is exact.
+__device__ __forceinline__ void sincos_2pi(float u, float& s, float& c) {
+  const float t = 4.0f * u;
+  const float q = rintf(t);
+  const float r = (t - q) * 1.57079632679489662f;
+  const float r2 = r * r;
+  float ps = fmaf(r2, 2.75573192e-6f, -1.98412698e-4f);   // 1/9!, -1/7!
+  ps = fmaf(r2, ps, 8.33333333e-3f);                       // 1/5!
+  ps = fmaf(r2, ps, -1.66666667e-1f);                      // -1/3!
+  const float sr = fmaf(r * r2, ps, r);
+  float pc = fmaf(r2, -2.75573192e-7f, 2.48015873e-5f);    // -1/10!, 1/8!
+  pc = fmaf(r2, pc, -1.38888889e-3f);                      // -1/6!
+  pc = fmaf(r2, pc, 4.16666667e-2f);                       // 1/4!
+  pc = fmaf(r2, pc, -0.5f);                                // -1/2!
+  const float cr = fmaf(r2, pc, 1.0f);
+  switch (((int)q) & 3) {
+    case 0: s = sr; c = cr; break;
+    case 1: s = cr; c = -sr; break;
+    case 2: s = -sr; c = -cr; break;
+    default: s = -cr; c = sr; break;
+  }
+}
+
 // Heat bath, Eq. (2), one system: s' ~ exp(beta h.s) from the uniforms u1, u2.
 // With a = beta |h| and t the angle to h, the inverse CDF of exp(a cos t) on
 // [-1, 1] gives both distances to the poles in a well-conditioned form:
@@ -278,18 +326,27 @@ __device__ __forceinline__ void or_move2(float2& sx, float2& sy, float2& sz, flo
 template <bool FAST>
 __device__ __forceinline__ void hb_move(float& sx, float& sy, float& sz, float hx, float hy,
                                         float hz, float beta, float u1, float u2) {
-  const float hn = sqrtf(hx * hx + hy * hy + hz * hz);
+  const float hn2 = hx * hx + hy * hy + hz * hz;
+  const bool zero = !(hn2 > 0.0f);
+  const float rs = zero ? 0.0f : rsqrtf(hn2);      // 1 / |h|
+  const float hn = hn2 * rs;                       // |h|
   const float a = beta * hn;
   float dm, dp;
   if (a > 1e-12f) {
+    const float inv_a = __frcp_rn(a);
     if (FAST) {
-      dm = -__logf(fmaf(1.0f - u1, __expf(-2.0f * a) - 1.0f, 1.0f)) / a;
+      dm = -__logf(fmaf(1.0f - u1, __expf(-2.0f * a) - 1.0f, 1.0f)) * inv_a;
       dp = 2.0f - dm;
     } else {
-      const float inv_a = 1.0f / a;
-      dm = -log1pf((1.0f - u1) * expm1f(-2.0f * a)) * inv_a;
-      dp = 2.0f - dm;                   // accurate while cos t >= 0
-      if (dm > 1.0f && a < 40.0f) dp = log1pf(u1 * expm1f(2.0f * a)) * inv_a;
+      // exp(-2a) - 1 has no cancellation for a >= 0.35; the hardware exp's
+      // relative error (<~ 2a * 6e-8) enters 1 - cos t as <~ 1.2e-7 absolute
+      const float em = (a >= 0.35f) ? __expf(-2.0f * a) - 1.0f : expm1f(-2.0f * a);
+      dm = -log1pf((1.0f - u1) * em) * inv_a;
+      dp = 2.0f - dm;                                // accurate while cos t >= 0
+      if (dm > 1.0f && a < 40.0f) {
+        const float ep = (a >= 0.35f) ? __expf(2.0f * a) - 1.0f : expm1f(2.0f * a);
+        dp = log1pf(u1 * ep) * inv_a;
+      }
     }
   } else {
     dm = 2.0f * (1.0f - u1);
@@ -301,16 +358,17 @@ __device__ __forceinline__ void hb_move(float& sx, float& sy, float& sz, float h
   const float st = sqrtf(dm * dp);
   float sp, cp;
   if (FAST) {
-    __sincosf(6.28318530717959f * u2, &sp, &cp);
+    __sincosf(6.28318530717959f * (u2 - 0.5f), &sp, &cp);
+    sp = -sp;
+    cp = -cp;
   } else {
-    sincospif(2.0f * u2, &sp, &cp);
+    sincos_2pi(u2, sp, cp);
   }
   float nx = 0.0f, ny = 0.0f, nz = 1.0f;
-  if (hn > 0.0f) {
-    const float inv = 1.0f / hn;
-    nx = hx * inv;
-    ny = hy * inv;
-    nz = hz * inv;
+  if (!zero) {
+    nx = hx * rs;
+    ny = hy * rs;
+    nz = hz * rs;
   }
   const float sg = nz >= 0.0f ? 1.0f : -1.0f;
   const float A = -1.0f / (sg + nz);
@@ -325,25 +383,99 @@ __device__ __forceinline__ void hb_move(float& sx, float& sy, float& sz, float h
   sz = oz * inv;
 }
 
-// Per-block, per-system sums of the per-thread values e[VEC] of a block whose
-// thread t holds item item0 + t (item = site * G + chunk g): out[g * VEC + v]
-// is the sum over the threads of chunk g, added in thread order in FP64, so
-// the result is independent of scheduling.  Every thread of the block calls it.
-template <int VEC, int BS>
-__device__ __forceinline__ void block_system_sums(const float* e, uint32_t item0, int G, int Wp,
-                                                  double* out, float (*red)[VEC]) {
-#pragma unroll
-  for (int v = 0; v < VEC; ++v) red[threadIdx.x][v] = e[v];
-  __syncthreads();
-  const int r0 = (int)(item0 % (uint32_t)G);
-  for (int j = threadIdx.x; j < Wp; j += BS) {
-    const int g = j / VEC, v = j - (j / VEC) * VEC;
-    const int t0 = (g - r0 + G) % G;
-    double acc = 0.0;
-    for (int t = t0; t < BS; t += G) acc += (double)red[t][v];
-    out[j] = acc;
+// ----------------------------------------------------------------------------
+// Lattice geometry and couplings
+// ----------------------------------------------------------------------------
+struct SiteGeom {
+  uint32_t own;     // storage site of the updated spin
+  uint32_t nb[6];   // storage sites of +x, -x, +y, -y, +z, -z
+  uint32_t site;    // natural site index x + L (y + L z)
+};
+
+// Storage indices of the site of the given parity with half-index h and of its
+// six (opposite-parity) neighbours, periodic boundaries.
+__device__ __forceinline__ SiteGeom site_geom(const SampleDev& sd, uint32_t h, int parity) {
+  const uint32_t L = sd.L, Lh = sd.Lh, half_n = (uint32_t)sd.N >> 1;
+  const uint32_t r = (__umulhi(h, sd.fdLh_m) + h) >> sd.fdLh_s;     // row = y + L z
+  const uint32_t hx = h - r * Lh;
+  const uint32_t z = (__umulhi(r, sd.fdL_m) + r) >> sd.fdL_s;
+  const uint32_t y = r - z * L;
+  const uint32_t x = 2u * hx + ((uint32_t)(parity + y + z) & 1u);
+  const uint32_t ob = (uint32_t)(1 - parity) * half_n;
+  const uint32_t xp = (x + 1 == L) ? 0u : x + 1, xm = (x == 0) ? L - 1 : x - 1;
+  const uint32_t yp = (y + 1 == L) ? 0u : y + 1, ym = (y == 0) ? L - 1 : y - 1;
+  const uint32_t zp = (z + 1 == L) ? 0u : z + 1, zm = (z == 0) ? L - 1 : z - 1;
+  const uint32_t xh = x >> 1;
+  SiteGeom gm;
+  gm.own = (uint32_t)parity * half_n + h;
+  gm.nb[0] = ob + (xp >> 1) + r * Lh;
+  gm.nb[1] = ob + (xm >> 1) + r * Lh;
+  gm.nb[2] = ob + xh + (yp + L * z) * Lh;
+  gm.nb[3] = ob + xh + (ym + L * z) * Lh;
+  gm.nb[4] = ob + xh + (y + L * zp) * Lh;
+  gm.nb[5] = ob + xh + (y + L * zm) * Lh;
+  gm.site = 2u * h + (x & 1u);
+  return gm;
+}
+
+// Coupling/field record of one storage site: 6 bonds (+x, -x, +y, -y, +z, -z), 3 field.
+template <bool J16>
+__device__ __forceinline__ void load_record(const void* rec, long long idx, float* j6, float* h3) {
+  if (J16) {
+    const uint2* r = reinterpret_cast<const uint2*>(rec) + idx * 3;
+    const uint2 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2);
+    float2 t;
+    t = h2f(a.x); j6[0] = t.x; j6[1] = t.y;
+    t = h2f(a.y); j6[2] = t.x; j6[3] = t.y;
+    t = h2f(b.x); j6[4] = t.x; j6[5] = t.y;
+    t = h2f(b.y); h3[0] = t.x; h3[1] = t.y;
+    t = h2f(c.x); h3[2] = t.x;
+  } else {
+    const float4* r = reinterpret_cast<const float4*>(rec) + idx * 3;
+    const float4 a = __ldg(r), b = __ldg(r + 1), c = __ldg(r + 2);
+    j6[0] = a.x; j6[1] = a.y; j6[2] = a.z; j6[3] = a.w;
+    j6[4] = b.x; j6[5] = b.y; h3[0] = b.z; h3[1] = b.w;
+    h3[2] = c.x;
   }
-  __syncthreads();
+}
+
+// The six couplings of a site as binary16 bit patterns, each broadcast to both
+// halves of a 32-bit word (FP16 records only).
+__device__ __forceinline__ void load_record_j16(const void* rec, long long idx, uint32_t* j2) {
+  const uint2* r = reinterpret_cast<const uint2*>(rec) + idx * 3;
+  const uint2 a = __ldg(r), b = __ldg(r + 1);
+  const uint32_t w[3] = {a.x, a.y, b.x};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    j2[2 * k] = (w[k] & 0xffffu) * 0x10001u;
+    j2[2 * k + 1] = (w[k] >> 16) * 0x10001u;
+  }
+}
+
+// a += s * j for two systems, s and j binary16 (packed), a binary32.  The
+// product of two binary16 numbers is exact in binary32, so this mixed-precision
+// fused multiply-add rounds exactly like a multiply followed by an add.
+__device__ __forceinline__ void fma_f16_pair(float2& a, uint32_t s2, uint32_t j2) {
+  asm("{\n\t.reg .f16 s0, s1, j0, j1;\n\t"
+      "mov.b32 {s0, s1}, %2;\n\t"
+      "mov.b32 {j0, j1}, %3;\n\t"
+      "fma.rn.f32.f16 %0, s0, j0, %0;\n\t"
+      "fma.rn.f32.f16 %1, s1, j1, %1;\n\t}"
+      : "+f"(a.x), "+f"(a.y)
+      : "r"(s2), "r"(j2));
+}
+
+// Byte offset of chunk g of storage site ss in plane 0 of a sample's block.
+template <int F>
+__device__ __forceinline__ long long chunk_offset(const SampleDev& sd, uint32_t g, uint32_t ss) {
+  return ((long long)g * sd.N + ss) * FmtInfo<F>::CHUNK;
+}
+
+// Sum of v over the 32 lanes of a warp, result in lane 0 (fixed order).
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
 }
 
 // Fast unsigned division by a runtime constant (Granlund & Montgomery, 1994):

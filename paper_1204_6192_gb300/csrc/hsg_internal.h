@@ -3,10 +3,13 @@
 // Device data layout (all samples of a context in one allocation each):
 //   spins   per sample, sites in parity-split order: storage site
 //           ss(i) = p(i) * N/2 + (i >> 1), so each half-sweep touches one
-//           contiguous half of the array.  Component formats keep three planes
-//           [c][ss][Wp]; packed formats one plane [ss][Wp] of 32-bit words.
-//           The system index is innermost: one 16-byte chunk holds VEC
-//           systems of one site, so a warp reads 512 contiguous bytes.
+//           contiguous half of the array.  Systems come in chunks of 4: chunk g
+//           holds systems 4g .. 4g+3 of one site (16 bytes for FP32 and the
+//           packed 32-bit formats, 8 bytes for FP16/BF16).  Layout
+//           [plane c][chunk g][ss][4 systems]: component formats have three
+//           planes (x, y, z), packed formats one.  Consecutive sites of one
+//           chunk are contiguous, so a warp of consecutive sites reads 256-512
+//           contiguous bytes, and one thread can walk the chunks of its site.
 //   records per storage site 12 scalars (FP32 or FP16):
 //           [J+x, J-x, J+y, J-y], [J+z, J-z, Hx, Hy], [Hz, 0, 0, 0]
 //           i.e. the six bonds of the site and its field, shared by all Wp
@@ -46,11 +49,10 @@ struct SweepParams {
   unsigned char* spins;
   const void* rec;
   const SampleDev* samples;
-  const int2* blocks;       // (sample, first item) per block
+  const int4* blocks;       // (sample, chunk group, first half-site) per block
   const float* beta;        // [n_samples][Wp]
   const unsigned long long* counters;   // [0] sweeps done, [1] PT passes done
-  int G, Wp;
-  uint32_t fdG_m, fdG_s;
+  int G, Wp, GPT;            // chunks per site, padded systems, chunks per thread
   uint32_t seed_lo, seed_hi;
   int parity;
   int sweep_offset;
@@ -62,11 +64,11 @@ struct EnergyParams {
   const unsigned char* spins;
   const void* rec;
   const SampleDev* samples;
-  const int2* blocks;       // the sweep block table: (sample, first item)
+  const int4* blocks;       // the sweep block table
   double* partials;         // [2][n_blocks][Wp]: even-site and odd-site terms per block
+  double* partials2;        // [n_samples][splits][Wp]: second reduction level
   double* E;                // [n_samples][Wp]
-  int G, Wp, n_samples, n_blocks;
-  uint32_t fdG_m, fdG_s;
+  int G, Wp, GPT, n_samples, n_blocks, splits;
 };
 
 struct PTParams {
@@ -95,7 +97,7 @@ struct MeasureParams {
 struct ConvParams {
   unsigned char* spins;
   const SampleDev* samples;
-  const int2* blocks;       // same as the sweep table with parity ignored (both halves)
+  const int4* blocks;       // (sample, chunk g, first site) per block, all sites
   float* xyz;               // [sum_s W * N_s * 3]
   const long long* xyz_off; // per sample, float offset of its block
   int G, Wp, W;
