@@ -1,0 +1,110 @@
+"""Statistical parity of equilibrium observables, GPU against the FP64 oracle.
+
+Workload: L = 8, Gaussian J, 2 replicas x 8 temperatures, 200 steps of
+1 HB + 5 OR + PT, a measurement after every step; the second half of the
+series is averaged.  e(T) = <E>/N per temperature slot (both replicas) and
+<q^2> = <sum_{mu nu} (q^{mu nu})^2> per slot.  Errors from 10 bins.  The GPU and
+oracle chains use the same random numbers, so their difference is smaller
+than the combined error; the bound 3 sigma per slot is conservative.
+
+For the compressed storage forms the same comparison states the error of
+e(T) and <q^2> against the FP64 oracle (printed; run with -s to see it).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1204_6192_gb300 import hsg, inputs
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 200
+NBINS = 10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def workload(h_r=0.0, fp16_couplings=False):
+    t = inputs.geometric_temperatures(0.15, 0.6, 8)
+    smp = inputs.make_sample(8, t, h_r, disorder_seed=1)
+    r = inputs.round_fp16 if fp16_couplings else (lambda a: np.asarray(a, np.float32).astype(np.float64))
+    return inputs.Sample(L=8, J=r(smp.J), H=r(smp.H), temps=t)
+
+
+def series_gpu(smp, precision="fp32", j16=False):
+    ctx = hsg.Context([smp], 2, 1, precision=precision, j_fp16=j16)
+    E, Q = [], []
+    for _ in range(STEPS):
+        ctx.step(1)
+        m = ctx.measure()
+        E.append(m["E"][0])                                   # [R_O, R_T]
+        Q.append((m["q"][0] ** 2).sum(axis=(1, 2)))           # [R_T]
+    ctx.close()
+    return np.array(E), np.array(Q)
+
+
+def series_oracle(smp):
+    sim = oracle.OracleSim([smp], 2, 1)
+    E, Q = [], []
+    for _ in range(STEPS):
+        sim.step(1)
+        m = sim.measure()[0]
+        E.append(m["E"])
+        Q.append((m["q"] ** 2).sum(axis=(1, 2)))
+    return np.array(E), np.array(Q)
+
+
+def mean_err(x):
+    x = x[len(x) // 2:]
+    bins = np.array([b.mean(axis=0) for b in np.array_split(x, NBINS)])
+    return x.mean(axis=0), bins.std(axis=0, ddof=1) / np.sqrt(NBINS)
+
+
+def observables(E, Q, N):
+    e_m, e_s = mean_err(E.mean(axis=1) / N)     # replica-averaged energy per spin
+    q_m, q_s = mean_err(Q)
+    return e_m, e_s, q_m, q_s
+
+
+@pytest.fixture(scope="module")
+def oracle_fp32_couplings():
+    smp = workload()
+    return smp, observables(*series_oracle(smp), N=512)
+
+
+@pytest.fixture(scope="module")
+def oracle_fp16_couplings():
+    smp = workload(h_r=0.1, fp16_couplings=True)
+    return smp, observables(*series_oracle(smp), N=512)
+
+
+def compare(a, b, label, limit):
+    e_g, es_g, q_g, qs_g = a
+    e_o, es_o, q_o, qs_o = b
+    ze = (e_g - e_o) / np.sqrt(es_g ** 2 + es_o ** 2 + 1e-30)
+    zq = (q_g - q_o) / np.sqrt(qs_g ** 2 + qs_o ** 2 + 1e-30)
+    print(f"\n[{label}] e(T) GPU - oracle: {np.array2string(e_g - e_o, precision=5)}"
+          f"\n[{label}]   in sigma:        {np.array2string(ze, precision=2)}"
+          f"\n[{label}] <q^2> GPU - oracle: {np.array2string(q_g - q_o, precision=5)}"
+          f"\n[{label}]   in sigma:        {np.array2string(zq, precision=2)}")
+    assert np.all(np.abs(ze) <= limit), ze
+    assert np.all(np.abs(zq) <= limit), zq
+
+
+def test_equilibrium_observables_fp32(oracle_fp32_couplings):
+    smp, ref = oracle_fp32_couplings
+    gpu = observables(*series_gpu(smp), N=512)
+    compare(gpu, ref, "fp32", 3.0)
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16", "angle16", "oct16"])
+def test_compressed_storage_error_against_fp64(oracle_fp16_couplings, precision):
+    """Compressed spins with FP16 couplings against the FP64 oracle (no storage
+    rounding): the storage error stays within the statistical error."""
+    smp, ref = oracle_fp16_couplings
+    gpu = observables(*series_gpu(smp, precision=precision, j16=True), N=512)
+    compare(gpu, ref, precision, 4.0)
