@@ -87,13 +87,19 @@ typedef struct {
   int n_or_per_step;  /* OR sweeps per hsg_step (default 5) */
   int device;         /* CUDA device ordinal (default 0) */
   void* stream;       /* cudaStream_t to use; NULL: the library creates a non-blocking stream */
-  int variant;        /* sweep kernel schedule: 0 = automatic, else an HSG_VARIANT_* value */
+  int variant;        /* step schedule: 0 = automatic, else an HSG_VARIANT_* value */
+  int barrier_timeout_ms;   /* bound of every grid-barrier wait of the persistent schedule
+                               (default 2000); a wait that runs out ends the launch and the
+                               next synchronising call returns HSG_ETIMEOUT */
+  int inject_barrier_fault; /* testing only: nonzero makes one block skip the first grid
+                               barrier of the next persistent launch, so the others time out */
 } hsg_options;
 
 enum {
   HSG_VARIANT_AUTO = 0,
-  HSG_VARIANT_TWO_PASS = 1,   /* one launch per half-sweep over all samples */
-  HSG_VARIANT_RESIDENT = 2    /* whole sweeps of a small lattice held in shared memory */
+  HSG_VARIANT_TWO_PASS = 1,   /* hsg_step replays a CUDA graph of one launch per phase */
+  HSG_VARIANT_PERSISTENT = 2  /* hsg_step runs all its steps in one cooperative launch whose
+                                 blocks meet at bounded grid barriers between phases */
 };
 
 /* Fill *opt with the defaults listed above. */
@@ -134,8 +140,14 @@ hsg_status hsg_pt_exchange(hsg_ctx* ctx);
    memory-slot order) instead of recomputed ones. */
 hsg_status hsg_pt_exchange_energies(hsg_ctx* ctx, const double* E_sys);
 
-/* n_steps steps of n_hb HB sweeps + n_or OR sweeps + energies + PT, replayed
-   from a CUDA graph captured on the first call. */
+/* n_steps steps of n_hb HB sweeps + n_or OR sweeps + energies + PT.  Two-pass
+   schedule: a CUDA graph of one launch per phase, captured on the first call
+   and replayed per step.  Persistent schedule (needs n_or >= 1): one
+   cooperative launch for all n_steps.  Automatic: the first call times both
+   schedules and several chunks-per-thread settings on the context itself
+   (restoring its state afterwards) and keeps the fastest; the choice is cached
+   per problem shape for the process.  All settings run the same arithmetic and
+   give bit-identical results. */
 hsg_status hsg_step(hsg_ctx* ctx, int n_steps);
 
 /* FP64 energies (Eq. 1) of every system, memory-slot order, into host
@@ -191,6 +203,7 @@ typedef struct {
   uint64_t sweep_count;    /* sweeps done (the HB counter word) */
   uint64_t pt_count;       /* PT passes done */
   void* stream;            /* the cudaStream_t the context runs on */
+  int chunks_per_thread;   /* sweep kernels: chunks of 4 systems one thread walks */
 } hsg_info;
 hsg_status hsg_get_info(hsg_ctx* ctx, hsg_info* info);
 

@@ -6,6 +6,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -68,6 +70,15 @@ struct hsg_ctx {
 
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
+
+  // persistent schedule
+  int variant = HSG_VARIANT_TWO_PASS;   // resolved step schedule
+  bool tune_pending = false;            // automatic schedule not yet tuned
+  long long max_sweep_blocks = 0;       // sweep table capacity (one chunk per thread)
+  unsigned int* d_bar = nullptr;        // grid barrier: arrivals, generation, error word
+  int persist_grid = 0;
+  size_t persist_smem = 0;
+  bool inject_fault = false;
 
   hsg_status err = HSG_OK;
   std::string msg;
@@ -245,6 +256,29 @@ hsg_status enqueue_step(hsg_ctx* c) {
   return HSG_OK;
 }
 
+// A bounded device wait that ran out (persistent schedule) is reported here,
+// after the stream has been synchronised.
+hsg_status poll_device_error(hsg_ctx* c) {
+  unsigned int err = 0;
+  HSG_CUDA(c, cudaMemcpy(&err, c->d_bar + 2, sizeof(err), cudaMemcpyDeviceToHost));
+  if (err) return fail(c, HSG_ETIMEOUT, "a grid barrier wait of the persistent step kernel timed out");
+  return HSG_OK;
+}
+
+PersistParams persist_params(hsg_ctx* c, int n_steps) {
+  PersistParams P;
+  P.sw = sweep_params(c, 0, 0);
+  P.en = energy_params(c);
+  P.pt = pt_params(c, 0, 1);
+  P.bar = c->d_bar;
+  P.timeout_ns = (unsigned long long)std::max(1, c->opt.barrier_timeout_ms) * 1000000ull;
+  P.n_steps = n_steps;
+  P.nhb = c->opt.n_hb_per_step;
+  P.nor = c->opt.n_or_per_step;
+  P.drop_first = c->inject_fault ? 1 : 0;
+  return P;
+}
+
 hsg_status ensure_xyz(hsg_ctx* c) {
   if (c->d_xyz) return HSG_OK;
   HSG_TRY(dev_alloc(c, &c->d_xyz, (size_t)c->xyz_floats * sizeof(float)));
@@ -258,6 +292,176 @@ bool finite_all(const float* a, size_t n) {
   for (size_t i = 0; i < n; ++i)
     if (!std::isfinite(a[i])) return false;
   return true;
+}
+
+// chunks per thread: enough threads to fill the GPU (~152 SMs x 2048); the
+// rest of the chunks are walked by each thread, so that the site geometry and
+// couplings are computed once per site
+int default_gpt(hsg_ctx*, const int* L, int n_samples, int G) {
+  long long half_sites = 0;
+  for (int s = 0; s < n_samples; ++s) half_sites += (long long)L[s] * L[s] * L[s] / 2;
+  const long long gpt = half_sites * G / (152ll * 2048);
+  return (int)std::max(1ll, std::min((long long)G, gpt));
+}
+
+// Build the sweep block table for `gpt` chunks per thread and set up the
+// chosen step schedule (drops a captured graph: its parameters change).
+hsg_status configure_schedule(hsg_ctx* c, int variant, int gpt) {
+  gpt = std::max(1, std::min(c->G, gpt));
+  const int n_gg = (c->G + gpt - 1) / gpt;
+  std::vector<int4> blocks;
+  int max_rows = 1;
+  for (int s = 0; s < c->ns; ++s) {
+    SampleDev& d = c->sd[s];
+    d.blk0 = (int)blocks.size();
+    for (int gg = 0; gg < n_gg; ++gg)
+      for (int h0 = 0; h0 < d.N / 2; h0 += SWEEP_BS) blocks.push_back(make_int4(s, gg, h0, 0));
+    d.blk1 = (int)blocks.size();
+    max_rows = std::max(max_rows, d.blk1 - d.blk0);
+  }
+  if ((long long)blocks.size() > c->max_sweep_blocks) return fail(c, HSG_ESTATE, "sweep table overflow");
+  c->GPT = gpt;
+  c->n_sweep_blocks = (int)blocks.size();
+  c->e_splits = std::min(64, std::max(1, max_rows / 256));
+  HSG_CUDA(c, cudaMemcpyAsync(c->d_sweep_blocks, blocks.data(), sizeof(int4) * blocks.size(),
+                              cudaMemcpyHostToDevice, c->stream));
+  HSG_CUDA(c, cudaMemcpyAsync(c->d_sd, c->sd.data(), sizeof(SampleDev) * c->ns,
+                              cudaMemcpyHostToDevice, c->stream));
+  HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (c->graph_exec) {
+    cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+  }
+  if (c->graph) {
+    cudaGraphDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->variant = variant;
+  if (variant == HSG_VARIANT_PERSISTENT) {
+    c->persist_smem = sizeof(float) * (SWEEP_BS / 32) * c->GPT * c->VEC;
+    int max_grid = 0;
+    HSG_CUDA(c, max_persistent_grid(c->fmt, c->j16, c->opt.fast_math != 0, c->persist_smem, &max_grid));
+    if (max_grid < 2) return fail(c, HSG_ECUDA, "persistent kernel does not fit on the device");
+    const int wgs = (c->Wp + 31) / 32;
+    long long need = std::max<long long>(c->n_sweep_blocks, (long long)c->e_splits * wgs * c->ns);
+    need = std::max<long long>(need, ((long long)c->ns * c->Wp + SWEEP_BS - 1) / SWEEP_BS);
+    c->persist_grid = (int)std::max(2ll, std::min<long long>(max_grid, need));
+  }
+  return HSG_OK;
+}
+
+// n_steps steps with the configured schedule (graph captured on first use).
+hsg_status run_steps(hsg_ctx* c, int n_steps) {
+  if (c->variant == HSG_VARIANT_PERSISTENT) {
+    HSG_CUDA(c, cudaMemsetAsync(c->d_bar, 0, sizeof(unsigned int), c->stream));
+    PersistParams P = persist_params(c, n_steps);
+    c->inject_fault = false;
+    HSG_CUDA(c, launch_persistent(c->fmt, c->j16, c->opt.fast_math != 0, P, c->persist_grid,
+                                  c->persist_smem, c->stream));
+    return HSG_OK;
+  }
+  if (!c->graph_exec) {
+    HSG_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    hsg_status st = enqueue_step(c);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (st != HSG_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    HSG_CUDA(c, e);
+    c->graph = g;
+    HSG_CUDA(c, cudaGraphInstantiate(&c->graph_exec, c->graph, 0));
+  }
+  for (int k = 0; k < n_steps; ++k) HSG_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream));
+  return HSG_OK;
+}
+
+// Autotuner: the schedules and chunks-per-thread settings compute identical
+// results, so they are timed on the live context (2 steps each, after a warm-up
+// step) and the fastest is kept; the state is saved before and restored after,
+// so the Markov chain is untouched.  Results are cached per problem shape for
+// the life of the process.
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<int, int>> g_tune_cache;
+
+std::string tune_key(hsg_ctx* c) {
+  std::string k = std::to_string(c->fmt) + "/" + std::to_string(c->j16) + "/" +
+                  std::to_string(c->opt.fast_math) + "/" + std::to_string(c->W) + "/" +
+                  std::to_string(c->opt.n_hb_per_step) + "/" + std::to_string(c->opt.n_or_per_step) +
+                  "/L";
+  for (int L : c->L) k += std::to_string(L) + ",";
+  return k;
+}
+
+hsg_status autotune(hsg_ctx* c) {
+  c->tune_pending = false;
+  const std::string key = tune_key(c);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) return configure_schedule(c, it->second.first, it->second.second);
+  }
+  // save the state the trial steps will change
+  void* spins_copy = nullptr;
+  HSG_CUDA(c, cudaMalloc(&spins_copy, c->spin_bytes));
+  const size_t n_perm = (size_t)c->ns * c->R_O * c->R_T;
+  const size_t n_acc = (size_t)c->ns * c->R_O * std::max(1, c->R_T - 1);
+  std::vector<int> perm(n_perm);
+  std::vector<float> beta((size_t)c->ns * c->Wp);
+  std::vector<double> E((size_t)c->ns * c->Wp);
+  std::vector<unsigned long long> acc(n_acc), cnt(2);
+  cudaStream_t st = c->stream;
+  HSG_CUDA(c, cudaMemcpyAsync(spins_copy, c->spins, c->spin_bytes, cudaMemcpyDeviceToDevice, st));
+  HSG_CUDA(c, cudaMemcpyAsync(perm.data(), c->d_perm, sizeof(int) * n_perm, cudaMemcpyDeviceToHost, st));
+  HSG_CUDA(c, cudaMemcpyAsync(beta.data(), c->d_beta, sizeof(float) * beta.size(), cudaMemcpyDeviceToHost, st));
+  HSG_CUDA(c, cudaMemcpyAsync(E.data(), c->d_E, sizeof(double) * E.size(), cudaMemcpyDeviceToHost, st));
+  HSG_CUDA(c, cudaMemcpyAsync(acc.data(), c->d_acc, sizeof(unsigned long long) * n_acc, cudaMemcpyDeviceToHost, st));
+  HSG_CUDA(c, cudaMemcpyAsync(cnt.data(), c->d_counters, sizeof(unsigned long long) * 2, cudaMemcpyDeviceToHost, st));
+  HSG_CUDA(c, cudaStreamSynchronize(st));
+
+  std::vector<int> gpts;
+  for (int g : {c->G, (c->G + 1) / 2, (c->G + 3) / 4, 2, 1, c->GPT})
+    if (g >= 1 && g <= c->G && std::find(gpts.begin(), gpts.end(), g) == gpts.end()) gpts.push_back(g);
+  cudaEvent_t e0, e1;
+  HSG_CUDA(c, cudaEventCreate(&e0));
+  HSG_CUDA(c, cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_v = HSG_VARIANT_TWO_PASS, best_g = c->GPT;
+  for (int v : {HSG_VARIANT_TWO_PASS, HSG_VARIANT_PERSISTENT}) {
+    for (int g : gpts) {
+      HSG_TRY(configure_schedule(c, v, g));
+      HSG_TRY(run_steps(c, 1));
+      HSG_CUDA(c, cudaEventRecord(e0, st));
+      HSG_TRY(run_steps(c, 2));
+      HSG_CUDA(c, cudaEventRecord(e1, st));
+      HSG_CUDA(c, cudaEventSynchronize(e1));
+      HSG_TRY(poll_device_error(c));
+      float ms = 0.0f;
+      HSG_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        best_v = v;
+        best_g = g;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // restore
+  HSG_CUDA(c, cudaMemcpyAsync(c->spins, spins_copy, c->spin_bytes, cudaMemcpyDeviceToDevice, st));
+  HSG_CUDA(c, cudaMemcpyAsync(c->d_perm, perm.data(), sizeof(int) * n_perm, cudaMemcpyHostToDevice, st));
+  HSG_CUDA(c, cudaMemcpyAsync(c->d_beta, beta.data(), sizeof(float) * beta.size(), cudaMemcpyHostToDevice, st));
+  HSG_CUDA(c, cudaMemcpyAsync(c->d_E, E.data(), sizeof(double) * E.size(), cudaMemcpyHostToDevice, st));
+  HSG_CUDA(c, cudaMemcpyAsync(c->d_acc, acc.data(), sizeof(unsigned long long) * n_acc, cudaMemcpyHostToDevice, st));
+  HSG_CUDA(c, cudaMemcpyAsync(c->d_counters, cnt.data(), sizeof(unsigned long long) * 2, cudaMemcpyHostToDevice, st));
+  HSG_CUDA(c, cudaStreamSynchronize(st));
+  HSG_CUDA(c, cudaFree(spins_copy));
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = std::make_pair(best_v, best_g);
+  }
+  return configure_schedule(c, best_v, best_g);
 }
 
 hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double* temps,
@@ -340,18 +544,9 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   }
 
   // layout
-  std::vector<int4> sweep_blocks, conv_blocks;
-  // chunks per thread: enough threads to fill the GPU (~152 SMs x 2048), the
-  // rest of the chunks walked by each thread so site geometry and couplings
-  // are computed once per site
-  {
-    long long half_sites = 0;
-    for (int s = 0; s < n_samples; ++s) half_sites += (long long)L[s] * L[s] * L[s] / 2;
-    const long long target = 152ll * 2048;
-    long long gpt = half_sites * G / target;
-    c->GPT = (int)std::max(1ll, std::min((long long)G, gpt));
-  }
-  const int n_gg = (G + c->GPT - 1) / c->GPT;
+  std::vector<int4> conv_blocks;
+  long long max_sweep_blocks = 0;
+  c->GPT = default_gpt(c, L, n_samples, G);
   size_t spin_off = 0, rec_off = 0;
   long long xyz = 0;
   for (int s = 0; s < n_samples; ++s) {
@@ -365,10 +560,7 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
     d.plane_stride = (long long)d.N * Wp * c->ELEM;
     d.rec_off = (long long)rec_off;
     d.sys_base = s * Wp;
-    d.blk0 = (int)sweep_blocks.size();
-    for (int gg = 0; gg < n_gg; ++gg)
-      for (int h0 = 0; h0 < d.N / 2; h0 += SWEEP_BS) sweep_blocks.push_back(make_int4(s, gg, h0, 0));
-    d.blk1 = (int)sweep_blocks.size();
+    max_sweep_blocks += (long long)G * ((d.N / 2 + SWEEP_BS - 1) / SWEEP_BS);
     for (int g = 0; g < G; ++g)
       for (int s0 = 0; s0 < d.N; s0 += 256) conv_blocks.push_back(make_int4(s, g, s0, 0));
     size_t sb = (size_t)c->PL * d.plane_stride;
@@ -383,12 +575,7 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   c->xyz_floats = xyz;
   c->spin_bytes = spin_off;
   c->rec_bytes = rec_off * (c->j16 ? 24 : 48);
-  c->n_sweep_blocks = (int)sweep_blocks.size();
-  {
-    int max_rows = 1;
-    for (const SampleDev& d : c->sd) max_rows = std::max(max_rows, d.blk1 - d.blk0);
-    c->e_splits = std::min(64, std::max(1, max_rows / 256));
-  }
+  c->max_sweep_blocks = max_sweep_blocks;
   c->n_conv_blocks = (int)conv_blocks.size();
 
   // records: six bonds and the field of every storage site
@@ -440,10 +627,10 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   HSG_ALLOC(c->spins, c->spin_bytes);
   HSG_ALLOC(c->rec, c->rec_bytes);
   HSG_ALLOC(c->d_sd, sizeof(SampleDev) * n_samples);
-  HSG_ALLOC(c->d_sweep_blocks, sizeof(int4) * sweep_blocks.size());
+  HSG_ALLOC(c->d_sweep_blocks, sizeof(int4) * max_sweep_blocks);
   HSG_ALLOC(c->d_conv_blocks, sizeof(int4) * conv_blocks.size());
-  HSG_ALLOC(c->d_epart, sizeof(double) * 2 * sweep_blocks.size() * Wp);
-  HSG_ALLOC(c->d_epart2, sizeof(double) * n_samples * c->e_splits * Wp);
+  HSG_ALLOC(c->d_epart, sizeof(double) * 2 * max_sweep_blocks * Wp);
+  HSG_ALLOC(c->d_epart2, sizeof(double) * n_samples * 64 * Wp);
   HSG_ALLOC(c->d_beta, sizeof(float) * n_samples * Wp);
   HSG_ALLOC(c->d_temps, sizeof(double) * n_samples * n_temps);
   HSG_ALLOC(c->d_inv_temps, sizeof(double) * n_samples * n_temps);
@@ -451,6 +638,7 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   HSG_ALLOC(c->d_E, sizeof(double) * n_samples * Wp);
   HSG_ALLOC(c->d_acc, sizeof(unsigned long long) * n_samples * n_replicas * std::max(1, n_temps - 1));
   HSG_ALLOC(c->d_counters, sizeof(unsigned long long) * 2);
+  HSG_ALLOC(c->d_bar, sizeof(unsigned int) * 4);
 #undef HSG_ALLOC
 
   std::vector<double> inv(n_samples * (size_t)n_temps);
@@ -473,7 +661,6 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   }
   HSG_UP(c->rec, c->j16 ? (const void*)rech.data() : (const void*)recf.data(), c->rec_bytes);
   HSG_UP(c->d_sd, c->sd.data(), sizeof(SampleDev) * n_samples);
-  HSG_UP(c->d_sweep_blocks, sweep_blocks.data(), sizeof(int4) * sweep_blocks.size());
   HSG_UP(c->d_conv_blocks, conv_blocks.data(), sizeof(int4) * conv_blocks.size());
   HSG_UP(c->d_temps, temps, sizeof(double) * n_samples * n_temps);
   HSG_UP(c->d_inv_temps, inv.data(), sizeof(double) * inv.size());
@@ -483,11 +670,22 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
 #undef HSG_UP
   e = cudaMemset(c->d_acc, 0, sizeof(unsigned long long) * n_samples * n_replicas * std::max(1, n_temps - 1));
   if (e == cudaSuccess) e = cudaMemset(c->d_E, 0, sizeof(double) * n_samples * Wp);
+  if (e == cudaSuccess) e = cudaMemset(c->d_bar, 0, sizeof(unsigned int) * 4);
   if (e == cudaSuccess) e = cudaMemset(c->spins, 0, c->spin_bytes);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     c->msg = std::string("device init: ") + cudaGetErrorString(e);
     return cleanup_fail(HSG_ECUDA);
+  }
+  // step schedule: automatic contexts are tuned at their first hsg_step; until
+  // then (and for explicit choices) the two-pass graph or the requested one
+  {
+    c->tune_pending = opt.variant == HSG_VARIANT_AUTO && opt.n_or_per_step >= 1;
+    int want = opt.variant == HSG_VARIANT_AUTO ? HSG_VARIANT_TWO_PASS : opt.variant;
+    if (opt.n_or_per_step < 1) want = HSG_VARIANT_TWO_PASS;
+    c->inject_fault = opt.inject_barrier_fault != 0;
+    hsg_status st2 = configure_schedule(c, want, c->GPT);
+    if (st2 != HSG_OK) return cleanup_fail(st2);
   }
   ConvParams cp = conv_params(c, nullptr, nullptr);
   e = launch_init(c->fmt, cp, c->n_conv_blocks, c->stream);
@@ -515,6 +713,7 @@ void hsg_default_options(hsg_options* opt) {
   opt->precision = HSG_FP32;
   opt->n_hb_per_step = 1;
   opt->n_or_per_step = 5;
+  opt->barrier_timeout_ms = 2000;
 }
 
 hsg_status hsg_create(hsg_ctx** out, int L, const double* temps, int n_temps, int n_replicas,
@@ -567,6 +766,7 @@ hsg_status hsg_pt_exchange_energies(hsg_ctx* c, const double* E_sys) {
   HSG_CUDA(c, launch_pt(pt_params(c, 0, 1), c->stream));
   // the host array may be released by the caller on return
   HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  HSG_TRY(poll_device_error(c));
   return HSG_OK;
 }
 
@@ -575,21 +775,8 @@ hsg_status hsg_step(hsg_ctx* c, int n_steps) {
   if (n_steps < 0) return bad_arg(c, "n_steps < 0");
   if (n_steps == 0) return HSG_OK;
   HSG_CUDA(c, cudaSetDevice(c->device));
-  if (!c->graph_exec) {
-    HSG_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    hsg_status st = enqueue_step(c);
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
-    if (st != HSG_OK) {
-      if (g) cudaGraphDestroy(g);
-      return st;
-    }
-    HSG_CUDA(c, e);
-    c->graph = g;
-    HSG_CUDA(c, cudaGraphInstantiate(&c->graph_exec, c->graph, 0));
-  }
-  for (int k = 0; k < n_steps; ++k) HSG_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream));
-  return HSG_OK;
+  if (c->tune_pending) HSG_TRY(autotune(c));
+  return run_steps(c, n_steps);
 }
 
 hsg_status hsg_energies(hsg_ctx* c, double* E_sys) {
@@ -600,6 +787,7 @@ hsg_status hsg_energies(hsg_ctx* c, double* E_sys) {
   HSG_CUDA(c, cudaMemcpy2DAsync(E_sys, sizeof(double) * c->W, c->d_E, sizeof(double) * c->Wp,
                                 sizeof(double) * c->W, c->ns, cudaMemcpyDeviceToHost, c->stream));
   HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  HSG_TRY(poll_device_error(c));
   return HSG_OK;
 }
 
@@ -610,6 +798,7 @@ hsg_status hsg_last_energies(hsg_ctx* c, double* E_sys) {
   HSG_CUDA(c, cudaMemcpy2DAsync(E_sys, sizeof(double) * c->W, c->d_E, sizeof(double) * c->Wp,
                                 sizeof(double) * c->W, c->ns, cudaMemcpyDeviceToHost, c->stream));
   HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  HSG_TRY(poll_device_error(c));
   return HSG_OK;
 }
 
@@ -652,6 +841,7 @@ hsg_status hsg_measure(hsg_ctx* c, hsg_obs* o) {
     HSG_CUDA(c, cudaMemcpyAsync(o->qk, c->d_qk, sizeof(double) * c->ns * c->R_T * 54,
                                 cudaMemcpyDeviceToHost, c->stream));
   HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  HSG_TRY(poll_device_error(c));
   for (int s = 0; s < c->ns; ++s)
     for (int r = 0; r < c->R_O; ++r)
       for (int t = 0; t < c->R_T; ++t) {
@@ -690,6 +880,7 @@ hsg_status hsg_get_spins(hsg_ctx* c, float* xyz) {
   HSG_CUDA(c, cudaMemcpyAsync(xyz, c->d_xyz, sizeof(float) * c->xyz_floats, cudaMemcpyDeviceToHost,
                               c->stream));
   HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  HSG_TRY(poll_device_error(c));
   return HSG_OK;
 }
 
@@ -703,6 +894,7 @@ hsg_status hsg_set_spins(hsg_ctx* c, const float* xyz) {
   HSG_CUDA(c, launch_set(c->fmt, conv_params(c, c->d_xyz, c->d_xyz_off), c->n_conv_blocks, c->stream));
   // the host buffer has been read once the copy is done
   HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  HSG_TRY(poll_device_error(c));
   return HSG_OK;
 }
 
@@ -713,6 +905,7 @@ hsg_status hsg_get_perm(hsg_ctx* c, int32_t* perm) {
   HSG_CUDA(c, cudaMemcpyAsync(perm, c->d_perm, sizeof(int) * c->ns * c->R_O * c->R_T,
                               cudaMemcpyDeviceToHost, c->stream));
   HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  HSG_TRY(poll_device_error(c));
   return HSG_OK;
 }
 
@@ -726,6 +919,7 @@ hsg_status hsg_get_pt_stats(hsg_ctx* c, uint64_t* accepted, uint64_t* n_calls) {
                                 cudaMemcpyDeviceToHost, c->stream));
   HSG_CUDA(c, cudaMemcpyAsync(cnt, c->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
   HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  HSG_TRY(poll_device_error(c));
   if (n_calls) *n_calls = cnt[1];
   return HSG_OK;
 }
@@ -737,6 +931,7 @@ hsg_status hsg_get_info(hsg_ctx* c, hsg_info* info) {
   unsigned long long cnt[2];
   HSG_CUDA(c, cudaMemcpyAsync(cnt, c->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
   HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  HSG_TRY(poll_device_error(c));
   info->n_samples = c->ns;
   info->n_temps = c->R_T;
   info->n_replicas = c->R_O;
@@ -744,7 +939,8 @@ hsg_status hsg_get_info(hsg_ctx* c, hsg_info* info) {
   info->Wp = c->Wp;
   info->precision = c->fmt;
   info->j_fp16 = c->j16 ? 1 : 0;
-  info->variant = HSG_VARIANT_TWO_PASS;
+  info->variant = c->variant;
+  info->chunks_per_thread = c->GPT;
   info->total_sites = c->total_sites;
   info->total_spins = c->total_sites * c->W;
   info->spin_bytes = (long long)c->spin_bytes;
@@ -759,6 +955,7 @@ hsg_status hsg_sync(hsg_ctx* c) {
   HSG_CHECK_CTX(c);
   HSG_CUDA(c, cudaSetDevice(c->device));
   HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  HSG_TRY(poll_device_error(c));
   HSG_CUDA(c, cudaGetLastError());
   return HSG_OK;
 }

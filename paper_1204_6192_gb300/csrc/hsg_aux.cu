@@ -6,8 +6,7 @@
 // Every reduction is deterministic: per-thread partial sums, a fixed-order
 // shuffle/shared-memory tree inside a block, and a second kernel that adds the
 // block partials in a fixed order.  Two runs give bit-identical results.
-#include "hsg_device.cuh"
-#include "hsg_internal.h"
+#include "hsg_kernels.cuh"
 
 namespace hsg {
 
@@ -56,9 +55,9 @@ __global__ void __launch_bounds__(RED_BS) k_energy(const EnergyParams p) {
       const long long dg = (long long)(g - g0) * gstride;
       Chunk nc[6][PL], co[PL], ce[PL];
 #pragma unroll
-      for (int n = 0; n < 6; ++n) load_chunks<F, true>(base + nb_off[n] + dg, ps, nc[n]);
-      load_chunks<F, true>(base + odd_off + dg, ps, co);
-      load_chunks<F, true>(base + even_off + dg, ps, ce);
+      for (int n = 0; n < 6; ++n) load_chunks<F, LD_RO>(base + nb_off[n] + dg, ps, nc[n]);
+      load_chunks<F, LD_RO>(base + odd_off + dg, ps, co);
+      load_chunks<F, LD_RO>(base + even_off + dg, ps, ce);
       Spins<VEC> hf, t;
       decode<F>(nc[0], t);
 #pragma unroll
@@ -123,41 +122,16 @@ __global__ void __launch_bounds__(RED_BS) k_energy(const EnergyParams p) {
 // in two fixed-order levels: split k of the sample's rows is added by a block
 // of 32 systems x 8 row lanes (coalesced rows of Wp doubles), then the splits.
 __global__ void __launch_bounds__(256) k_energy_final1(const EnergyParams p) {
-  const int s = blockIdx.z, split = blockIdx.x;
-  const int w = blockIdx.y * 32 + threadIdx.x;
-  const SampleDev& sd = p.samples[s];
-  const int nrows = sd.blk1 - sd.blk0;
-  const int per = (nrows + p.splits - 1) / p.splits;
-  const int r0 = sd.blk0 + split * per;
-  const int r1 = min(r0 + per, sd.blk1);
-  double acc = 0.0;
-  if (w < p.Wp) {
-    for (int r = r0 + (int)threadIdx.y; r < r1; r += 8) {
-      acc += p.partials[(long long)r * p.Wp + w];
-      acc += p.partials[((long long)p.n_blocks + r) * p.Wp + w];
-    }
-  }
   __shared__ double red[8][32];
-  red[threadIdx.y][threadIdx.x] = acc;
-  __syncthreads();
-  if (threadIdx.y == 0 && w < p.Wp) {
-    double t = 0.0;
-    for (int k = 0; k < 8; ++k) t += red[k][threadIdx.x];
-    p.partials2[((long long)s * p.splits + split) * p.Wp + w] = t;
-  }
+  energy_final1_unit<false>(p, blockIdx.z, blockIdx.y, blockIdx.x, red);
 }
 
 __global__ void k_energy_final2(const EnergyParams p) {
-  const int s = blockIdx.x;
-  for (int w = threadIdx.x; w < p.Wp; w += blockDim.x) {
-    double e = 0.0;
-    for (int k = 0; k < p.splits; ++k) e += p.partials2[((long long)s * p.splits + k) * p.Wp + w];
-    p.E[(long long)s * p.Wp + w] = e;
-  }
+  for (int w = threadIdx.x; w < p.Wp; w += blockDim.x) energy_final2_unit<false>(p, blockIdx.x, w);
 }
 
 cudaError_t launch_energy_final(const EnergyParams& p, cudaStream_t st) {
-  k_energy_final1<<<dim3(p.splits, (p.Wp + 31) / 32, p.n_samples), dim3(32, 8), 0, st>>>(p);
+  k_energy_final1<<<dim3(p.splits, (p.Wp + 31) / 32, p.n_samples), 256, 0, st>>>(p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_energy_final2<<<p.n_samples, 128, 0, st>>>(p);
@@ -192,32 +166,8 @@ cudaError_t launch_energy(int fmt, bool j16, const EnergyParams& p, cudaStream_t
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_pt(const PTParams p) {
   const int n_chains = p.n_samples * p.R_O;
-  for (int c = threadIdx.x; c < n_chains; c += blockDim.x) {
-    const int s = c / p.R_O, r = c - s * p.R_O;
-    int* perm = p.perm + (long long)c * p.R_T;
-    const double* E = p.E + (long long)s * p.Wp + r * p.R_T;
-    const double* ib = p.inv_temps + (long long)s * p.R_T;
-    const uint32_t step = (uint32_t)p.counters[1];
-    if (p.bump_pt) {
-      for (int k = 0; k + 1 < p.R_T; ++k) {
-        const int a = perm[k], b = perm[k + 1];
-        const double dbeta = ib[k + 1] - ib[k];
-        const double dE = E[b] - E[a];
-        const double x = dbeta * dE;
-        const uint4 rnd = philox4x32_10(make_uint4((uint32_t)k, (uint32_t)c, step, TAG_PT),
-                                        p.seed_lo, p.seed_hi);
-        const double u = (double)u01(rnd.x);
-        const bool acc = (x >= 0.0) || (u < exp(x));
-        if (acc) {
-          perm[k] = b;
-          perm[k + 1] = a;
-          p.accepted[(long long)c * (p.R_T - 1) + k] += 1ull;
-        }
-      }
-    }
-    float* beta = p.beta + (long long)s * p.Wp + r * p.R_T;
-    for (int t = 0; t < p.R_T; ++t) beta[perm[t]] = (float)ib[t];
-  }
+  const uint32_t step = (uint32_t)p.counters[1];
+  for (int c = threadIdx.x; c < n_chains; c += blockDim.x) pt_chain<false>(p, c, step);
   __syncthreads();
   if (threadIdx.x == 0) {
     p.counters[0] += (unsigned long long)p.sweeps_per_call;
@@ -458,7 +408,7 @@ __global__ void k_get(const ConvParams p) {
   const int sidx = p.blocks[blockIdx.x].x;
   const unsigned char* o = p.spins + it.sd->spin_off + chunk_offset<F>(*it.sd, it.g, it.ss);
   typename FmtInfo<F>::Chunk c[PL];
-  load_chunks<F, false>(o, it.sd->plane_stride, c);
+  load_chunks<F, LD_PLAIN>(o, it.sd->plane_stride, c);
   Spins<VEC> s;
   decode<F>(c, s);
   float* out = p.xyz + p.xyz_off[sidx];

@@ -216,15 +216,18 @@ __device__ __forceinline__ void encode(const Spins<4>& s, typename FmtInfo<F>::C
 }
 
 // Chunk loads and stores of one site (PLANES chunks, plane_stride bytes apart).
-// ro: through the read-only path (data not written during the launch).
-template <int F, bool RO>
+// LD_RO: read-only path (data not written during the launch); LD_PLAIN: the
+// default path; LD_CG: L2 only (data written by other blocks of a running
+// persistent launch).
+enum { LD_RO = 0, LD_PLAIN = 1, LD_CG = 2 };
+template <int F, int POLICY>
 __device__ __forceinline__ void load_chunks(const unsigned char* p, long long plane_stride,
                                             typename FmtInfo<F>::Chunk* c) {
   using C = typename FmtInfo<F>::Chunk;
 #pragma unroll
   for (int pl = 0; pl < FmtInfo<F>::PLANES; ++pl) {
     const C* q = reinterpret_cast<const C*>(p + pl * plane_stride);
-    c[pl] = RO ? __ldg(q) : *q;
+    c[pl] = POLICY == LD_RO ? __ldg(q) : (POLICY == LD_CG ? __ldcg(q) : *q);
   }
 }
 

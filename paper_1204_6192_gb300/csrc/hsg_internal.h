@@ -105,6 +105,16 @@ struct ConvParams {
   uint32_t seed_lo, seed_hi;
 };
 
+struct PersistParams {
+  SweepParams sw;           // parity and sweep offset set per phase inside the kernel
+  EnergyParams en;
+  PTParams pt;
+  unsigned int* bar;        // [0] arrivals, [1] generation, [2] error word
+  unsigned long long timeout_ns;
+  int n_steps, nhb, nor;
+  int drop_first;           // fault injection: block 0 skips the first barrier
+};
+
 // launchers (hsg_kernels*.cu)
 cudaError_t launch_half_sweep(int fmt, bool hb, bool j16, bool fast, bool energy,
                               const SweepParams& p, int n_blocks, cudaStream_t st);
@@ -114,6 +124,9 @@ cudaError_t launch_pt(const PTParams& p, cudaStream_t st);
 cudaError_t launch_bump(unsigned long long* counters, int sweeps, int pts, cudaStream_t st);
 cudaError_t launch_measure(int fmt, const MeasureParams& p, int lmax, cudaStream_t st);
 cudaError_t launch_init(int fmt, const ConvParams& p, int n_blocks, cudaStream_t st);
+cudaError_t max_persistent_grid(int fmt, bool j16, bool fast, size_t smem, int* grid);
+cudaError_t launch_persistent(int fmt, bool j16, bool fast, const PersistParams& P, int grid,
+                              size_t smem, cudaStream_t st);
 cudaError_t launch_get(int fmt, const ConvParams& p, int n_blocks, cudaStream_t st);
 cudaError_t launch_set(int fmt, const ConvParams& p, int n_blocks, cudaStream_t st);
 

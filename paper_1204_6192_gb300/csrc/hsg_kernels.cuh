@@ -1,0 +1,258 @@
+// Device bodies shared by the per-phase kernels and the persistent step
+// kernel: one block's share of a half-sweep (Sec. 3.1, Eqs. 2-3), one unit of
+// the FP64 energy reduction (Eq. 1) and one parallel-tempering chain (Eq. 4).
+#pragma once
+
+#include "hsg_device.cuh"
+#include "hsg_internal.h"
+
+namespace hsg {
+
+// One block's share of a half-sweep: virtual block `bidx` of the sweep block
+// table.  CG: every load of data written during the launch bypasses L1 (for
+// the persistent kernel, whose blocks see each other's writes across grid
+// barriers).  esum: shared memory [SWEEP_BS / 32][GPT * VEC] (EN only).
+template <int F, bool HB, bool J16, bool FAST, bool EN, bool CG>
+__device__ __forceinline__ void sweep_block(const SweepParams& p, int bidx, float* esum) {
+  constexpr int VEC = FmtInfo<F>::VEC, PL = FmtInfo<F>::PLANES;
+  using Chunk = typename FmtInfo<F>::Chunk;
+  const int4 blk = p.blocks[bidx];
+  const SampleDev& sd = p.samples[blk.x];
+  const uint32_t h = (uint32_t)blk.z + threadIdx.x;
+  const uint32_t half_n = (uint32_t)sd.N >> 1;
+  const bool active = h < half_n;
+  if (!EN && !active) return;
+  const int g0 = blk.y * p.GPT;
+  const int g1 = min(p.G, g0 + p.GPT);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  SiteGeom gm;
+  float j6[6], h3[3];
+  uint32_t jh[6];                                  // FP16 couplings, broadcast pairs
+  constexpr bool MIXED = (F == FMT_F16) && J16;
+  long long nb_off[6], own_off = 0;
+  const unsigned char* base = p.spins + sd.spin_off;
+  const long long ps = sd.plane_stride;
+  const long long gstride = (long long)sd.N * FmtInfo<F>::CHUNK;
+  if (active) {
+    gm = site_geom(sd, h, p.parity);
+    load_record<J16>(p.rec, sd.rec_off + gm.own, j6, h3);
+    if (MIXED) load_record_j16(p.rec, sd.rec_off + gm.own, jh);
+#pragma unroll
+    for (int n = 0; n < 6; ++n) nb_off[n] = chunk_offset<F>(sd, g0, gm.nb[n]);
+    own_off = chunk_offset<F>(sd, g0, gm.own);
+  }
+  const uint32_t sweep =
+      HB ? (uint32_t)((CG ? __ldcg(p.counters) : p.counters[0]) + (unsigned long long)p.sweep_offset)
+         : 0u;
+
+  for (int g = g0; g < g1; ++g) {
+    float e[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) e[v] = 0.0f;
+    if (active) {
+      const long long dg = (long long)(g - g0) * gstride;
+      Chunk nc[6][PL];
+#pragma unroll
+      for (int n = 0; n < 6; ++n) load_chunks<F, CG ? LD_CG : LD_RO>(base + nb_off[n] + dg, ps, nc[n]);
+      unsigned char* own_p = p.spins + sd.spin_off + own_off + dg;
+      Chunk c[PL];
+      load_chunks<F, CG ? LD_CG : LD_PLAIN>(own_p, ps, c);
+
+      // local field h = sum_n J_n s_n + H, in the order +x, -x, +y, -y, +z, -z
+      Spins<VEC> hf;
+      if constexpr (MIXED) {
+        // FP16 spins and couplings: fused f16 x f16 + f32, bit-identical to
+        // multiply-then-add because the products are exact
+#pragma unroll
+        for (int k = 0; k < VEC / 2; ++k) {
+          hf.x[k] = make_float2(0.0f, 0.0f);
+          hf.y[k] = make_float2(0.0f, 0.0f);
+          hf.z[k] = make_float2(0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int n = 0; n < 6; ++n) {
+          fma_f16_pair(hf.x[0], nc[n][0].x, jh[n]);
+          fma_f16_pair(hf.x[1], nc[n][0].y, jh[n]);
+          fma_f16_pair(hf.y[0], nc[n][1].x, jh[n]);
+          fma_f16_pair(hf.y[1], nc[n][1].y, jh[n]);
+          fma_f16_pair(hf.z[0], nc[n][2].x, jh[n]);
+          fma_f16_pair(hf.z[1], nc[n][2].y, jh[n]);
+        }
+      } else {
+        {
+          Spins<VEC> nb;
+          decode<F>(nc[0], nb);
+          const float2 jj = f2(j6[0]);
+#pragma unroll
+          for (int k = 0; k < VEC / 2; ++k) {
+            hf.x[k] = mul2(jj, nb.x[k]);
+            hf.y[k] = mul2(jj, nb.y[k]);
+            hf.z[k] = mul2(jj, nb.z[k]);
+          }
+        }
+#pragma unroll
+        for (int n = 1; n < 6; ++n) {
+          Spins<VEC> nb;
+          decode<F>(nc[n], nb);
+          const float2 jj = f2(j6[n]);
+#pragma unroll
+          for (int k = 0; k < VEC / 2; ++k) {
+            hf.x[k] = add2(hf.x[k], mul2(jj, nb.x[k]));
+            hf.y[k] = add2(hf.y[k], mul2(jj, nb.y[k]));
+            hf.z[k] = add2(hf.z[k], mul2(jj, nb.z[k]));
+          }
+        }
+      }
+      {
+        const float2 hx = f2(h3[0]), hy = f2(h3[1]), hz = f2(h3[2]);
+#pragma unroll
+        for (int k = 0; k < VEC / 2; ++k) {
+          hf.x[k] = add2(hf.x[k], hx);
+          hf.y[k] = add2(hf.y[k], hy);
+          hf.z[k] = add2(hf.z[k], hz);
+        }
+      }
+
+      Spins<VEC> s;
+      decode<F>(c, s);
+      if (HB) {
+        const uint32_t sys0 = (uint32_t)sd.sys_base + (uint32_t)g * VEC;   // even
+        const float* beta = p.beta + (long long)blk.x * p.Wp + g * VEC;
+        float bt[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) bt[v] = CG ? __ldcg(beta + v) : beta[v];
+#pragma unroll
+        for (int k = 0; k < VEC / 2; ++k) {
+          const uint4 r = philox4x32_10(make_uint4(gm.site, (sys0 >> 1) + k, sweep, TAG_HB),
+                                        p.seed_lo, p.seed_hi);
+          hb_move<FAST>(s.x[k].x, s.y[k].x, s.z[k].x, hf.x[k].x, hf.y[k].x, hf.z[k].x,
+                        bt[2 * k], u01(r.x), u01(r.y));
+          hb_move<FAST>(s.x[k].y, s.y[k].y, s.z[k].y, hf.x[k].y, hf.y[k].y, hf.z[k].y,
+                        bt[2 * k + 1], u01(r.z), u01(r.w));
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < VEC / 2; ++k) or_move2(s.x[k], s.y[k], s.z[k], hf.x[k], hf.y[k], hf.z[k]);
+      }
+      encode<F>(s, c);
+      store_chunks<F>(own_p, ps, c);
+
+      if (EN) {
+        // energy of the new state from the stored values: every bond joins one
+        // odd and one even site, E = - sum_odd s_i.h_i - sum_even H_j.s_j
+        Spins<VEC> st;
+        decode<F>(c, st);
+#pragma unroll
+        for (int k = 0; k < VEC / 2; ++k) {
+          float2 d;
+          if (p.parity == 1) {
+            d = add2(add2(mul2(st.x[k], hf.x[k]), mul2(st.y[k], hf.y[k])), mul2(st.z[k], hf.z[k]));
+          } else {
+            d = add2(add2(mul2(st.x[k], f2(h3[0])), mul2(st.y[k], f2(h3[1]))),
+                     mul2(st.z[k], f2(h3[2])));
+          }
+          e[2 * k] = -d.x;
+          e[2 * k + 1] = -d.y;
+        }
+      }
+    }
+    if (EN) {
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) {
+        const float t = warp_sum(e[v]);
+        if (lane == 0) esum[warp * p.GPT * VEC + (g - g0) * VEC + v] = t;
+      }
+    }
+  }
+  if (EN) {
+    __syncthreads();
+    double* out = p.epart + ((long long)p.parity * p.n_blocks + bidx) * p.Wp;
+    for (int j = threadIdx.x; j < p.Wp; j += SWEEP_BS) {
+      double acc = 0.0;
+      const int jj = j - g0 * VEC;
+      if (jj >= 0 && jj < (g1 - g0) * VEC) {
+        for (int w = 0; w < SWEEP_BS / 32; ++w) acc += (double)esum[w * p.GPT * VEC + jj];
+      }
+      out[j] = acc;
+    }
+    __syncthreads();   // esum is reused by the next virtual block of this block
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 energy sums.  Level 1: split `split` of the sample's block rows, systems
+// 32*wg .. 32*wg+31, on 256 threads = 32 systems x 8 row lanes.  Level 2: the
+// splits of one system.  Fixed order throughout.
+// ---------------------------------------------------------------------------
+template <bool CG>
+__device__ __forceinline__ void energy_final1_unit(const EnergyParams& p, int s, int wg, int split,
+                                                   double (*red)[32]) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int w = wg * 32 + tx;
+  const SampleDev& sd = p.samples[s];
+  const int nrows = sd.blk1 - sd.blk0;
+  const int per = (nrows + p.splits - 1) / p.splits;
+  const int r0 = sd.blk0 + split * per;
+  const int r1 = min(r0 + per, sd.blk1);
+  double acc = 0.0;
+  if (w < p.Wp) {
+    for (int r = r0 + ty; r < r1; r += 8) {
+      const double* a = p.partials + (long long)r * p.Wp + w;
+      const double* b = p.partials + ((long long)p.n_blocks + r) * p.Wp + w;
+      acc += CG ? __ldcg(a) : *a;
+      acc += CG ? __ldcg(b) : *b;
+    }
+  }
+  red[ty][tx] = acc;
+  __syncthreads();
+  if (ty == 0 && w < p.Wp) {
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += red[k][tx];
+    p.partials2[((long long)s * p.splits + split) * p.Wp + w] = t;
+  }
+  __syncthreads();
+}
+
+template <bool CG>
+__device__ __forceinline__ void energy_final2_unit(const EnergyParams& p, int s, int w) {
+  double e = 0.0;
+  for (int k = 0; k < p.splits; ++k) {
+    const double* a = p.partials2 + ((long long)s * p.splits + k) * p.Wp + w;
+    e += CG ? __ldcg(a) : *a;
+  }
+  p.E[(long long)s * p.Wp + w] = e;
+}
+
+// Parallel tempering, Eq. (4), for chain c = (sample, replica): pairs (k, k+1)
+// from the lowest temperature up, accepted with min[1, exp(dbeta dE)]; an
+// accepted exchange swaps the temperatures of the two configurations; then
+// the chain's systems get their new inverse temperatures.
+template <bool CG>
+__device__ __forceinline__ void pt_chain(const PTParams& p, int c, uint32_t step) {
+  const int s = c / p.R_O, r = c - s * p.R_O;
+  int* perm = p.perm + (long long)c * p.R_T;
+  const double* E = p.E + (long long)s * p.Wp + r * p.R_T;
+  const double* ib = p.inv_temps + (long long)s * p.R_T;
+  if (p.bump_pt) {
+    for (int k = 0; k + 1 < p.R_T; ++k) {
+      const int a = perm[k], b = perm[k + 1];
+      const double dbeta = ib[k + 1] - ib[k];
+      const double dE = (CG ? __ldcg(E + b) : E[b]) - (CG ? __ldcg(E + a) : E[a]);
+      const double x = dbeta * dE;
+      const uint4 rnd = philox4x32_10(make_uint4((uint32_t)k, (uint32_t)c, step, TAG_PT),
+                                      p.seed_lo, p.seed_hi);
+      const double u = (double)u01(rnd.x);
+      const bool acc = (x >= 0.0) || (u < exp(x));
+      if (acc) {
+        perm[k] = b;
+        perm[k + 1] = a;
+        p.accepted[(long long)c * (p.R_T - 1) + k] += 1ull;
+      }
+    }
+  }
+  float* beta = p.beta + (long long)s * p.Wp + r * p.R_T;
+  for (int t = 0; t < p.R_T; ++t) beta[perm[t]] = (float)ib[t];
+}
+
+}  // namespace hsg

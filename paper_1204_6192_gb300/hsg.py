@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "libhsg.so")
 PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2, "angle16": 3, "oct16": 4}
 STATUS = {0: "HSG_OK", 1: "HSG_EINVAL", 2: "HSG_ENOMEM", 3: "HSG_ECUDA", 4: "HSG_ETIMEOUT",
           5: "HSG_ESTATE"}
-VARIANT_AUTO, VARIANT_TWO_PASS, VARIANT_RESIDENT = 0, 1, 2
+VARIANT_AUTO, VARIANT_TWO_PASS, VARIANT_PERSISTENT = 0, 1, 2
 
 
 class HsgError(RuntimeError):
@@ -33,7 +33,8 @@ class HsgError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("j_fp16", ctypes.c_int), ("fast_math", ctypes.c_int),
                 ("n_hb_per_step", ctypes.c_int), ("n_or_per_step", ctypes.c_int),
-                ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("variant", ctypes.c_int)]
+                ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("variant", ctypes.c_int),
+                ("barrier_timeout_ms", ctypes.c_int), ("inject_barrier_fault", ctypes.c_int)]
 
 
 class Obs(ctypes.Structure):
@@ -48,7 +49,7 @@ class Info(ctypes.Structure):
                 ("total_sites", ctypes.c_longlong), ("total_spins", ctypes.c_longlong),
                 ("spin_bytes", ctypes.c_longlong), ("rec_bytes", ctypes.c_longlong),
                 ("sweep_count", ctypes.c_uint64), ("pt_count", ctypes.c_uint64),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("chunks_per_thread", ctypes.c_int)]
 
 
 _lib = None
@@ -118,7 +119,8 @@ class Context:
 
     def __init__(self, samples: Sequence, n_replicas: int, seed: int, precision: str = "fp32",
                  j_fp16: bool = False, fast_math: bool = False, n_hb: int = 1, n_or: int = 5,
-                 device: int = 0, stream: Optional[int] = None, variant: int = VARIANT_AUTO):
+                 device: int = 0, stream: Optional[int] = None, variant: int = VARIANT_AUTO,
+                 barrier_timeout_ms: int = 2000, inject_barrier_fault: bool = False):
         L = lib()
         self._ctx = ctypes.c_void_p()
         opt = default_options()
@@ -130,6 +132,8 @@ class Context:
         opt.device = device
         opt.stream = stream
         opt.variant = variant
+        opt.barrier_timeout_ms = barrier_timeout_ms
+        opt.inject_barrier_fault = int(bool(inject_barrier_fault))
         self.samples = list(samples)
         self.n_samples = len(self.samples)
         self.n_temps = len(self.samples[0].temps)

@@ -312,3 +312,70 @@ def test_invalid_arguments_rejected():
         ctx.sweep_or(-1)
     ctx.sweep_or(1)       # an argument error is not sticky
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_persistent_schedule_bit_identical(precision):
+    """The persistent step kernel (one cooperative launch, grid barriers) runs
+    the same arithmetic as the per-phase graph: identical spins, energies and
+    permutations, here for a batch of three lattice sizes."""
+    samples = [inputs.small_sample(L, n_temps=4, h_r=0.2, disorder_seed=L) for L in (4, 8, 12)]
+    out = {}
+    for variant in (hsg.VARIANT_TWO_PASS, hsg.VARIANT_PERSISTENT):
+        ctx = hsg.Context(samples, 2, 6, precision=precision, j_fp16=precision != "fp32",
+                          variant=variant)
+        assert ctx.info().variant == variant
+        ctx.step(2)
+        ctx.step(3)
+        out[variant] = ([s.copy() for s in ctx.get_spins()], ctx.last_energies(), ctx.get_perm(),
+                        ctx.info().sweep_count, ctx.info().pt_count)
+        ctx.close()
+    a, b = out[hsg.VARIANT_TWO_PASS], out[hsg.VARIANT_PERSISTENT]
+    for x, y in zip(a[0], b[0]):
+        np.testing.assert_array_equal(x, y)
+    np.testing.assert_array_equal(a[1], b[1])
+    np.testing.assert_array_equal(a[2], b[2])
+    assert a[3] == b[3] == 30 and a[4] == b[4] == 5
+
+
+def test_persistent_barrier_timeout_is_reported():
+    """A block that never arrives at a grid barrier: the other blocks' bounded
+    waits run out, the launch ends, and the host gets HSG_ETIMEOUT; the device
+    stays usable for a new context."""
+    smp = inputs.small_sample(8, n_temps=4)
+    ctx = hsg.Context([smp], 2, 1, variant=hsg.VARIANT_PERSISTENT, barrier_timeout_ms=200,
+                      inject_barrier_fault=True)
+    ctx.step(1)
+    with pytest.raises(hsg.HsgError) as ei:
+        ctx.sync()
+    assert ei.value.status == 4
+    with pytest.raises(hsg.HsgError):          # sticky
+        ctx.step(1)
+    ctx.close()
+    ctx = hsg.Context([smp], 2, 1, variant=hsg.VARIANT_PERSISTENT)
+    ctx.step(2)
+    ctx.sync()
+    assert ctx.info().pt_count == 2
+    ctx.close()
+
+
+def test_autotuned_schedule_matches_fixed_schedule():
+    """The automatic schedule times the candidates on the live context at the
+    first step and restores the state: the trajectory equals the one of a
+    fixed two-pass context bit for bit."""
+    samples = [inputs.small_sample(L, n_temps=4, h_r=0.2, disorder_seed=L) for L in (6, 10)]
+    runs = []
+    for variant in (hsg.VARIANT_AUTO, hsg.VARIANT_TWO_PASS):
+        ctx = hsg.Context(samples, 2, 8, precision="fp16", j_fp16=True, variant=variant)
+        ctx.sweep_hb(1)
+        ctx.step(3)
+        info = ctx.info()
+        assert info.variant in (hsg.VARIANT_TWO_PASS, hsg.VARIANT_PERSISTENT)
+        assert 1 <= info.chunks_per_thread <= info.Wp // 4
+        assert info.sweep_count == 19 and info.pt_count == 3
+        runs.append(([s.copy() for s in ctx.get_spins()], ctx.get_perm(), ctx.last_energies()))
+        ctx.close()
+    for x, y in zip(runs[0][0], runs[1][0]):
+        np.testing.assert_array_equal(x, y)
+    np.testing.assert_array_equal(runs[0][1], runs[1][1])
+    np.testing.assert_array_equal(runs[0][2], runs[1][2])
