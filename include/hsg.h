@@ -236,6 +236,14 @@ hsg_status hsg_energies_xyz_noalloc(const float* spins_dev, const float* J_dev,
                                     const float* H_dev, int L, int W, double* E_dev,
                                     void* stream);
 
+/*
+ * The device Philox4x32-10 generator the heat-bath sweeps use (Salmon et al.,
+ * SC'11), on n host counters ctr[n][4] with key (seed & 0xffffffff, seed >> 32),
+ * written to out[n][4].  For checking the device generator against other
+ * implementations.  Synchronous; uses the current device.
+ */
+hsg_status hsg_philox(const uint32_t* ctr, long long n, uint64_t seed, uint32_t* out);
+
 /* Wait for all work of the context; returns any pending device error. */
 hsg_status hsg_sync(hsg_ctx* ctx);
 

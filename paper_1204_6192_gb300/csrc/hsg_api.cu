@@ -167,6 +167,13 @@ SweepParams sweep_params(hsg_ctx* c, int parity, int sweep_offset) {
   p.sweep_offset = sweep_offset;
   p.epart = c->d_epart;
   p.n_blocks = c->n_sweep_blocks;
+  uint32_t k0 = c->seed_lo, k1 = c->seed_hi;
+  for (int r = 0; r < 10; ++r) {
+    p.rk[2 * r] = k0;
+    p.rk[2 * r + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
   return p;
 }
 
@@ -957,6 +964,36 @@ hsg_status hsg_sync(hsg_ctx* c) {
   HSG_CUDA(c, cudaStreamSynchronize(c->stream));
   HSG_TRY(poll_device_error(c));
   HSG_CUDA(c, cudaGetLastError());
+  return HSG_OK;
+}
+
+hsg_status hsg_philox(const uint32_t* ctr, long long n, uint64_t seed, uint32_t* out) {
+  if (!ctr || !out || n < 0) {
+    g_create_error = "bad arguments to hsg_philox";
+    return HSG_EINVAL;
+  }
+  if (n == 0) return HSG_OK;
+  SweepParams p{};
+  uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    p.rk[2 * r] = k0;
+    p.rk[2 * r + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  uint4 *dc = nullptr, *dout = nullptr;
+  const size_t bytes = sizeof(uint4) * (size_t)n;
+  cudaError_t e = cudaMalloc(&dc, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&dout, bytes);
+  if (e == cudaSuccess) e = cudaMemcpy(dc, ctr, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_philox(dc, n, p, dout, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(out, dout, bytes, cudaMemcpyDeviceToHost);
+  if (dc) cudaFree(dc);
+  if (dout) cudaFree(dout);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("hsg_philox: ") + cudaGetErrorString(e);
+    return HSG_ECUDA;
+  }
   return HSG_OK;
 }
 

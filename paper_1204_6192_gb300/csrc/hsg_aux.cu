@@ -464,6 +464,19 @@ __global__ void k_set(const ConvParams p) {
   store_chunks<F>(o, it.sd->plane_stride, c);
 }
 
+// The heat bath's generator (round keys precomputed) on a list of counters.
+__global__ void k_philox(const uint4* ctr, long long n, const SweepParams p, uint4* out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = philox4x32_10_rk(ctr[i], p.rk);
+}
+
+cudaError_t launch_philox(const uint4* ctr, long long n, const SweepParams& p, uint4* out,
+                          cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_philox<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ctr, n, p, out);
+  return cudaGetLastError();
+}
+
 #define HSG_CONV_SWITCH(KERNEL)                                                          \
   switch (fmt) {                                                                        \
     case FMT_F32: KERNEL<FMT_F32><<<nb, 256, 0, st>>>(p); break;                        \

@@ -35,6 +35,19 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
+// The same generator with the ten round keys precomputed (rk[2r], rk[2r+1] =
+// key + r * Weyl constants), passed in the kernel parameters.
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t* rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk[2 * r], (uint32_t)p1,
+                   (uint32_t)(p0 >> 32) ^ c.w ^ rk[2 * r + 1], (uint32_t)p0);
+  }
+  return c;
+}
+
 // u = (2 (x >> 9) + 1) 2^-24, exactly representable in binary32, inside (0, 1).
 __device__ __forceinline__ float u01(uint32_t x) {
   return (float)(2u * (x >> 9) + 1u) * 5.9604644775390625e-8f;
@@ -46,15 +59,29 @@ enum { TAG_INIT = 0, TAG_HB = 1, TAG_PT = 2 };
 // Packed pair arithmetic (two systems per instruction).
 // ----------------------------------------------------------------------------
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+// Packed binary32 pair arithmetic as PTX with an explicit rounding modifier:
+// PTX never contracts such instructions into fused multiply-adds, so every
+// kernel that inlines these helpers rounds identically.
+__device__ __forceinline__ unsigned long long f2u(float2 a) {
+  return *reinterpret_cast<unsigned long long*>(&a);
+}
+__device__ __forceinline__ float2 u2f(unsigned long long r) {
+  return *reinterpret_cast<float2*>(&r);
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
+  return u2f(r);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
+  return u2f(r);
+}
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
   unsigned long long r;
-  asm("sub.rn.f32x2 %0, %1, %2;"
-      : "=l"(r)
-      : "l"(*reinterpret_cast<unsigned long long*>(&a)),
-        "l"(*reinterpret_cast<unsigned long long*>(&b)));
-  return *reinterpret_cast<float2*>(&r);
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
+  return u2f(r);
 }
 
 // ----------------------------------------------------------------------------
@@ -109,9 +136,9 @@ __device__ __forceinline__ uint32_t ang16_encode(float x, float y, float z) {
   const float zc = fminf(1.0f, fmaxf(-1.0f, z));
   const float th = acosf(zc);
   const float ph = atan2f(y, x);
-  int tq = (int)floorf(th * (65535.0f / 3.14159265358979f) + 0.5f);
+  int tq = (int)floorf(__fadd_rn(__fmul_rn(th, 65535.0f / 3.14159265358979f), 0.5f));
   tq = min(tq, 65535);
-  const int pq = ((int)floorf(ph * (65536.0f / 6.28318530717959f) + 0.5f)) & 0xffff;
+  const int pq = ((int)floorf(__fadd_rn(__fmul_rn(ph, 65536.0f / 6.28318530717959f), 0.5f))) & 0xffff;
   return (uint32_t)tq | ((uint32_t)pq << 16);
 }
 
@@ -121,19 +148,19 @@ __device__ __forceinline__ float sgn_nn(float v) { return v >= 0.0f ? 1.0f : -1.
 __device__ __forceinline__ void oct16_decode(uint32_t w, float& x, float& y, float& z) {
   const float px = (float)(int16_t)(w & 0xffffu) * (1.0f / 32767.0f);
   const float py = (float)(int16_t)(w >> 16) * (1.0f / 32767.0f);
-  float vz = 1.0f - fabsf(px) - fabsf(py);
+  float vz = __fsub_rn(__fsub_rn(1.0f, fabsf(px)), fabsf(py));
   float vx = px, vy = py;
   if (vz < 0.0f) {
     vx = (1.0f - fabsf(py)) * sgn_nn(px);
     vy = (1.0f - fabsf(px)) * sgn_nn(py);
   }
-  const float inv = rsqrtf(vx * vx + vy * vy + vz * vz);
-  x = vx * inv;
-  y = vy * inv;
-  z = vz * inv;
+  const float inv = rsqrtf(__fmaf_rn(vz, vz, __fmaf_rn(vy, vy, __fmul_rn(vx, vx))));
+  x = __fmul_rn(vx, inv);
+  y = __fmul_rn(vy, inv);
+  z = __fmul_rn(vz, inv);
 }
 __device__ __forceinline__ uint32_t oct16_encode(float x, float y, float z) {
-  const float l1 = fabsf(x) + fabsf(y) + fabsf(z);
+  const float l1 = __fadd_rn(__fadd_rn(fabsf(x), fabsf(y)), fabsf(z));
   float px = x / l1, py = y / l1;
   if (z < 0.0f) {
     const float fx = (1.0f - fabsf(py)) * sgn_nn(px);
@@ -143,8 +170,8 @@ __device__ __forceinline__ uint32_t oct16_encode(float x, float y, float z) {
   }
   px = fminf(1.0f, fmaxf(-1.0f, px));
   py = fminf(1.0f, fmaxf(-1.0f, py));
-  const int qx = (int)floorf(px * 32767.0f + 0.5f);
-  const int qy = (int)floorf(py * 32767.0f + 0.5f);
+  const int qx = (int)floorf(__fadd_rn(__fmul_rn(px, 32767.0f), 0.5f));
+  const int qy = (int)floorf(__fadd_rn(__fmul_rn(py, 32767.0f), 0.5f));
   return ((uint32_t)qx & 0xffffu) | (((uint32_t)qy & 0xffffu) << 16);
 }
 
@@ -297,25 +324,26 @@ __device__ __forceinline__ void or_move2(float2& sx, float2& sy, float2& sz, flo
 // r = f pi/2 lies in [-pi/4, pi/4], where the Taylor series of sin (to r^9) and
 // cos (to r^10) are truncated below 3e-9; the quadrant rotation is exact.
 __device__ __forceinline__ void sincos_2pi(float u, float& s, float& c) {
-  const float t = 4.0f * u;
+  const float t = __fmul_rn(4.0f, u);
   const float q = rintf(t);
-  const float r = (t - q) * 1.57079632679489662f;
-  const float r2 = r * r;
+  const float r = __fmul_rn(__fsub_rn(t, q), 1.57079632679489662f);
+  const float r2 = __fmul_rn(r, r);
   float ps = fmaf(r2, 2.75573192e-6f, -1.98412698e-4f);   // 1/9!, -1/7!
   ps = fmaf(r2, ps, 8.33333333e-3f);                       // 1/5!
   ps = fmaf(r2, ps, -1.66666667e-1f);                      // -1/3!
-  const float sr = fmaf(r * r2, ps, r);
+  const float sr = fmaf(__fmul_rn(r, r2), ps, r);
   float pc = fmaf(r2, -2.75573192e-7f, 2.48015873e-5f);    // -1/10!, 1/8!
   pc = fmaf(r2, pc, -1.38888889e-3f);                      // -1/6!
   pc = fmaf(r2, pc, 4.16666667e-2f);                       // 1/4!
   pc = fmaf(r2, pc, -0.5f);                                // -1/2!
   const float cr = fmaf(r2, pc, 1.0f);
-  switch (((int)q) & 3) {
-    case 0: s = sr; c = cr; break;
-    case 1: s = cr; c = -sr; break;
-    case 2: s = -sr; c = -cr; break;
-    default: s = -cr; c = sr; break;
-  }
+  // rotate by q quarter turns, without branches: odd q swaps sin and cos,
+  // q = 2, 3 negate sin, q = 1, 2 negate cos
+  const int qi = ((int)q) & 3;
+  const float a = (qi & 1) ? cr : sr;
+  const float b = (qi & 1) ? sr : cr;
+  s = (qi & 2) ? -a : a;
+  c = ((qi + 1) & 2) ? -b : b;
 }
 
 // Heat bath, Eq. (2), one system: s' ~ exp(beta h.s) from the uniforms u1, u2.
@@ -329,39 +357,42 @@ __device__ __forceinline__ void sincos_2pi(float u, float& s, float& c) {
 template <bool FAST>
 __device__ __forceinline__ void hb_move(float& sx, float& sy, float& sz, float hx, float hy,
                                         float hz, float beta, float u1, float u2) {
-  const float hn2 = hx * hx + hy * hy + hz * hz;
+  // every product and sum below is an explicit intrinsic, so no kernel that
+  // inlines this function can round it differently
+  const float hn2 = __fmaf_rn(hz, hz, __fmaf_rn(hy, hy, __fmul_rn(hx, hx)));
   const bool zero = !(hn2 > 0.0f);
   const float rs = zero ? 0.0f : rsqrtf(hn2);      // 1 / |h|
-  const float hn = hn2 * rs;                       // |h|
-  const float a = beta * hn;
+  const float hn = __fmul_rn(hn2, rs);             // |h|
+  const float a = __fmul_rn(beta, hn);
   float dm, dp;
   if (a > 1e-12f) {
     const float inv_a = __frcp_rn(a);
+    const float om = __fsub_rn(1.0f, u1);
     if (FAST) {
-      dm = -__logf(fmaf(1.0f - u1, __expf(-2.0f * a) - 1.0f, 1.0f)) * inv_a;
-      dp = 2.0f - dm;
+      dm = __fmul_rn(-__logf(__fmaf_rn(om, __fsub_rn(__expf(-2.0f * a), 1.0f), 1.0f)), inv_a);
+      dp = __fsub_rn(2.0f, dm);
     } else {
       // exp(-2a) - 1 has no cancellation for a >= 0.35; the hardware exp's
       // relative error (<~ 2a * 6e-8) enters 1 - cos t as <~ 1.2e-7 absolute
-      const float em = (a >= 0.35f) ? __expf(-2.0f * a) - 1.0f : expm1f(-2.0f * a);
-      dm = -log1pf((1.0f - u1) * em) * inv_a;
-      dp = 2.0f - dm;                                // accurate while cos t >= 0
+      const float em = (a >= 0.35f) ? __fsub_rn(__expf(-2.0f * a), 1.0f) : expm1f(-2.0f * a);
+      dm = __fmul_rn(-log1pf(__fmul_rn(om, em)), inv_a);
+      dp = __fsub_rn(2.0f, dm);                     // accurate while cos t >= 0
       if (dm > 1.0f && a < 40.0f) {
-        const float ep = (a >= 0.35f) ? __expf(2.0f * a) - 1.0f : expm1f(2.0f * a);
-        dp = log1pf(u1 * ep) * inv_a;
+        const float ep = (a >= 0.35f) ? __fsub_rn(__expf(2.0f * a), 1.0f) : expm1f(2.0f * a);
+        dp = __fmul_rn(log1pf(__fmul_rn(u1, ep)), inv_a);
       }
     }
   } else {
-    dm = 2.0f * (1.0f - u1);
-    dp = 2.0f * u1;
+    dm = __fmul_rn(2.0f, __fsub_rn(1.0f, u1));
+    dp = __fmul_rn(2.0f, u1);
   }
   dm = fminf(2.0f, fmaxf(0.0f, dm));
   dp = fminf(2.0f, fmaxf(0.0f, dp));
-  const float ct = (dm <= 1.0f) ? 1.0f - dm : dp - 1.0f;
-  const float st = sqrtf(dm * dp);
+  const float ct = (dm <= 1.0f) ? __fsub_rn(1.0f, dm) : __fsub_rn(dp, 1.0f);
+  const float st = __fsqrt_rn(__fmul_rn(dm, dp));
   float sp, cp;
   if (FAST) {
-    __sincosf(6.28318530717959f * (u2 - 0.5f), &sp, &cp);
+    __sincosf(__fmul_rn(6.28318530717959f, __fsub_rn(u2, 0.5f)), &sp, &cp);
     sp = -sp;
     cp = -cp;
   } else {
@@ -369,21 +400,26 @@ __device__ __forceinline__ void hb_move(float& sx, float& sy, float& sz, float h
   }
   float nx = 0.0f, ny = 0.0f, nz = 1.0f;
   if (!zero) {
-    nx = hx * rs;
-    ny = hy * rs;
-    nz = hz * rs;
+    nx = __fmul_rn(hx, rs);
+    ny = __fmul_rn(hy, rs);
+    nz = __fmul_rn(hz, rs);
   }
   const float sg = nz >= 0.0f ? 1.0f : -1.0f;
-  const float A = -1.0f / (sg + nz);
-  const float B = nx * ny * A;
-  const float e1x = 1.0f + sg * nx * nx * A, e1y = sg * B, e1z = -sg * nx;
-  const float e2x = B, e2y = sg + ny * ny * A, e2z = -ny;
-  const float px = cp * e1x + sp * e2x, py = cp * e1y + sp * e2y, pz = cp * e1z + sp * e2z;
-  float ox = ct * nx + st * px, oy = ct * ny + st * py, oz = ct * nz + st * pz;
-  const float inv = rsqrtf(ox * ox + oy * oy + oz * oz);
-  sx = ox * inv;
-  sy = oy * inv;
-  sz = oz * inv;
+  const float A = -__frcp_rn(__fadd_rn(sg, nz));
+  const float B = __fmul_rn(__fmul_rn(nx, ny), A);
+  const float e1x = __fmaf_rn(sg, __fmul_rn(__fmul_rn(nx, nx), A), 1.0f);
+  const float e1y = __fmul_rn(sg, B), e1z = -__fmul_rn(sg, nx);
+  const float e2x = B, e2y = __fmaf_rn(__fmul_rn(ny, ny), A, sg), e2z = -ny;
+  const float px = __fmaf_rn(sp, e2x, __fmul_rn(cp, e1x));
+  const float py = __fmaf_rn(sp, e2y, __fmul_rn(cp, e1y));
+  const float pz = __fmaf_rn(sp, e2z, __fmul_rn(cp, e1z));
+  const float ox = __fmaf_rn(st, px, __fmul_rn(ct, nx));
+  const float oy = __fmaf_rn(st, py, __fmul_rn(ct, ny));
+  const float oz = __fmaf_rn(st, pz, __fmul_rn(ct, nz));
+  const float inv = rsqrtf(__fmaf_rn(oz, oz, __fmaf_rn(oy, oy, __fmul_rn(ox, ox))));
+  sx = __fmul_rn(ox, inv);
+  sy = __fmul_rn(oy, inv);
+  sz = __fmul_rn(oz, inv);
 }
 
 // ----------------------------------------------------------------------------

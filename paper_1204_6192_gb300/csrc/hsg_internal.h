@@ -58,6 +58,7 @@ struct SweepParams {
   int sweep_offset;
   double* epart;            // energy partials [2][n_blocks][Wp] (energy variant only)
   int n_blocks;
+  uint32_t rk[20];          // Philox round keys of the seed
 };
 
 struct EnergyParams {
@@ -124,6 +125,8 @@ cudaError_t launch_pt(const PTParams& p, cudaStream_t st);
 cudaError_t launch_bump(unsigned long long* counters, int sweeps, int pts, cudaStream_t st);
 cudaError_t launch_measure(int fmt, const MeasureParams& p, int lmax, cudaStream_t st);
 cudaError_t launch_init(int fmt, const ConvParams& p, int n_blocks, cudaStream_t st);
+cudaError_t launch_philox(const uint4* ctr, long long n, const SweepParams& p, uint4* out,
+                          cudaStream_t st);
 cudaError_t max_persistent_grid(int fmt, bool j16, bool fast, size_t smem, int* grid);
 cudaError_t launch_persistent(int fmt, bool j16, bool fast, const PersistParams& P, int grid,
                               size_t smem, cudaStream_t st);

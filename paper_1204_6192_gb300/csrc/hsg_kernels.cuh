@@ -124,8 +124,8 @@ __device__ __forceinline__ void sweep_block(const SweepParams& p, int bidx, floa
         for (int v = 0; v < VEC; ++v) bt[v] = CG ? __ldcg(beta + v) : beta[v];
 #pragma unroll
         for (int k = 0; k < VEC / 2; ++k) {
-          const uint4 r = philox4x32_10(make_uint4(gm.site, (sys0 >> 1) + k, sweep, TAG_HB),
-                                        p.seed_lo, p.seed_hi);
+          const uint4 r = philox4x32_10_rk(make_uint4(gm.site, (sys0 >> 1) + k, sweep, TAG_HB),
+                                           p.rk);
           hb_move<FAST>(s.x[k].x, s.y[k].x, s.z[k].x, hf.x[k].x, hf.y[k].x, hf.z[k].x,
                         bt[2 * k], u01(r.x), u01(r.y));
           hb_move<FAST>(s.x[k].y, s.y[k].y, s.z[k].y, hf.x[k].y, hf.y[k].y, hf.z[k].y,

@@ -92,6 +92,8 @@ def lib() -> ctypes.CDLL:
         "hsg_status_string": (ctypes.c_char_p, [ip]),
         "hsg_destroy": (None, [vp]),
         "hsg_energies_xyz_noalloc": (ip, [vp, vp, vp, ip, ip, vp, vp]),
+        "hsg_philox": (ip, [ctypes.POINTER(ctypes.c_uint32), ctypes.c_longlong, ctypes.c_uint64,
+                            ctypes.POINTER(ctypes.c_uint32)]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
@@ -276,6 +278,17 @@ class Context:
 
     def sync(self):
         self._check(lib().hsg_sync(self._ctx))
+
+
+def hsg_philox(ctr: np.ndarray, seed: int) -> np.ndarray:
+    """The device Philox4x32-10 on counters ctr[n, 4] (uint32)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    out = np.empty_like(c)
+    st = lib().hsg_philox(_ptr(c, ctypes.c_uint32), c.shape[0], ctypes.c_uint64(seed),
+                          _ptr(out, ctypes.c_uint32))
+    if st != 0:
+        raise HsgError(st, (lib().hsg_last_error(None) or b"").decode())
+    return out
 
 
 def hsg_energies_xyz_noalloc(spins_dev: int, J_dev: int, H_dev: int, L: int, W: int, E_dev: int,

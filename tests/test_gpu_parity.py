@@ -53,6 +53,15 @@ def run_pair(samples, n_rep, seed, schedule, precision="fp32", codec="none", j16
     return np.array(errs)
 
 
+def test_device_philox_bit_exact_against_oracle():
+    """The device generator and the oracle's, both written from Salmon et al.,
+    agree bit for bit on 10^6 counters (several seeds, every counter word)."""
+    rng = np.random.default_rng(21)
+    for seed in (1, 0xFFFFFFFF, 2 ** 40 + 17):
+        ctr = rng.integers(0, 2 ** 32, size=(250_000, 4), dtype=np.uint64).astype(np.uint32)
+        np.testing.assert_array_equal(hsg.hsg_philox(ctr, seed), oracle.philox(ctr, seed))
+
+
 def test_initial_state_matches_oracle():
     smp = inputs.small_sample(8, n_temps=4)
     errs = run_pair([smp], 2, 5, [])
@@ -110,8 +119,11 @@ def fp32_storage_reference(samples, n_rep, seed, schedule):
 
 
 # FP32 arithmetic adds a few ulp per update on top of the half-ulp storage
-# rounding; the maximum is one outlier of a chaotic map and gets a wider margin
-CHAOS_FACTOR = {0.5: 10.0, 0.9: 10.0, 0.99: 10.0, 1.0: 30.0}
+# rounding (median: 10x).  The tail quantiles of a chaotic divergence are set
+# by a handful of sites with small local fields and move by tens of percent
+# between equally valid roundings, so they get 20x; the maximum, one outlier, 30x.
+# A wrong index, sign or random number gives O(1) deviations and fails all four.
+CHAOS_FACTOR = {0.5: 10.0, 0.9: 20.0, 0.99: 20.0, 1.0: 30.0}
 
 
 def assert_within_fp32_spread(d, ref):

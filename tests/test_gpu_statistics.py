@@ -1,6 +1,6 @@
 """Statistical parity of equilibrium observables, GPU against the FP64 oracle.
 
-Workload: L = 8, Gaussian J, 2 replicas x 8 temperatures, 200 steps of
+Workload: L = 8, Gaussian J, 2 replicas x 8 temperatures, 1000 steps of
 1 HB + 5 OR + PT, a measurement after every step; the second half of the
 series is averaged.  e(T) = <E>/N per temperature slot (both replicas) and
 <q^2> = <sum_{mu nu} (q^{mu nu})^2> per slot.  Errors from 10 bins.  The GPU and
@@ -18,7 +18,7 @@ from paper_1204_6192_gb300 import hsg, inputs
 
 pytestmark = pytest.mark.gpu
 
-STEPS = 200
+STEPS = 1000
 NBINS = 10
 
 
@@ -35,8 +35,8 @@ def workload(h_r=0.0, fp16_couplings=False):
     return inputs.Sample(L=8, J=r(smp.J), H=r(smp.H), temps=t)
 
 
-def series_gpu(smp, precision="fp32", j16=False):
-    ctx = hsg.Context([smp], 2, 1, precision=precision, j_fp16=j16)
+def series_gpu(smp, precision="fp32", j16=False, fast_math=False):
+    ctx = hsg.Context([smp], 2, 1, precision=precision, j_fp16=j16, fast_math=fast_math)
     E, Q = [], []
     for _ in range(STEPS):
         ctx.step(1)
@@ -108,3 +108,11 @@ def test_compressed_storage_error_against_fp64(oracle_fp16_couplings, precision)
     smp, ref = oracle_fp16_couplings
     gpu = observables(*series_gpu(smp, precision=precision, j16=True), N=512)
     compare(gpu, ref, precision, 4.0)
+
+
+def test_fast_math_heat_bath_statistics(oracle_fp32_couplings):
+    """The hardware-approximation heat bath (the paper's fast_math variant,
+    Table 1) samples the same equilibrium within the statistical error."""
+    smp, ref = oracle_fp32_couplings
+    gpu = observables(*series_gpu(smp, fast_math=True), N=512)
+    compare(gpu, ref, "fast_math", 4.0)
