@@ -354,6 +354,11 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
 
+    info = ctx.info()
+    persistent = info.variant == 2
+    launches_per_step = 1 if persistent else info.n_passes * 2 * sweeps + 3
+    schedule = {"variant": "persistent" if persistent else "two_pass (CUDA graph)",
+                "chunks_per_thread": info.chunks_per_thread, "passes": info.n_passes}
     updates_rank = sweeps * spins * args.steps
     updates = updates_rank * world
     value = ms * 1e6 / updates
@@ -372,9 +377,10 @@ def main():
                    "storage": wl.precision, "couplings": "fp16" if wl.j_fp16 else "fp32",
                    "step": f"{wl.n_hb} HB + {wl.n_or} OR + energies + PT, measure every "
                            f"{args.measure_every}",
-                   "l2": "state larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+                   "l2": "state larger than L2 (no flush)", "parallelism": f"replicas x{world}",
+                   "schedule": schedule},
         "spin_updates_per_s": round(updates / (ms * 1e-3), 1),
-        "gpu_launches": args.steps * (2 * sweeps + 3) + n_meas * 4,
+        "gpu_launches": args.steps * launches_per_step + n_meas * 4,
         "roofline": {"bound": "hbm", "kernel": f"k_half_sweep OR {wl.precision}",
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_kind": peak_kind,

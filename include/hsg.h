@@ -93,6 +93,16 @@ typedef struct {
                                next synchronising call returns HSG_ETIMEOUT */
   int inject_barrier_fault; /* testing only: nonzero makes one block skip the first grid
                                barrier of the next persistent launch, so the others time out */
+  long long pass_bytes;     /* system blocking of hsg_step: the systems are cut into passes
+                               (ranges of 4-system chunks, samples kept whole where they fit)
+                               of at most this many bytes of spins plus couplings, and each
+                               pass runs all sweeps of the step before the next one, so that
+                               its later sweeps read the L2 cache.  0 (default): chosen by
+                               the automatic schedule, one pass for an explicit variant.
+                               Results do not depend on it. */
+  int chunks_per_thread;    /* sweep kernels: chunks of 4 systems one thread walks; 0
+                               (default): chosen from the problem size (and by the
+                               automatic schedule).  Results do not depend on it. */
 } hsg_options;
 
 enum {
@@ -204,6 +214,8 @@ typedef struct {
   uint64_t pt_count;       /* PT passes done */
   void* stream;            /* the cudaStream_t the context runs on */
   int chunks_per_thread;   /* sweep kernels: chunks of 4 systems one thread walks */
+  int n_passes;            /* system-blocked passes per step (1: no blocking) */
+  long long pass_bytes;    /* footprint bound of a pass in use (0: one pass) */
 } hsg_info;
 hsg_status hsg_get_info(hsg_ctx* ctx, hsg_info* info);
 

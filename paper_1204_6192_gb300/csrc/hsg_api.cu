@@ -80,6 +80,13 @@ struct hsg_ctx {
   size_t persist_smem = 0;
   bool inject_fault = false;
 
+  // system-blocked passes: a step sweeps one range of the block table (a group
+  // of systems) through all its sweeps before the next range
+  std::vector<int> pass_bound{0, 0};    // [n_passes + 1] block table bounds
+  int* d_pass_bound = nullptr;
+  long long pass_bytes = 0;             // resolved footprint bound (0: one pass)
+  int max_passes = 1;
+
   hsg_status err = HSG_OK;
   std::string msg;
   std::vector<void*> allocations;
@@ -167,6 +174,7 @@ SweepParams sweep_params(hsg_ctx* c, int parity, int sweep_offset) {
   p.sweep_offset = sweep_offset;
   p.epart = c->d_epart;
   p.n_blocks = c->n_sweep_blocks;
+  p.blk_base = 0;
   uint32_t k0 = c->seed_lo, k1 = c->seed_hi;
   for (int r = 0; r < 10; ++r) {
     p.rk[2 * r] = k0;
@@ -231,13 +239,17 @@ ConvParams conv_params(hsg_ctx* c, float* xyz, const long long* xyz_off) {
   return p;
 }
 
-// One sweep: the even half-sweep, then the odd one.  With `energy`, both
-// launches also leave the per-block energy partials of the new state.
-hsg_status half_sweeps(hsg_ctx* c, bool hb, int sweep_offset, bool energy = false) {
+// One sweep of the block table range [b0, b1) (all of it by default): the
+// even half-sweep, then the odd one.  With `energy`, both launches also leave
+// the per-block energy partials of the new state.
+hsg_status half_sweeps(hsg_ctx* c, bool hb, int sweep_offset, bool energy = false, int b0 = 0,
+                       int b1 = -1) {
+  if (b1 < 0) b1 = c->n_sweep_blocks;
   for (int parity = 0; parity < 2; ++parity) {
     SweepParams p = sweep_params(c, parity, sweep_offset);
-    HSG_CUDA(c, launch_half_sweep(c->fmt, hb, c->j16, c->opt.fast_math != 0, energy, p,
-                                  c->n_sweep_blocks, c->stream));
+    p.blk_base = b0;
+    HSG_CUDA(c, launch_half_sweep(c->fmt, hb, c->j16, c->opt.fast_math != 0, energy, p, b1 - b0,
+                                  c->stream));
   }
   return HSG_OK;
 }
@@ -249,11 +261,17 @@ hsg_status enqueue_energy(hsg_ctx* c) {
 }
 
 // A step: n_hb HB sweeps, n_or OR sweeps (the last one also produces the
-// energy partials of the final state), the energy sums and one PT pass.
+// energy partials of the final state), the energy sums and one PT pass.  The
+// sweeps run pass by pass; systems are independent and every random number is
+// keyed by (site, system, sweep), so the order of the passes changes nothing.
 hsg_status enqueue_step(hsg_ctx* c) {
   const int nhb = c->opt.n_hb_per_step, nor = c->opt.n_or_per_step;
-  for (int k = 0; k < nhb; ++k) HSG_TRY(half_sweeps(c, true, k));
-  for (int k = 0; k < nor; ++k) HSG_TRY(half_sweeps(c, false, nhb + k, k == nor - 1));
+  const int np = (int)c->pass_bound.size() - 1;
+  for (int ps = 0; ps < np; ++ps) {
+    const int b0 = c->pass_bound[ps], b1 = c->pass_bound[ps + 1];
+    for (int k = 0; k < nhb; ++k) HSG_TRY(half_sweeps(c, true, k, false, b0, b1));
+    for (int k = 0; k < nor; ++k) HSG_TRY(half_sweeps(c, false, nhb + k, k == nor - 1, b0, b1));
+  }
   if (nor > 0) {
     HSG_CUDA(c, launch_energy_final(energy_params(c), c->stream));
   } else {
@@ -283,6 +301,8 @@ PersistParams persist_params(hsg_ctx* c, int n_steps) {
   P.nhb = c->opt.n_hb_per_step;
   P.nor = c->opt.n_or_per_step;
   P.drop_first = c->inject_fault ? 1 : 0;
+  P.pass_bound = c->d_pass_bound;
+  P.n_passes = (int)c->pass_bound.size() - 1;
   return P;
 }
 
@@ -311,24 +331,49 @@ int default_gpt(hsg_ctx*, const int* L, int n_samples, int G) {
   return (int)std::max(1ll, std::min((long long)G, gpt));
 }
 
-// Build the sweep block table for `gpt` chunks per thread and set up the
-// chosen step schedule (drops a captured graph: its parameters change).
-hsg_status configure_schedule(hsg_ctx* c, int variant, int gpt) {
+// Build the sweep block table for `gpt` chunks per thread, cut it into passes
+// whose footprint (spins of their chunk groups plus the records of their
+// samples) stays within `pass_bytes` (0: one pass; a pass holds at least one
+// chunk group), and set up the chosen step schedule (drops a captured graph:
+// its parameters change).
+hsg_status configure_schedule(hsg_ctx* c, int variant, int gpt, long long pass_bytes) {
   gpt = std::max(1, std::min(c->G, gpt));
   const int n_gg = (c->G + gpt - 1) / gpt;
+  const long long site_chunk_bytes = (long long)c->PL * c->VEC * c->ELEM;
+  const long long site_rec_bytes = 12ll * (c->j16 ? 2 : 4);
   std::vector<int4> blocks;
+  std::vector<int> bounds{0};
+  long long used = 0;
+  int last_sample = -1;
   int max_rows = 1;
   for (int s = 0; s < c->ns; ++s) {
     SampleDev& d = c->sd[s];
     d.blk0 = (int)blocks.size();
-    for (int gg = 0; gg < n_gg; ++gg)
+    for (int gg = 0; gg < n_gg; ++gg) {
+      const int chunks = std::min(gpt, c->G - gg * gpt);
+      long long add = (long long)d.N * chunks * site_chunk_bytes;
+      if (s != last_sample) add += (long long)d.N * site_rec_bytes;
+      if (pass_bytes > 0 && (int)blocks.size() > bounds.back() && used + add > pass_bytes) {
+        bounds.push_back((int)blocks.size());
+        used = 0;
+        add = (long long)d.N * (chunks * site_chunk_bytes + site_rec_bytes);
+      }
+      used += add;
+      last_sample = s;
       for (int h0 = 0; h0 < d.N / 2; h0 += SWEEP_BS) blocks.push_back(make_int4(s, gg, h0, 0));
+    }
     d.blk1 = (int)blocks.size();
     max_rows = std::max(max_rows, d.blk1 - d.blk0);
   }
+  bounds.push_back((int)blocks.size());
   if ((long long)blocks.size() > c->max_sweep_blocks) return fail(c, HSG_ESTATE, "sweep table overflow");
+  if ((int)bounds.size() - 1 > c->max_passes) return fail(c, HSG_ESTATE, "pass table overflow");
   c->GPT = gpt;
   c->n_sweep_blocks = (int)blocks.size();
+  c->pass_bound = bounds;
+  c->pass_bytes = pass_bytes;
+  HSG_CUDA(c, cudaMemcpyAsync(c->d_pass_bound, bounds.data(), sizeof(int) * bounds.size(),
+                              cudaMemcpyHostToDevice, c->stream));
   c->e_splits = std::min(64, std::max(1, max_rows / 256));
   HSG_CUDA(c, cudaMemcpyAsync(c->d_sweep_blocks, blocks.data(), sizeof(int4) * blocks.size(),
                               cudaMemcpyHostToDevice, c->stream));
@@ -389,14 +434,19 @@ hsg_status run_steps(hsg_ctx* c, int n_steps) {
 // step) and the fastest is kept; the state is saved before and restored after,
 // so the Markov chain is untouched.  Results are cached per problem shape for
 // the life of the process.
+struct TuneChoice {
+  int variant, gpt;
+  long long pass_bytes;
+};
 std::mutex g_tune_mu;
-std::map<std::string, std::pair<int, int>> g_tune_cache;
+std::map<std::string, TuneChoice> g_tune_cache;
 
 std::string tune_key(hsg_ctx* c) {
   std::string k = std::to_string(c->fmt) + "/" + std::to_string(c->j16) + "/" +
                   std::to_string(c->opt.fast_math) + "/" + std::to_string(c->W) + "/" +
                   std::to_string(c->opt.n_hb_per_step) + "/" + std::to_string(c->opt.n_or_per_step) +
-                  "/L";
+                  "/" + std::to_string(c->opt.pass_bytes) + "/" +
+                  std::to_string(c->opt.chunks_per_thread) + "/L";
   for (int L : c->L) k += std::to_string(L) + ",";
   return k;
 }
@@ -407,7 +457,8 @@ hsg_status autotune(hsg_ctx* c) {
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune_cache.find(key);
-    if (it != g_tune_cache.end()) return configure_schedule(c, it->second.first, it->second.second);
+    if (it != g_tune_cache.end())
+      return configure_schedule(c, it->second.variant, it->second.gpt, it->second.pass_bytes);
   }
   // save the state the trial steps will change
   void* spins_copy = nullptr;
@@ -430,26 +481,42 @@ hsg_status autotune(hsg_ctx* c) {
   std::vector<int> gpts;
   for (int g : {c->G, (c->G + 1) / 2, (c->G + 3) / 4, 2, 1, c->GPT})
     if (g >= 1 && g <= c->G && std::find(gpts.begin(), gpts.end(), g) == gpts.end()) gpts.push_back(g);
+  if (c->opt.chunks_per_thread > 0) gpts.assign(1, c->GPT);
   cudaEvent_t e0, e1;
   HSG_CUDA(c, cudaEventCreate(&e0));
   HSG_CUDA(c, cudaEventCreate(&e1));
+  // pass footprints: one pass, and passes that fit the L2 cache (then every
+  // sweep of a pass after the first reads its spins and records from L2)
+  std::vector<long long> budgets;
+  if (c->opt.pass_bytes > 0) {
+    budgets.push_back(c->opt.pass_bytes);
+  } else {
+    int l2 = 0;
+    HSG_CUDA(c, cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device));
+    budgets.push_back(0);
+    if (l2 > 0 && (long long)c->spin_bytes + (long long)c->rec_bytes > l2 / 2) {
+      budgets.push_back((long long)l2 * 3 / 4);
+      budgets.push_back((long long)l2 / 2);
+    }
+  }
   float best = 1e30f;
-  int best_v = HSG_VARIANT_TWO_PASS, best_g = c->GPT;
-  for (int v : {HSG_VARIANT_TWO_PASS, HSG_VARIANT_PERSISTENT}) {
-    for (int g : gpts) {
-      HSG_TRY(configure_schedule(c, v, g));
-      HSG_TRY(run_steps(c, 1));
-      HSG_CUDA(c, cudaEventRecord(e0, st));
-      HSG_TRY(run_steps(c, 2));
-      HSG_CUDA(c, cudaEventRecord(e1, st));
-      HSG_CUDA(c, cudaEventSynchronize(e1));
-      HSG_TRY(poll_device_error(c));
-      float ms = 0.0f;
-      HSG_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
-      if (ms < best) {
-        best = ms;
-        best_v = v;
-        best_g = g;
+  TuneChoice bestc{HSG_VARIANT_TWO_PASS, c->GPT, budgets[0]};
+  for (long long pb : budgets) {
+    for (int v : {HSG_VARIANT_TWO_PASS, HSG_VARIANT_PERSISTENT}) {
+      for (int g : gpts) {
+        HSG_TRY(configure_schedule(c, v, g, pb));
+        HSG_TRY(run_steps(c, 1));
+        HSG_CUDA(c, cudaEventRecord(e0, st));
+        HSG_TRY(run_steps(c, 2));
+        HSG_CUDA(c, cudaEventRecord(e1, st));
+        HSG_CUDA(c, cudaEventSynchronize(e1));
+        HSG_TRY(poll_device_error(c));
+        float ms = 0.0f;
+        HSG_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+          best = ms;
+          bestc = TuneChoice{v, g, pb};
+        }
       }
     }
   }
@@ -466,9 +533,9 @@ hsg_status autotune(hsg_ctx* c) {
   HSG_CUDA(c, cudaFree(spins_copy));
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune_cache[key] = std::make_pair(best_v, best_g);
+    g_tune_cache[key] = bestc;
   }
-  return configure_schedule(c, best_v, best_g);
+  return configure_schedule(c, bestc.variant, bestc.gpt, bestc.pass_bytes);
 }
 
 hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double* temps,
@@ -487,6 +554,8 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
     return bad_arg(nullptr, "unknown precision");
   if (opt.n_hb_per_step < 0 || opt.n_or_per_step < 0)
     return bad_arg(nullptr, "negative sweeps per step");
+  if (opt.pass_bytes < 0) return bad_arg(nullptr, "pass_bytes < 0");
+  if (opt.chunks_per_thread < 0) return bad_arg(nullptr, "chunks_per_thread < 0");
   const int W = n_temps * n_replicas;
   if (W > 1024) return bad_arg(nullptr, "n_temps * n_replicas must be <= 1024");
   const int Wp = (W + 7) / 8 * 8;
@@ -553,7 +622,8 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   // layout
   std::vector<int4> conv_blocks;
   long long max_sweep_blocks = 0;
-  c->GPT = default_gpt(c, L, n_samples, G);
+  c->GPT = opt.chunks_per_thread > 0 ? std::min(G, opt.chunks_per_thread)
+                                     : default_gpt(c, L, n_samples, G);
   size_t spin_off = 0, rec_off = 0;
   long long xyz = 0;
   for (int s = 0; s < n_samples; ++s) {
@@ -583,6 +653,7 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   c->spin_bytes = spin_off;
   c->rec_bytes = rec_off * (c->j16 ? 24 : 48);
   c->max_sweep_blocks = max_sweep_blocks;
+  c->max_passes = n_samples * G;
   c->n_conv_blocks = (int)conv_blocks.size();
 
   // records: six bonds and the field of every storage site
@@ -635,6 +706,7 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   HSG_ALLOC(c->rec, c->rec_bytes);
   HSG_ALLOC(c->d_sd, sizeof(SampleDev) * n_samples);
   HSG_ALLOC(c->d_sweep_blocks, sizeof(int4) * max_sweep_blocks);
+  HSG_ALLOC(c->d_pass_bound, sizeof(int) * (c->max_passes + 1));
   HSG_ALLOC(c->d_conv_blocks, sizeof(int4) * conv_blocks.size());
   HSG_ALLOC(c->d_epart, sizeof(double) * 2 * max_sweep_blocks * Wp);
   HSG_ALLOC(c->d_epart2, sizeof(double) * n_samples * 64 * Wp);
@@ -691,7 +763,7 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
     int want = opt.variant == HSG_VARIANT_AUTO ? HSG_VARIANT_TWO_PASS : opt.variant;
     if (opt.n_or_per_step < 1) want = HSG_VARIANT_TWO_PASS;
     c->inject_fault = opt.inject_barrier_fault != 0;
-    hsg_status st2 = configure_schedule(c, want, c->GPT);
+    hsg_status st2 = configure_schedule(c, want, c->GPT, opt.pass_bytes);
     if (st2 != HSG_OK) return cleanup_fail(st2);
   }
   ConvParams cp = conv_params(c, nullptr, nullptr);
@@ -948,6 +1020,8 @@ hsg_status hsg_get_info(hsg_ctx* c, hsg_info* info) {
   info->j_fp16 = c->j16 ? 1 : 0;
   info->variant = c->variant;
   info->chunks_per_thread = c->GPT;
+  info->n_passes = (int)c->pass_bound.size() - 1;
+  info->pass_bytes = c->pass_bytes;
   info->total_sites = c->total_sites;
   info->total_spins = c->total_sites * c->W;
   info->spin_bytes = (long long)c->spin_bytes;

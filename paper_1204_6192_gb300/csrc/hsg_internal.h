@@ -58,6 +58,7 @@ struct SweepParams {
   int sweep_offset;
   double* epart;            // energy partials [2][n_blocks][Wp] (energy variant only)
   int n_blocks;
+  int blk_base;             // block table entry of launch block 0 (a pass's first block)
   uint32_t rk[20];          // Philox round keys of the seed
 };
 
@@ -114,6 +115,8 @@ struct PersistParams {
   unsigned long long timeout_ns;
   int n_steps, nhb, nor;
   int drop_first;           // fault injection: block 0 skips the first barrier
+  const int* pass_bound;    // [n_passes + 1]: block table range of each pass
+  int n_passes;
 };
 
 // launchers (hsg_kernels*.cu)

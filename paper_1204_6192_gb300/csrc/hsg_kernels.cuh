@@ -55,6 +55,7 @@ __device__ __forceinline__ void sweep_block(const SweepParams& p, int bidx, floa
       Chunk nc[6][PL];
 #pragma unroll
       for (int n = 0; n < 6; ++n) load_chunks<F, CG ? LD_CG : LD_RO>(base + nb_off[n] + dg, ps, nc[n]);
+      // (the address of the own chunk after the neighbour loads: fewer live registers)
       unsigned char* own_p = p.spins + sd.spin_off + own_off + dg;
       Chunk c[PL];
       load_chunks<F, CG ? LD_CG : LD_PLAIN>(own_p, ps, c);

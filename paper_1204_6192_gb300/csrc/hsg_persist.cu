@@ -62,17 +62,22 @@ __global__ void __launch_bounds__(SWEEP_BS) k_persistent(const PersistParams P) 
     return grid_barrier(P.bar, P.timeout_ns);
   };
   for (int step = 0; step < P.n_steps; ++step) {
-    for (int k = 0; k < nsw; ++k) {
-      const bool hb = k < P.nhb, en = (k == nsw - 1);
-      sp.sweep_offset = k;
-      for (int parity = 0; parity < 2; ++parity) {
-        sp.parity = parity;
-        for (int b = blockIdx.x; b < sp.n_blocks; b += gridDim.x) {
-          if (hb) sweep_block<F, true, J16, FAST, false, true>(sp, b, esum);
-          else if (en) sweep_block<F, false, J16, false, true, true>(sp, b, esum);
-          else sweep_block<F, false, J16, false, false, true>(sp, b, esum);
+    // the sweeps of a step pass by pass: each pass is a range of the block
+    // table (a group of systems) swept nsw times before the next one starts
+    for (int ps = 0; ps < P.n_passes; ++ps) {
+      const int b0 = P.pass_bound[ps], b1 = P.pass_bound[ps + 1];
+      for (int k = 0; k < nsw; ++k) {
+        const bool hb = k < P.nhb, en = (k == nsw - 1);
+        sp.sweep_offset = k;
+        for (int parity = 0; parity < 2; ++parity) {
+          sp.parity = parity;
+          for (int b = b0 + (int)blockIdx.x; b < b1; b += gridDim.x) {
+            if (hb) sweep_block<F, true, J16, FAST, false, true>(sp, b, esum);
+            else if (en) sweep_block<F, false, J16, false, true, true>(sp, b, esum);
+            else sweep_block<F, false, J16, false, false, true>(sp, b, esum);
+          }
+          if (!sync()) return;
         }
-        if (!sync()) return;
       }
     }
     // energies of the final state from the partials of the last OR sweep

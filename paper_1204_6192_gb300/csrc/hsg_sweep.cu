@@ -18,7 +18,7 @@ namespace hsg {
 template <int F, bool HB, bool J16, bool FAST, bool EN>
 __global__ void __launch_bounds__(SWEEP_BS) k_half_sweep(const SweepParams p) {
   extern __shared__ float esum[];
-  sweep_block<F, HB, J16, FAST, EN, false>(p, blockIdx.x, esum);
+  sweep_block<F, HB, J16, FAST, EN, false>(p, p.blk_base + (int)blockIdx.x, esum);
 }
 
 template <int F>

@@ -34,7 +34,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("j_fp16", ctypes.c_int), ("fast_math", ctypes.c_int),
                 ("n_hb_per_step", ctypes.c_int), ("n_or_per_step", ctypes.c_int),
                 ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("variant", ctypes.c_int),
-                ("barrier_timeout_ms", ctypes.c_int), ("inject_barrier_fault", ctypes.c_int)]
+                ("barrier_timeout_ms", ctypes.c_int), ("inject_barrier_fault", ctypes.c_int),
+                ("pass_bytes", ctypes.c_longlong), ("chunks_per_thread", ctypes.c_int)]
 
 
 class Obs(ctypes.Structure):
@@ -49,7 +50,8 @@ class Info(ctypes.Structure):
                 ("total_sites", ctypes.c_longlong), ("total_spins", ctypes.c_longlong),
                 ("spin_bytes", ctypes.c_longlong), ("rec_bytes", ctypes.c_longlong),
                 ("sweep_count", ctypes.c_uint64), ("pt_count", ctypes.c_uint64),
-                ("stream", ctypes.c_void_p), ("chunks_per_thread", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("chunks_per_thread", ctypes.c_int),
+                ("n_passes", ctypes.c_int), ("pass_bytes", ctypes.c_longlong)]
 
 
 _lib = None
@@ -122,7 +124,8 @@ class Context:
     def __init__(self, samples: Sequence, n_replicas: int, seed: int, precision: str = "fp32",
                  j_fp16: bool = False, fast_math: bool = False, n_hb: int = 1, n_or: int = 5,
                  device: int = 0, stream: Optional[int] = None, variant: int = VARIANT_AUTO,
-                 barrier_timeout_ms: int = 2000, inject_barrier_fault: bool = False):
+                 barrier_timeout_ms: int = 2000, inject_barrier_fault: bool = False,
+                 pass_bytes: int = 0, chunks_per_thread: int = 0):
         L = lib()
         self._ctx = ctypes.c_void_p()
         opt = default_options()
@@ -136,6 +139,8 @@ class Context:
         opt.variant = variant
         opt.barrier_timeout_ms = barrier_timeout_ms
         opt.inject_barrier_fault = int(bool(inject_barrier_fault))
+        opt.pass_bytes = int(pass_bytes)
+        opt.chunks_per_thread = int(chunks_per_thread)
         self.samples = list(samples)
         self.n_samples = len(self.samples)
         self.n_temps = len(self.samples[0].temps)

@@ -319,6 +319,10 @@ def test_invalid_arguments_rejected():
     J[3, 1] = np.nan
     with pytest.raises(hsg.HsgError):
         hsg.Context([inputs.Sample(L=8, J=J, H=smp.H, temps=smp.temps)], 2, 1)
+    for kw in ({"pass_bytes": -1}, {"chunks_per_thread": -2}):
+        with pytest.raises(hsg.HsgError) as ei:
+            hsg.Context([smp], 2, 1, **kw)
+        assert ei.value.status == 1
     ctx = hsg.Context([smp], 2, 1)
     with pytest.raises(hsg.HsgError):
         ctx.sweep_or(-1)
@@ -348,6 +352,39 @@ def test_persistent_schedule_bit_identical(precision):
     np.testing.assert_array_equal(a[1], b[1])
     np.testing.assert_array_equal(a[2], b[2])
     assert a[3] == b[3] == 30 and a[4] == b[4] == 5
+
+
+@pytest.mark.parametrize("variant", [hsg.VARIANT_TWO_PASS, hsg.VARIANT_PERSISTENT])
+@pytest.mark.parametrize("pass_bytes", [1, 40000])
+def test_system_blocked_passes_bit_identical(variant, pass_bytes):
+    """Sweeping the systems pass by pass (each pass a range of 4-system chunks
+    swept through the whole step before the next) computes the same step as one
+    pass: systems are independent and the random numbers are keyed by site,
+    system and sweep.  pass_bytes = 1 makes every chunk its own pass; 40000
+    groups chunks, and samples, up to that footprint."""
+    samples = [inputs.small_sample(L, n_temps=8, h_r=0.2, disorder_seed=L) for L in (4, 8, 12)]
+    out = []
+    for pb in (0, pass_bytes):
+        ctx = hsg.Context(samples, 2, 6, precision="fp16", j_fp16=True, variant=variant,
+                          pass_bytes=pb)
+        info = ctx.info()
+        assert info.pass_bytes == pb
+        if pb == 0:
+            assert info.n_passes == 1
+        elif pb == 1:
+            assert info.n_passes == 3 * (info.Wp // 4) // info.chunks_per_thread
+        else:
+            assert 1 < info.n_passes < 3 * (info.Wp // 4)
+        ctx.step(2)
+        ctx.step(1)
+        out.append(([s.copy() for s in ctx.get_spins()], ctx.last_energies(), ctx.get_perm(),
+                    ctx.info().sweep_count))
+        ctx.close()
+    for x, y in zip(out[0][0], out[1][0]):
+        np.testing.assert_array_equal(x, y)
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    np.testing.assert_array_equal(out[0][2], out[1][2])
+    assert out[0][3] == out[1][3] == 18
 
 
 def test_persistent_barrier_timeout_is_reported():
