@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the plain-FP32 comparison lines")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--schedule", default="auto", choices=["auto", "two_pass", "persistent"],
+                    help="step schedule: tuned at the first step (default) or fixed")
     return ap.parse_args()
 
 
@@ -138,9 +140,11 @@ def algorithmic_half_sweep_bytes(ctx, wl):
 def run_ours(args, wl, torch, dev, rank, world, measure_every, do_roofline=True):
     from paper_1204_6192_gb300 import hsg
     stream = torch.cuda.Stream(device=dev)
+    variant = {"auto": hsg.VARIANT_AUTO, "two_pass": hsg.VARIANT_TWO_PASS,
+               "persistent": hsg.VARIANT_PERSISTENT}[getattr(args, "schedule", "auto")]
     ctx = hsg.Context(wl.samples, wl.n_replicas, wl.seed + rank, precision=wl.precision,
                       j_fp16=wl.j_fp16, n_hb=wl.n_hb, n_or=wl.n_or, device=dev.index,
-                      stream=stream.cuda_stream)
+                      stream=stream.cuda_stream, variant=variant)
     info = ctx.info()
     spins = info.total_spins
     sweeps = wl.n_hb + wl.n_or
@@ -207,6 +211,21 @@ def roofline(ctx, stream, torch, wl, reps=20):
     t1.synchronize()
     ms_hb = t0.elapsed_time(t1) / (2 * (reps // 4 or 1))
     return ms_half, ms_hb
+
+
+def time_observables(ctx, reps=3):
+    """Host wall time of one call of each measurement entry point (outside the
+    timed steps): hsg_measure (energies, q, q(k)) and hsg_measure_overlaps (spin
+    and chiral pair overlaps)."""
+    out = {}
+    for name, fn in (("hsg_measure", lambda: ctx.measure()),
+                     ("hsg_measure_overlaps", lambda: ctx.measure_overlaps())):
+        fn()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        out[name] = round((time.perf_counter() - t0) * 1e3 / reps, 3)
+    return out
 
 
 def traffic_summary(kernel_key):
@@ -349,6 +368,7 @@ def main():
         torch.distributed.barrier()
     ms_half, ms_hb = roofline(ctx, stream, torch, wl)
     clocks.stop()
+    observables_ms = time_observables(ctx)
     if world > 1:
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -380,13 +400,14 @@ def main():
                    "l2": "state larger than L2 (no flush)", "parallelism": f"replicas x{world}",
                    "schedule": schedule},
         "spin_updates_per_s": round(updates / (ms * 1e-3), 1),
-        "gpu_launches": args.steps * launches_per_step + n_meas * 4,
+        "gpu_launches": args.steps * launches_per_step + n_meas * 2,
         "roofline": {"bound": "hbm", "kernel": f"k_half_sweep OR {wl.precision}",
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                      "traffic": traffic, "algorithmic_bytes_per_launch": A,
                      "ms_per_launch": round(ms_half, 5), "hb_ms_per_launch": round(ms_hb, 5)},
         "clocks": clocks.summary(),
+        "observables_ms": observables_ms,
     }
 
     if not args.no_e2e:

@@ -186,6 +186,26 @@ typedef struct {
 } hsg_obs;
 hsg_status hsg_measure(hsg_ctx* ctx, hsg_obs* out);
 
+/* Replica-pair overlaps of the current state (Sec. 2: the four-replica
+ * susceptibility sums chi_1, chi_2, chi_3 and the chiral overlap).  For every
+ * temperature slot t and every pair (a, b) of the first min(n_replicas, 4)
+ * replicas, in the order (0,1) (0,2) (1,2) (0,3) (1,3) (2,3) (hsg_info's
+ * n_overlap_pairs of them), with A, B the configurations replicas a and b hold
+ * at slot t:
+ *   D  double[n_samples][n_temps][n_pairs][4][2]:
+ *        D_ab(k) = (1/N) sum_i (s_i^A . s_i^B) e^{+i k.R_i}
+ *   C  double[n_samples][n_temps][n_pairs][3][4][2]:
+ *        C_ab^alpha(k) = (1/N) sum_i kappa_i^{alpha,A} kappa_i^{alpha,B} e^{+i k.R_i}
+ *        with the local chirality kappa_i^alpha = s_{i+alpha} . (s_i x s_{i-alpha}),
+ *        alpha = x, y, z, periodic neighbours
+ * at the modes k = 0, (2 pi/L) e_x, e_y, e_z; [re, im].  The paper's four-replica
+ * sums contract the components within each site, so with replicas numbered from
+ * 1: chi_1(k) = N^2 |D_12|^2, chi_2(k) = N^2 D_13 conj(D_14),
+ * chi_3(k) = N^2 D_13 conj(D_24).  Caller-owned host buffers; either may be NULL
+ * (not both).  HSG_EINVAL when n_replicas < 2.  The spins are read as stored;
+ * row sums are FP32, the rest FP64.  Synchronises. */
+hsg_status hsg_measure_overlaps(hsg_ctx* ctx, double* D, double* C);
+
 /* Spins as FP32 (x, y, z), layout described above.  *_dev take device
    pointers of the context's device; the others host pointers.  get decodes
    the stored precision; set encodes with the context's codec. */
@@ -216,6 +236,7 @@ typedef struct {
   int chunks_per_thread;   /* sweep kernels: chunks of 4 systems one thread walks */
   int n_passes;            /* system-blocked passes per step (1: no blocking) */
   long long pass_bytes;    /* footprint bound of a pass in use (0: one pass) */
+  int n_overlap_pairs;     /* replica pairs hsg_measure_overlaps reports (0 if n_replicas < 2) */
 } hsg_info;
 hsg_status hsg_get_info(hsg_ctx* ctx, hsg_info* info);
 

@@ -72,6 +72,8 @@ def lib():
             "orc_energy": (None, [dp, dp, dp, c_int, c_int, dp]),
             "orc_pt": (None, [dp, dp, i32p, c_int, c_int, u64, u64, u32, i32p]),
             "orc_measure": (None, [dp, c_int, c_int, i32p, dp, dp]),
+            "orc_chirality": (None, [dp, c_int, dp]),
+            "orc_overlaps": (None, [dp, c_int, c_int, c_int, i32p, dp, dp]),
             "orc_num_threads": (c_int, []),
         }
         for name, (res, args) in sig.items():
@@ -115,6 +117,28 @@ def local_field(s_sys: np.ndarray, J: np.ndarray, H: Optional[np.ndarray], L: in
     lib().orc_local_field(_dp(np.ascontiguousarray(s_sys)), _dp(np.ascontiguousarray(J)),
                           _dp(None if H is None else np.ascontiguousarray(H)), L, i, _dp(h))
     return h
+
+
+def chirality(s: np.ndarray, L: int) -> np.ndarray:
+    """Local chirality kappa[N, 3] (a = x, y, z) of one system s[N, 3]."""
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    k = np.zeros((L ** 3, 3))
+    lib().orc_chirality(_dp(s), L, _dp(k))
+    return k
+
+
+def overlaps(s: np.ndarray, L: int, R_O: int, R_T: int, perm: np.ndarray):
+    """Replica-pair overlaps of one sample, s[W, N, 3] (memory-slot order) and
+    perm[R_O, R_T]: D[R_T, P, 4, 2] and C[R_T, P, 3, 4, 2] (modes 0, kx, ky, kz),
+    pairs (0,1) (0,2) (1,2) (0,3) (1,3) (2,3) of the first min(R_O, 4) replicas."""
+    r = min(R_O, 4)
+    P = r * (r - 1) // 2
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    perm = np.ascontiguousarray(perm, dtype=np.int32)
+    D = np.zeros((R_T, P, 4, 2))
+    C = np.zeros((R_T, P, 3, 4, 2))
+    lib().orc_overlaps(_dp(s), L, R_O, R_T, _p(perm, ctypes.c_int32), _dp(D), _dp(C))
+    return D, C
 
 
 def hb_moves(s, h, beta, u1, u2) -> np.ndarray:

@@ -402,6 +402,78 @@ void orc_measure(const double* s, int L, int R_T, const int32_t* perm, double* q
   }
 }
 
+/* Local chirality of one system: for each site i and lattice direction a,
+   kappa = s_{i+a} . (s_i x s_{i-a}) with periodic neighbours (Sec. 2). */
+void orc_chirality(const double* s, int L, double* kappa) {
+  long N = (long)L * L * L;
+  for (long i = 0; i < N; ++i) {
+    int c[3] = {(int)(i % L), (int)((i / L) % L), (int)(i / ((long)L * L))};
+    for (int a = 0; a < 3; ++a) {
+      int cp[3] = {c[0], c[1], c[2]}, cm[3] = {c[0], c[1], c[2]};
+      cp[a] = (c[a] + 1) % L;
+      cm[a] = (c[a] + L - 1) % L;
+      long ip = cp[0] + (long)L * (cp[1] + (long)L * cp[2]);
+      long im = cm[0] + (long)L * (cm[1] + (long)L * cm[2]);
+      const double* u = s + 3 * ip;  /* s_{i+a} */
+      const double* v = s + 3 * i;   /* s_i */
+      const double* w = s + 3 * im;  /* s_{i-a} */
+      double cross[3] = {v[1] * w[2] - v[2] * w[1], v[2] * w[0] - v[0] * w[2],
+                         v[0] * w[1] - v[1] * w[0]};
+      kappa[3 * i + a] = u[0] * cross[0] + u[1] * cross[1] + u[2] * cross[2];
+    }
+  }
+}
+
+/* Replica-pair spin and chiral overlaps at the modes k = 0, (2 pi/L) e_a, by
+   direct summation in FP64 (the four-replica sums and the chiral overlap of
+   Sec. 2). */
+void orc_overlaps(const double* s, int L, int R_O, int R_T, const int32_t* perm, double* D,
+                  double* C) {
+  static const int PA[6] = {0, 0, 1, 0, 1, 2}, PB[6] = {1, 2, 2, 3, 3, 3};
+  long N = (long)L * L * L;
+  int r = R_O < 4 ? R_O : 4;
+  int n_pairs = r * (r - 1) / 2;
+  double* ka = (double*)malloc(sizeof(double) * 3 * N);
+  double* kb = (double*)malloc(sizeof(double) * 3 * N);
+  for (int t = 0; t < R_T; ++t) {
+    for (int k = 0; k < n_pairs; ++k) {
+      const double* sa = s + 3 * ((long)PA[k] * R_T + perm[PA[k] * R_T + t]) * N;
+      const double* sb = s + 3 * ((long)PB[k] * R_T + perm[PB[k] * R_T + t]) * N;
+      orc_chirality(sa, L, ka);
+      orc_chirality(sb, L, kb);
+      double accD[4][2] = {{0}}, accC[3][4][2] = {{{0}}};
+      for (long i = 0; i < N; ++i) {
+        int c[3] = {(int)(i % L), (int)((i / L) % L), (int)(i / ((long)L * L))};
+        double ph[4][2] = {{1.0, 0.0}};
+        for (int a = 0; a < 3; ++a) {
+          double arg = 2.0 * ORC_PI * (double)c[a] / (double)L;
+          ph[a + 1][0] = cos(arg);
+          ph[a + 1][1] = sin(arg);
+        }
+        double d = sa[3 * i] * sb[3 * i] + sa[3 * i + 1] * sb[3 * i + 1] + sa[3 * i + 2] * sb[3 * i + 2];
+        for (int m = 0; m < 4; ++m) {
+          accD[m][0] += d * ph[m][0];
+          accD[m][1] += d * ph[m][1];
+          for (int a = 0; a < 3; ++a) {
+            double pk = ka[3 * i + a] * kb[3 * i + a];
+            accC[a][m][0] += pk * ph[m][0];
+            accC[a][m][1] += pk * ph[m][1];
+          }
+        }
+      }
+      for (int m = 0; m < 4; ++m)
+        for (int ri = 0; ri < 2; ++ri) {
+          if (D) D[(((long)t * n_pairs + k) * 4 + m) * 2 + ri] = accD[m][ri] / (double)N;
+          if (C)
+            for (int a = 0; a < 3; ++a)
+              C[((((long)t * n_pairs + k) * 3 + a) * 4 + m) * 2 + ri] = accC[a][m][ri] / (double)N;
+        }
+    }
+  }
+  free(ka);
+  free(kb);
+}
+
 int orc_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

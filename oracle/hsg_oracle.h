@@ -67,6 +67,17 @@ void   orc_pt(const double* E, const double* temps, int32_t* perm, int R_O, int 
               uint64_t chain_base, uint64_t seed, uint32_t pt_step, int32_t* accepted);
 void   orc_measure(const double* s, int L, int R_T, const int32_t* perm, double* q,
                    double* qk);
+/* Local chirality (Sec. 2, three spins on a line): kappa[i][a] =
+   s_{i+a} . (s_i x s_{i-a}) for a = x, y, z, one system s[N][3]. */
+void   orc_chirality(const double* s, int L, double* kappa);
+/* Replica-pair overlaps at slot t for pairs (a, b) of the first min(R_O, 4)
+   replicas, in the order (0,1) (0,2) (1,2) (0,3) (1,3) (2,3) (the pairs of
+   the first r replicas come first):
+   D[t][pair][m][re,im] = (1/N) sum_i (s_i^A . s_i^B) e^{i k_m.R_i} and
+   C[t][pair][alpha][m][re,im] = (1/N) sum_i kappa_i^{alpha,A} kappa_i^{alpha,B} e^{i k_m.R_i},
+   k_0 = 0, k_{1,2,3} = (2 pi / L) e_{x,y,z}.  Either output may be NULL. */
+void   orc_overlaps(const double* s, int L, int R_O, int R_T, const int32_t* perm, double* D,
+                    double* C);
 int    orc_num_threads(void);
 
 #ifdef __cplusplus

@@ -61,6 +61,10 @@ struct hsg_ctx {
   unsigned long long* d_acc = nullptr;
   unsigned long long* d_counters = nullptr;
   double* d_mpart = nullptr;
+  double* d_opart = nullptr;          // overlap partials (allocated at first use)
+  bool e_valid = false;               // d_E holds the energies of the current state
+  double* d_D = nullptr;
+  double* d_C = nullptr;
   double* d_q = nullptr;
   double* d_qk = nullptr;
   float* d_xyz = nullptr;
@@ -374,7 +378,8 @@ hsg_status configure_schedule(hsg_ctx* c, int variant, int gpt, long long pass_b
   c->pass_bytes = pass_bytes;
   HSG_CUDA(c, cudaMemcpyAsync(c->d_pass_bound, bounds.data(), sizeof(int) * bounds.size(),
                               cudaMemcpyHostToDevice, c->stream));
-  c->e_splits = std::min(64, std::max(1, max_rows / 256));
+  // energy sums: about 16 block rows per first-level unit, at most MAX_E_SPLITS
+  c->e_splits = std::min(MAX_E_SPLITS, std::max(1, max_rows / 16));
   HSG_CUDA(c, cudaMemcpyAsync(c->d_sweep_blocks, blocks.data(), sizeof(int4) * blocks.size(),
                               cudaMemcpyHostToDevice, c->stream));
   HSG_CUDA(c, cudaMemcpyAsync(c->d_sd, c->sd.data(), sizeof(SampleDev) * c->ns,
@@ -709,7 +714,7 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   HSG_ALLOC(c->d_pass_bound, sizeof(int) * (c->max_passes + 1));
   HSG_ALLOC(c->d_conv_blocks, sizeof(int4) * conv_blocks.size());
   HSG_ALLOC(c->d_epart, sizeof(double) * 2 * max_sweep_blocks * Wp);
-  HSG_ALLOC(c->d_epart2, sizeof(double) * n_samples * 64 * Wp);
+  HSG_ALLOC(c->d_epart2, sizeof(double) * n_samples * MAX_E_SPLITS * Wp);
   HSG_ALLOC(c->d_beta, sizeof(float) * n_samples * Wp);
   HSG_ALLOC(c->d_temps, sizeof(double) * n_samples * n_temps);
   HSG_ALLOC(c->d_inv_temps, sizeof(double) * n_samples * n_temps);
@@ -813,6 +818,7 @@ hsg_status hsg_sweep_or(hsg_ctx* c, int n) {
   if (n < 0) return bad_arg(c, "n_sweeps < 0");
   if (n == 0) return HSG_OK;
   HSG_CUDA(c, cudaSetDevice(c->device));
+  c->e_valid = false;
   for (int k = 0; k < n; ++k) HSG_TRY(half_sweeps(c, false, k));
   HSG_CUDA(c, launch_bump(c->d_counters, n, 0, c->stream));
   return HSG_OK;
@@ -823,6 +829,7 @@ hsg_status hsg_sweep_hb(hsg_ctx* c, int n) {
   if (n < 0) return bad_arg(c, "n_sweeps < 0");
   if (n == 0) return HSG_OK;
   HSG_CUDA(c, cudaSetDevice(c->device));
+  c->e_valid = false;
   for (int k = 0; k < n; ++k) HSG_TRY(half_sweeps(c, true, k));
   HSG_CUDA(c, launch_bump(c->d_counters, n, 0, c->stream));
   return HSG_OK;
@@ -832,6 +839,7 @@ hsg_status hsg_pt_exchange(hsg_ctx* c) {
   HSG_CHECK_CTX(c);
   HSG_CUDA(c, cudaSetDevice(c->device));
   HSG_TRY(enqueue_energy(c));
+  c->e_valid = true;
   HSG_CUDA(c, launch_pt(pt_params(c, 0, 1), c->stream));
   return HSG_OK;
 }
@@ -842,6 +850,7 @@ hsg_status hsg_pt_exchange_energies(hsg_ctx* c, const double* E_sys) {
   HSG_CUDA(c, cudaSetDevice(c->device));
   HSG_CUDA(c, cudaMemcpy2DAsync(c->d_E, sizeof(double) * c->Wp, E_sys, sizeof(double) * c->W,
                                 sizeof(double) * c->W, c->ns, cudaMemcpyHostToDevice, c->stream));
+  c->e_valid = false;   // the caller's energies need not be those of the state
   HSG_CUDA(c, launch_pt(pt_params(c, 0, 1), c->stream));
   // the host array may be released by the caller on return
   HSG_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -855,7 +864,9 @@ hsg_status hsg_step(hsg_ctx* c, int n_steps) {
   if (n_steps == 0) return HSG_OK;
   HSG_CUDA(c, cudaSetDevice(c->device));
   if (c->tune_pending) HSG_TRY(autotune(c));
-  return run_steps(c, n_steps);
+  HSG_TRY(run_steps(c, n_steps));
+  c->e_valid = true;    // every step ends with the energies of its final state
+  return HSG_OK;
 }
 
 hsg_status hsg_energies(hsg_ctx* c, double* E_sys) {
@@ -863,6 +874,7 @@ hsg_status hsg_energies(hsg_ctx* c, double* E_sys) {
   if (!E_sys) return bad_arg(c, "E_sys is NULL");
   HSG_CUDA(c, cudaSetDevice(c->device));
   HSG_TRY(enqueue_energy(c));
+  c->e_valid = true;
   HSG_CUDA(c, cudaMemcpy2DAsync(E_sys, sizeof(double) * c->W, c->d_E, sizeof(double) * c->Wp,
                                 sizeof(double) * c->W, c->ns, cudaMemcpyDeviceToHost, c->stream));
   HSG_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -885,27 +897,33 @@ hsg_status hsg_measure(hsg_ctx* c, hsg_obs* o) {
   HSG_CHECK_CTX(c);
   if (!o) return bad_arg(c, "obs is NULL");
   HSG_CUDA(c, cudaSetDevice(c->device));
-  HSG_TRY(enqueue_energy(c));
+  // the energies a step leaves behind are those of its final state
+  if (!c->e_valid) HSG_TRY(enqueue_energy(c));
+  c->e_valid = true;
   const bool pairs = c->R_O >= 2 && (o->q || o->qk);
   if (pairs) {
+    const long long nmax = (long long)c->Lmax * c->Lmax * c->Lmax;
+    const int n_tiles = (int)((nmax + MEAS_TILE - 1) / MEAS_TILE);
     if (!c->d_mpart) {
-      HSG_TRY(dev_alloc(c, &c->d_mpart, sizeof(double) * c->ns * (size_t)c->Lmax * c->R_T * 45));
+      HSG_TRY(dev_alloc(c, &c->d_mpart, sizeof(double) * c->ns * 3 * (size_t)n_tiles * c->R_T *
+                                            meas_partial_values(true, false)));
       HSG_TRY(dev_alloc(c, &c->d_q, sizeof(double) * c->ns * (size_t)c->R_T * 9));
       HSG_TRY(dev_alloc(c, &c->d_qk, sizeof(double) * c->ns * (size_t)c->R_T * 54));
     }
-    MeasureParams p;
+    OverlapParams p;
     p.spins = c->spins;
     p.samples = c->d_sd;
     p.perm = c->d_perm;
     p.partials = c->d_mpart;
-    p.q = c->d_q;
-    p.qk = c->d_qk;
+    p.D = c->d_q;
+    p.C = c->d_qk;
     p.n_samples = c->ns;
     p.R_O = c->R_O;
     p.R_T = c->R_T;
     p.Wp = c->Wp;
-    p.Lmax = c->Lmax;
-    HSG_CUDA(c, launch_measure(c->fmt, p, c->Lmax, c->stream));
+    p.n_pairs = 3;          // units: the rows mu of the tensor
+    p.n_tiles = n_tiles;
+    HSG_CUDA(c, launch_qtensor(c->fmt, p, c->stream));
   }
   std::vector<double> E((size_t)c->ns * c->Wp);
   std::vector<int> perm((size_t)c->ns * c->R_O * c->R_T);
@@ -947,6 +965,53 @@ hsg_status hsg_set_spins_dev(hsg_ctx* c, const float* xyz_dev) {
   HSG_TRY(ensure_xyz(c));
   HSG_CUDA(c, launch_set(c->fmt, conv_params(c, const_cast<float*>(xyz_dev), c->d_xyz_off),
                          c->n_conv_blocks, c->stream));
+  c->e_valid = false;
+  return HSG_OK;
+}
+
+// Replica pairs of the overlap measurements: all pairs of the first
+// min(n_replicas, 4) replicas.
+int overlap_pairs(int R_O) {
+  const int r = std::min(R_O, 4);
+  return r * (r - 1) / 2;
+}
+
+hsg_status hsg_measure_overlaps(hsg_ctx* c, double* D, double* C) {
+  HSG_CHECK_CTX(c);
+  if (!D && !C) return bad_arg(c, "D and C are both NULL");
+  if (c->R_O < 2) return bad_arg(c, "overlaps need n_replicas >= 2");
+  HSG_CUDA(c, cudaSetDevice(c->device));
+  const int n_pairs = overlap_pairs(c->R_O);
+  const long long nmax = (long long)c->Lmax * c->Lmax * c->Lmax;
+  const int n_tiles = (int)((nmax + MEAS_TILE - 1) / MEAS_TILE);
+  if (!c->d_opart) {
+    HSG_TRY(dev_alloc(c, &c->d_opart, sizeof(double) * c->ns * (size_t)n_pairs * n_tiles * c->R_T *
+                                          meas_partial_values(false, true)));
+    HSG_TRY(dev_alloc(c, &c->d_D, sizeof(double) * c->ns * (size_t)c->R_T * n_pairs * 8));
+    HSG_TRY(dev_alloc(c, &c->d_C, sizeof(double) * c->ns * (size_t)c->R_T * n_pairs * 24));
+  }
+  OverlapParams p;
+  p.spins = c->spins;
+  p.samples = c->d_sd;
+  p.perm = c->d_perm;
+  p.partials = c->d_opart;
+  p.D = c->d_D;
+  p.C = C ? c->d_C : nullptr;
+  p.n_samples = c->ns;
+  p.R_O = c->R_O;
+  p.R_T = c->R_T;
+  p.Wp = c->Wp;
+  p.n_pairs = n_pairs;
+  p.n_tiles = n_tiles;
+  HSG_CUDA(c, launch_overlaps(c->fmt, p, C != nullptr, c->stream));
+  if (D)
+    HSG_CUDA(c, cudaMemcpyAsync(D, c->d_D, sizeof(double) * c->ns * c->R_T * n_pairs * 8,
+                                cudaMemcpyDeviceToHost, c->stream));
+  if (C)
+    HSG_CUDA(c, cudaMemcpyAsync(C, c->d_C, sizeof(double) * c->ns * c->R_T * n_pairs * 24,
+                                cudaMemcpyDeviceToHost, c->stream));
+  HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  HSG_TRY(poll_device_error(c));
   return HSG_OK;
 }
 
@@ -971,6 +1036,7 @@ hsg_status hsg_set_spins(hsg_ctx* c, const float* xyz) {
   HSG_CUDA(c, cudaMemcpyAsync(c->d_xyz, xyz, sizeof(float) * c->xyz_floats, cudaMemcpyHostToDevice,
                               c->stream));
   HSG_CUDA(c, launch_set(c->fmt, conv_params(c, c->d_xyz, c->d_xyz_off), c->n_conv_blocks, c->stream));
+  c->e_valid = false;
   // the host buffer has been read once the copy is done
   HSG_CUDA(c, cudaStreamSynchronize(c->stream));
   HSG_TRY(poll_device_error(c));
@@ -1021,6 +1087,7 @@ hsg_status hsg_get_info(hsg_ctx* c, hsg_info* info) {
   info->variant = c->variant;
   info->chunks_per_thread = c->GPT;
   info->n_passes = (int)c->pass_bound.size() - 1;
+  info->n_overlap_pairs = c->R_O >= 2 ? overlap_pairs(c->R_O) : 0;
   info->pass_bytes = c->pass_bytes;
   info->total_sites = c->total_sites;
   info->total_spins = c->total_sites * c->W;

@@ -126,15 +126,18 @@ __global__ void __launch_bounds__(256) k_energy_final1(const EnergyParams p) {
   energy_final1_unit<false>(p, blockIdx.z, blockIdx.y, blockIdx.x, red);
 }
 
+// one warp per system (8 per block)
 __global__ void k_energy_final2(const EnergyParams p) {
-  for (int w = threadIdx.x; w < p.Wp; w += blockDim.x) energy_final2_unit<false>(p, blockIdx.x, w);
+  const int gw = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (gw >= p.n_samples * p.Wp) return;
+  energy_final2_warp<false>(p, gw / p.Wp, gw % p.Wp, threadIdx.x & 31);
 }
 
 cudaError_t launch_energy_final(const EnergyParams& p, cudaStream_t st) {
   k_energy_final1<<<dim3(p.splits, (p.Wp + 31) / 32, p.n_samples), 256, 0, st>>>(p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_energy_final2<<<p.n_samples, 128, 0, st>>>(p);
+  k_energy_final2<<<(p.n_samples * p.Wp + 7) / 8, 256, 0, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -192,151 +195,6 @@ cudaError_t launch_bump(unsigned long long* counters, int sweeps, int pts, cudaS
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// Overlaps: q^{mu nu} = (1/N) sum_i s_i^mu(A) s_i^nu(B) and the modes
-// k = (2 pi/L) e_a, between the configurations A, B of replicas 0 and 1 that
-// hold temperature t.  A block handles one z-plane of one sample; a thread one
-// slot t and every YL-th row.  Per row the x-sums (with the e^{i kx x} twiddle)
-// run in FP32; rows are added in FP64 with the e^{i ky y} twiddle; the z twiddle
-// is applied in the final kernel.
-// ---------------------------------------------------------------------------
-template <int F>
-__global__ void __launch_bounds__(MEAS_BS) k_measure_planes(const MeasureParams p) {
-  const int s = blockIdx.y, z = blockIdx.x;
-  const SampleDev& sd = p.samples[s];
-  const int L = sd.L;
-  if (z >= L) return;
-  __shared__ float tw[2][512];
-  __shared__ double red[MEAS_BS][15];
-  for (int x = threadIdx.x; x < L; x += blockDim.x) {
-    float sx, cx;
-    sincospif(2.0f * (float)x / (float)L, &sx, &cx);
-    tw[0][x] = cx;
-    tw[1][x] = sx;
-  }
-  __syncthreads();
-  const int R_T = p.R_T;
-  const int YL = MEAS_BS / R_T;
-  const int t = threadIdx.x % R_T, yl = threadIdx.x / R_T;
-  const bool active = yl < YL;
-  double Q[9], QX[18], QY[18];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) Q[i] = 0.0;
-#pragma unroll
-  for (int i = 0; i < 18; ++i) { QX[i] = 0.0; QY[i] = 0.0; }
-  if (active) {
-    const int* perm = p.perm + (long long)s * p.R_O * R_T;
-    const int wA = perm[t], wB = R_T + perm[R_T + t];
-    const uint32_t half_n = (uint32_t)sd.N >> 1;
-    const unsigned char* base = p.spins + sd.spin_off;
-    for (int y = yl; y < L; y += YL) {
-      float R0[9], RX[18];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) R0[i] = 0.0f;
-#pragma unroll
-      for (int i = 0; i < 18; ++i) RX[i] = 0.0f;
-      const uint32_t row = (uint32_t)(y + L * z) * (uint32_t)L;
-      for (int x = 0; x < L; ++x) {
-        const uint32_t site = row + (uint32_t)x;
-        const uint32_t ss = (((uint32_t)(x + y + z)) & 1u) * half_n + (site >> 1);
-        float a[3], b[3];
-        decode_one<F>(base + chunk_offset<F>(sd, wA >> 2, ss), sd.plane_stride, wA & 3,
-                      a[0], a[1], a[2]);
-        decode_one<F>(base + chunk_offset<F>(sd, wB >> 2, ss), sd.plane_stride, wB & 3,
-                      b[0], b[1], b[2]);
-        const float cx = tw[0][x], sx = tw[1][x];
-#pragma unroll
-        for (int mu = 0; mu < 3; ++mu)
-#pragma unroll
-          for (int nu = 0; nu < 3; ++nu) {
-            const float pr = a[mu] * b[nu];
-            R0[mu * 3 + nu] += pr;
-            RX[(mu * 3 + nu) * 2] += pr * cx;
-            RX[(mu * 3 + nu) * 2 + 1] += pr * sx;
-          }
-      }
-      double sy, cy;
-      sincospi(2.0 * (double)y / (double)L, &sy, &cy);
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        Q[i] += (double)R0[i];
-        QX[2 * i] += (double)RX[2 * i];
-        QX[2 * i + 1] += (double)RX[2 * i + 1];
-        QY[2 * i] += (double)R0[i] * cy;
-        QY[2 * i + 1] += (double)R0[i] * sy;
-      }
-    }
-  }
-  // reduce over the YL row-lanes of each slot in three passes of 15 values
-  double* out = p.partials + (((long long)s * p.Lmax + z) * R_T) * 45;
-  for (int pass = 0; pass < 3; ++pass) {
-#pragma unroll
-    for (int i = 0; i < 15; ++i) {
-      const int v = pass * 15 + i;
-      red[threadIdx.x][i] = v < 9 ? Q[v] : (v < 27 ? QX[v - 9] : QY[v - 27]);
-    }
-    __syncthreads();
-    if (threadIdx.x < R_T) {
-      for (int i = 0; i < 15; ++i) {
-        double acc = 0.0;
-        for (int k = 0; k < YL; ++k) acc += red[k * R_T + threadIdx.x][i];
-        out[threadIdx.x * 45 + pass * 15 + i] = acc;
-      }
-    }
-    __syncthreads();
-  }
-}
-
-__global__ void k_measure_final(const MeasureParams p) {
-  const int s = blockIdx.x;
-  const SampleDev& sd = p.samples[s];
-  const int L = sd.L;
-  const double invN = 1.0 / (double)sd.N;
-  for (int idx = threadIdx.x; idx < p.R_T * 9; idx += blockDim.x) {
-    const int t = idx / 9, mn = idx % 9;
-    double q = 0, xr = 0, xi = 0, yr = 0, yi = 0, zr = 0, zi = 0;
-    for (int z = 0; z < L; ++z) {
-      const double* v = p.partials + (((long long)s * p.Lmax + z) * p.R_T + t) * 45;
-      q += v[mn];
-      xr += v[9 + 2 * mn];
-      xi += v[9 + 2 * mn + 1];
-      yr += v[27 + 2 * mn];
-      yi += v[27 + 2 * mn + 1];
-      double sz, cz;
-      sincospi(2.0 * (double)z / (double)L, &sz, &cz);
-      zr += v[mn] * cz;
-      zi += v[mn] * sz;
-    }
-    p.q[((long long)s * p.R_T + t) * 9 + mn] = q * invN;
-    double* k = p.qk + ((long long)s * p.R_T + t) * 54;
-    k[(0 * 9 + mn) * 2] = xr * invN;
-    k[(0 * 9 + mn) * 2 + 1] = xi * invN;
-    k[(1 * 9 + mn) * 2] = yr * invN;
-    k[(1 * 9 + mn) * 2 + 1] = yi * invN;
-    k[(2 * 9 + mn) * 2] = zr * invN;
-    k[(2 * 9 + mn) * 2 + 1] = zi * invN;
-  }
-}
-
-template <int F>
-static cudaError_t measure_fmt(const MeasureParams& p, int lmax, cudaStream_t st) {
-  k_measure_planes<F><<<dim3(lmax, p.n_samples), MEAS_BS, 0, st>>>(p);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_measure_final<<<p.n_samples, 256, 0, st>>>(p);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_measure(int fmt, const MeasureParams& p, int lmax, cudaStream_t st) {
-  switch (fmt) {
-    case FMT_F32: return measure_fmt<FMT_F32>(p, lmax, st);
-    case FMT_F16: return measure_fmt<FMT_F16>(p, lmax, st);
-    case FMT_BF16: return measure_fmt<FMT_BF16>(p, lmax, st);
-    case FMT_ANG16: return measure_fmt<FMT_ANG16>(p, lmax, st);
-    case FMT_OCT16: return measure_fmt<FMT_OCT16>(p, lmax, st);
-  }
-  return cudaErrorInvalidValue;
-}
 
 // ---------------------------------------------------------------------------
 // Initial state and conversions.  One thread per (site, chunk), all sites.

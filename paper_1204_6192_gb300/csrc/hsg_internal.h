@@ -27,9 +27,9 @@ namespace hsg {
 // spin storage formats (values of hsg_precision)
 enum Fmt { FMT_F32 = 0, FMT_F16 = 1, FMT_BF16 = 2, FMT_ANG16 = 3, FMT_OCT16 = 4 };
 
-constexpr int SWEEP_BS = 256;     // threads per block, streaming sweep kernels
+constexpr int SWEEP_BS = 256;
+constexpr int MAX_E_SPLITS = 256;   // first-level units per sample of the energy sums     // threads per block, streaming sweep kernels
 constexpr int RED_BS = SWEEP_BS;  // energy kernel: same blocks as the sweep
-constexpr int MEAS_BS = 256;      // threads per block, measurement partials
 
 struct FastDivH {
   uint32_t d, m, s;
@@ -86,15 +86,22 @@ struct PTParams {
   int bump_pt;              // 1: this is a PT pass (counters[1] += 1)
 };
 
-struct MeasureParams {
+
+// Replica-pair measurements (hsg_overlap.cu): the overlap tensor of replicas
+// 0 and 1 (one unit) or the scalar / chiral overlaps of n_pairs replica pairs.
+struct OverlapParams {
   const unsigned char* spins;
   const SampleDev* samples;
   const int* perm;
-  double* partials;         // [n_samples][Lmax][R_T][45]
-  double* q;                // [n_samples][R_T][9]
-  double* qk;               // [n_samples][R_T][3][9][2]
-  int n_samples, R_O, R_T, Wp, Lmax;
+  double* partials;         // [n_samples][n_pairs][n_tiles][R_T][values]
+  double* D;                // q [ns][R_T][3][3], or D [ns][R_T][n_pairs][4][2]; may be null
+  double* C;                // qk [ns][R_T][3][3][3][2], or C [ns][R_T][n_pairs][3][4][2]; may be null
+  int n_samples, R_O, R_T, Wp, n_pairs, n_tiles;
 };
+constexpr int MEAS_BS = 256;       // threads per block of the measurement kernels
+constexpr int MEAS_TILE = 1024;    // sites per block of the measurement kernels
+// FP64 partial values per (unit, tile, slot): 21 per tensor row, 28 (7 without chirality) per pair
+int meas_partial_values(bool qtensor, bool chiral);
 
 struct ConvParams {
   unsigned char* spins;
@@ -126,7 +133,9 @@ cudaError_t launch_energy(int fmt, bool j16, const EnergyParams& p, cudaStream_t
 cudaError_t launch_energy_final(const EnergyParams& p, cudaStream_t st);
 cudaError_t launch_pt(const PTParams& p, cudaStream_t st);
 cudaError_t launch_bump(unsigned long long* counters, int sweeps, int pts, cudaStream_t st);
-cudaError_t launch_measure(int fmt, const MeasureParams& p, int lmax, cudaStream_t st);
+cudaError_t launch_overlaps(int fmt, const OverlapParams& p, bool chiral, cudaStream_t st);
+// q^{mu nu}(k) of replicas 0 and 1: p.D = q, p.C = qk, partials [ns][R_T][3][n_blocks][21]
+cudaError_t launch_qtensor(int fmt, const OverlapParams& p, cudaStream_t st);
 cudaError_t launch_init(int fmt, const ConvParams& p, int n_blocks, cudaStream_t st);
 cudaError_t launch_philox(const uint4* ctr, long long n, const SweepParams& p, uint4* out,
                           cudaStream_t st);

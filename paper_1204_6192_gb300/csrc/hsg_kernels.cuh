@@ -215,20 +215,39 @@ __device__ __forceinline__ void energy_final1_unit(const EnergyParams& p, int s,
   __syncthreads();
 }
 
+// Level 2 for system w of sample s, one warp: lane j adds splits j, j + 32, ...
+// in order, then the lanes are added by a fixed shuffle tree.
 template <bool CG>
-__device__ __forceinline__ void energy_final2_unit(const EnergyParams& p, int s, int w) {
+__device__ __forceinline__ void energy_final2_warp(const EnergyParams& p, int s, int w, int lane) {
   double e = 0.0;
-  for (int k = 0; k < p.splits; ++k) {
+  for (int k = lane; k < p.splits; k += 32) {
     const double* a = p.partials2 + ((long long)s * p.splits + k) * p.Wp + w;
     e += CG ? __ldcg(a) : *a;
   }
-  p.E[(long long)s * p.Wp + w] = e;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+  if (lane == 0) p.E[(long long)s * p.Wp + w] = e;
 }
 
 // Parallel tempering, Eq. (4), for chain c = (sample, replica): pairs (k, k+1)
 // from the lowest temperature up, accepted with min[1, exp(dbeta dE)]; an
 // accepted exchange swaps the temperatures of the two configurations; then
 // the chain's systems get their new inverse temperatures.
+// Metropolis decision of a PT pair (Eq. 4): accept iff x >= 0 or u < exp(x),
+// decided exactly as in binary64.  u >= 2^-24 > exp(-17), so x < -17 always
+// rejects.  Otherwise exp is evaluated in FP32 (expf: within 2 ulp; rounding
+// x to FP32 adds at most 17 * 2^-24 relative), and only a u within 4e-6
+// relative of it goes to the FP64 exp.  (GB300's FP64 rate is a small fraction
+// of its FP32 rate and this chain is sequential.)
+__device__ __forceinline__ bool pt_accept(double x, float u) {
+  if (x >= 0.0) return true;
+  if (x < -17.0) return false;
+  const float e = expf((float)x);
+  if (u < e * (1.0f - 4e-6f)) return true;
+  if (u > e * (1.0f + 4e-6f)) return false;
+  return (double)u < exp(x);
+}
+
 template <bool CG>
 __device__ __forceinline__ void pt_chain(const PTParams& p, int c, uint32_t step) {
   const int s = c / p.R_O, r = c - s * p.R_O;
@@ -236,15 +255,23 @@ __device__ __forceinline__ void pt_chain(const PTParams& p, int c, uint32_t step
   const double* E = p.E + (long long)s * p.Wp + r * p.R_T;
   const double* ib = p.inv_temps + (long long)s * p.R_T;
   if (p.bump_pt) {
+    // the uniforms do not depend on the decisions: they are drawn 32 pairs at a
+    // time ahead of the sequential chain, so the Philox evaluations overlap
+    float uk[32];
     for (int k = 0; k + 1 < p.R_T; ++k) {
+      if ((k & 31) == 0) {
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j)
+          uk[j] = (k + j + 1 < p.R_T)
+                      ? u01(philox4x32_10(make_uint4((uint32_t)(k + j), (uint32_t)c, step, TAG_PT),
+                                          p.seed_lo, p.seed_hi).x)
+                      : 1.0f;
+      }
       const int a = perm[k], b = perm[k + 1];
       const double dbeta = ib[k + 1] - ib[k];
       const double dE = (CG ? __ldcg(E + b) : E[b]) - (CG ? __ldcg(E + a) : E[a]);
       const double x = dbeta * dE;
-      const uint4 rnd = philox4x32_10(make_uint4((uint32_t)k, (uint32_t)c, step, TAG_PT),
-                                      p.seed_lo, p.seed_hi);
-      const double u = (double)u01(rnd.x);
-      const bool acc = (x >= 0.0) || (u < exp(x));
+      const bool acc = pt_accept(x, uk[k & 31]);
       if (acc) {
         perm[k] = b;
         perm[k + 1] = a;

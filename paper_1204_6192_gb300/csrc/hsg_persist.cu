@@ -88,7 +88,9 @@ __global__ void __launch_bounds__(SWEEP_BS) k_persistent(const PersistParams P) 
       energy_final1_unit<true>(ep, rest / wgs, rest % wgs, split, red);
     }
     if (!sync()) return;
-    for (int i = tid; i < ep.n_samples * ep.Wp; i += nth) energy_final2_unit<true>(ep, i / ep.Wp, i % ep.Wp);
+    // level 2: one warp per system (whole warps, so every lane takes part in the shuffles)
+    for (int gw = tid >> 5; gw < ep.n_samples * ep.Wp; gw += nth >> 5)
+      energy_final2_warp<true>(ep, gw / ep.Wp, gw % ep.Wp, threadIdx.x & 31);
     if (!sync()) return;
     const uint32_t pstep = (uint32_t)__ldcg(P.pt.counters + 1);
     for (int c = tid; c < P.pt.n_samples * P.pt.R_O; c += nth) pt_chain<true>(P.pt, c, pstep);

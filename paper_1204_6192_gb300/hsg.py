@@ -51,7 +51,8 @@ class Info(ctypes.Structure):
                 ("spin_bytes", ctypes.c_longlong), ("rec_bytes", ctypes.c_longlong),
                 ("sweep_count", ctypes.c_uint64), ("pt_count", ctypes.c_uint64),
                 ("stream", ctypes.c_void_p), ("chunks_per_thread", ctypes.c_int),
-                ("n_passes", ctypes.c_int), ("pass_bytes", ctypes.c_longlong)]
+                ("n_passes", ctypes.c_int), ("pass_bytes", ctypes.c_longlong),
+                ("n_overlap_pairs", ctypes.c_int)]
 
 
 _lib = None
@@ -82,6 +83,7 @@ def lib() -> ctypes.CDLL:
         "hsg_energies": (ip, [vp, dp]),
         "hsg_last_energies": (ip, [vp, dp]),
         "hsg_measure": (ip, [vp, ctypes.POINTER(Obs)]),
+        "hsg_measure_overlaps": (ip, [vp, dp, dp]),
         "hsg_get_spins": (ip, [vp, fp]),
         "hsg_set_spins": (ip, [vp, fp]),
         "hsg_get_spins_dev": (ip, [vp, vp]),
@@ -233,6 +235,20 @@ class Context:
         self._check(lib().hsg_measure(self._ctx, ctypes.byref(o)))
         return {"E": E, "perm": perm, "q": qa, "qk": qk}
 
+    def measure_overlaps(self, spin: bool = True, chiral: bool = True):
+        """Replica-pair overlaps D [ns, R_T, P, 4, 2] and chiral overlaps
+        C [ns, R_T, P, 3, 4, 2] (modes k = 0, kx, ky, kz; re, im) for the P pairs
+        (0,1) (0,2) (1,2) (0,3) (1,3) (2,3) of the first min(R_O, 4) replicas."""
+        P = self.info().n_overlap_pairs
+        ns, R_T = self.n_samples, self.n_temps
+        D = np.zeros((ns, R_T, P, 4, 2)) if spin else None
+        C = np.zeros((ns, R_T, P, 3, 4, 2)) if chiral else None
+        dpp = ctypes.POINTER(ctypes.c_double)
+        self._check(lib().hsg_measure_overlaps(
+            self._ctx, _ptr(D, ctypes.c_double) if spin else dpp(),
+            _ptr(C, ctypes.c_double) if chiral else dpp()))
+        return {"D": D, "C": C}
+
     def spin_shapes(self):
         return [(self.W, n, 3) for n in self.Ns]
 
@@ -324,6 +340,7 @@ hsg_step = Context.step
 hsg_energies = Context.energies
 hsg_last_energies = Context.last_energies
 hsg_measure = Context.measure
+hsg_measure_overlaps = Context.measure_overlaps
 hsg_get_spins = Context.get_spins
 hsg_set_spins = Context.set_spins
 hsg_get_spins_dev = Context.get_spins_dev

@@ -97,3 +97,19 @@ def test_fullsize_step_matches_oracle_on_sampled_systems(full):
     E_new = ctx.energies()[0]
     np.testing.assert_allclose(E_step, E_new, rtol=1e-7)
     assert np.all(np.isfinite(ctx.measure()["q"]))
+
+
+def test_fullsize_overlaps_on_sampled_slots(full):
+    """hsg_measure_overlaps at full size: the spin and chiral pair overlaps of
+    two temperature slots, recomputed by the oracle from the two configurations
+    alone (FP32 row sums of 128 terms)."""
+    w, smp16, ctx = full
+    out = ctx.measure_overlaps()
+    spins = ctx.get_spins()[0]
+    perm = ctx.get_perm()[0]
+    R_T = len(smp16.temps)
+    for t in (0, R_T - 1):
+        sub = np.stack([spins[perm[0, t]], spins[R_T + perm[1, t]]]).astype(np.float64)
+        D, C = oracle.overlaps(sub, smp16.L, 2, 1, np.zeros((2, 1), dtype=np.int32))
+        np.testing.assert_allclose(out["D"][0, t], D[0], rtol=0, atol=2e-6)
+        np.testing.assert_allclose(out["C"][0, t], C[0], rtol=0, atol=2e-6)
