@@ -230,7 +230,7 @@ def time_observables(ctx, reps=3):
 
 def traffic_summary(kernel_key):
     """DRAM bytes per launch from the committed ncu summary, if it is current."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         with open(p) as f:
             d = json.load(f)

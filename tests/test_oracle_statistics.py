@@ -158,19 +158,31 @@ def test_pt_acceptance_frequency(orc):
             assert abs(freq - p) < 5 * np.sqrt(p * (1 - p) / n), (dE, freq, p)
 
 
+def read_golden(name):
+    import os
+    out = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                key, *vals = line.split()
+                out[key] = np.array([float(v) for v in vals])
+    return out
+
+
 def test_pt_upward_carry(orc):
-    """Hand-worked pass of Eq. (4) with R_T = 4: energies fall with slot, every
-    attempt has dbeta dE > 0 and is accepted, so the configuration that starts
-    at the lowest temperature is carried to the top in one pass:
-    memory slots [0, 1, 2, 3] -> [1, 2, 3, 0]."""
-    temps = np.array([0.5, 0.6, 0.7, 0.8])
-    E = np.array([0.0, -10.0, -20.0, -30.0])
-    perm, acc = orc.pt(E, temps, np.array([[0, 1, 2, 3]], dtype=np.int32), 1, 4, 0, 5, 0)
-    np.testing.assert_array_equal(perm[0], [1, 2, 3, 0])
-    np.testing.assert_array_equal(acc[0], [1, 1, 1])
-    # the reverse ordering is never accepted when the exponent is very negative
-    perm, acc = orc.pt(-E * 100, temps, np.array([[0, 1, 2, 3]], dtype=np.int32), 1, 4, 0, 5, 0)
-    np.testing.assert_array_equal(perm[0], [0, 1, 2, 3])
+    """Hand-worked pass of Eq. (4) with R_T = 4 (tests/golden/pt_upward_carry.txt):
+    energies fall with slot, every attempt is accepted, so the configuration
+    that starts at the lowest temperature is carried to the top in one pass;
+    with the energies scaled by -100 nothing is accepted."""
+    g = read_golden("pt_upward_carry.txt")
+    p0 = g["perm_in"].astype(np.int32)[None, :]
+    perm, acc = orc.pt(g["energies"], g["temps"], p0.copy(), 1, 4, 0, 5, 0)
+    np.testing.assert_array_equal(perm[0], g["perm_out"])
+    np.testing.assert_array_equal(acc[0], g["accepted"])
+    perm, acc = orc.pt(g["scaled_energies"], g["temps"], p0.copy(), 1, 4, 0, 5, 0)
+    np.testing.assert_array_equal(perm[0], g["scaled_perm_out"])
+    np.testing.assert_array_equal(acc[0], g["scaled_accepted"])
 
 
 def test_pt_keeps_boltzmann_per_temperature(orc):
@@ -200,3 +212,19 @@ def test_pt_keeps_boltzmann_per_temperature(orc):
         sigma = np.sqrt(N * (1 - 2 * mL / a - mL * mL) / per_slot.shape[0])
         for r in range(2):
             assert abs(per_slot[:, r, t].mean() - exact) < 5 * sigma, (t, r)
+
+
+def test_oracle_matches_its_recorded_run():
+    """The oracle reproduces the run recorded by tests/golden/make_oracle_fixture.py
+    (energies, permutation, overlap after two steps of a seeded L = 4 sample)."""
+    import importlib.util
+    import os
+    spec = importlib.util.spec_from_file_location(
+        "make_oracle_fixture", os.path.join(os.path.dirname(__file__), "golden", "make_oracle_fixture.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    g = read_golden("oracle_L4_two_steps.txt")
+    now = mod.run()
+    np.testing.assert_array_equal(now["perm"], g["perm"])
+    np.testing.assert_allclose(now["E"], g["E"], rtol=1e-10)
+    np.testing.assert_allclose(now["q"], g["q"], rtol=0, atol=1e-10)
