@@ -221,6 +221,32 @@ hsg_status hsg_get_perm(hsg_ctx* ctx, int32_t* perm);
    uint64[n_samples][n_replicas][n_temps - 1]; and the number of PT calls. */
 hsg_status hsg_get_pt_stats(hsg_ctx* ctx, uint64_t* accepted, uint64_t* n_calls);
 
+/* Diagnostics of the temperature random walk (Sec. 4), since creation (or as
+   restored from a checkpoint), host buffers (either may be NULL):
+     moved   uint64[n_samples][n_replicas][n_temps]: PT passes after which the
+             configuration that held temperature slot t before the pass holds
+             another slot (p_diff(T_t) = moved / n_passes)
+     tunnel  uint32[n_samples][n_replicas][n_temps] by memory slot: closed loops
+             T_1 -> T_{n_temps} -> T_1 the configuration has travelled
+             (tunnelling events); it starts at T_1 if it starts in slot 0
+   n_passes: PT passes done.  Synchronises. */
+hsg_status hsg_get_pt_diagnostics(hsg_ctx* ctx, uint64_t* moved, uint32_t* tunnel,
+                                  uint64_t* n_passes);
+
+/* Checkpoint and resume.  A checkpoint holds the whole state of the Markov
+   chain and its statistics: the spins exactly as stored, the temperature
+   permutations, inverse temperatures, last energies, sweep and PT counters,
+   PT acceptance counts and diagnostics.  It can be loaded into a context
+   created with the same samples (sizes, temperatures, J and H), replicas,
+   precision, coupling format and seed; the chain then continues bit for bit
+   as if it had not been interrupted (the step schedule does not matter).
+   The blob is host memory owned by the caller; hsg_checkpoint_size gives its
+   size.  Save and load synchronise.  Load returns HSG_EINVAL (and changes
+   nothing) for a blob of another context, a truncated or foreign blob. */
+hsg_status hsg_checkpoint_size(hsg_ctx* ctx, size_t* bytes);
+hsg_status hsg_checkpoint_save(hsg_ctx* ctx, void* buf, size_t bytes);
+hsg_status hsg_checkpoint_load(hsg_ctx* ctx, const void* buf, size_t bytes);
+
 typedef struct {
   int n_samples, n_temps, n_replicas;
   int W;                   /* systems per sample */

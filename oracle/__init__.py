@@ -190,6 +190,29 @@ class OracleSample:
         self.s = np.zeros((self.W, self.N, 3))
         lib().orc_init_spins(_dp(self.s), self.L, self.W, self.sys_base, self.seed, codec)
         self.perm = np.tile(np.arange(self.R_T, dtype=np.int32), (self.R_O, 1))
+        # temperature random-walk diagnostics (Sec. 4)
+        self.moved = np.zeros((self.R_O, self.R_T), dtype=np.int64)
+        self.tunnel = np.zeros((self.R_O, self.R_T), dtype=np.int64)
+        self._seen_bottom = self.perm == 0          # by memory slot: visited T_1
+        self._seen_top = np.zeros((self.R_O, self.R_T), dtype=bool)   # then T_R
+
+    def _diagnose(self, before: np.ndarray):
+        """After a PT pass: a slot counts as moved when the configuration it held
+        before the pass is elsewhere; a configuration that is back at T_1 after
+        visiting T_R after T_1 has completed one tunnelling loop."""
+        if self.R_T < 2:
+            return
+        self.moved += (self.perm != before)
+        for r in range(self.R_O):
+            for t in range(self.R_T):
+                m = self.perm[r, t]
+                if t == 0:
+                    if self._seen_top[r, m]:
+                        self.tunnel[r, m] += 1
+                    self._seen_bottom[r, m] = True
+                    self._seen_top[r, m] = False
+                elif t == self.R_T - 1 and self._seen_bottom[r, m]:
+                    self._seen_top[r, m] = True
 
     def beta_sys(self) -> np.ndarray:
         b = np.zeros(self.W)
@@ -212,8 +235,10 @@ class OracleSample:
         return E
 
     def pt(self, E, pt_step):
+        before = self.perm.copy()
         self.perm, acc = pt(E, self.temps, self.perm, self.R_O, self.R_T, self.chain_base,
                             self.seed, pt_step)
+        self._diagnose(before)
         return acc
 
     def measure(self):

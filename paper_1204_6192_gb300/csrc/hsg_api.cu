@@ -59,6 +59,11 @@ struct hsg_ctx {
   int* d_perm = nullptr;
   double* d_E = nullptr;
   unsigned long long* d_acc = nullptr;
+  unsigned long long* d_moved = nullptr;   // PT diagnostics [ns][R_O][R_T]
+  unsigned char* d_tstate = nullptr;
+  unsigned int* d_tunnel = nullptr;
+  uint64_t seed = 0;
+  uint64_t shape_hash = 0;            // lattice sizes, temperatures and records (checkpoints)
   unsigned long long* d_counters = nullptr;
   double* d_mpart = nullptr;
   double* d_opart = nullptr;          // overlap partials (allocated at first use)
@@ -214,6 +219,9 @@ PTParams pt_params(hsg_ctx* c, int sweeps_per_call, int bump_pt) {
   p.perm = c->d_perm;
   p.beta = c->d_beta;
   p.accepted = c->d_acc;
+  p.moved = c->d_moved;
+  p.tstate = c->d_tstate;
+  p.tunnel = c->d_tunnel;
   p.counters = c->d_counters;
   p.n_samples = c->ns;
   p.R_O = c->R_O;
@@ -434,6 +442,40 @@ hsg_status run_steps(hsg_ctx* c, int n_steps) {
   return HSG_OK;
 }
 
+// The device arrays that, with the spins, make up the state of the Markov chain
+// and its statistics (what a checkpoint holds and the autotuner restores).
+std::vector<std::pair<void*, size_t>> chain_regions(hsg_ctx* c) {
+  const size_t n_perm = (size_t)c->ns * c->R_O * c->R_T;
+  const size_t n_acc = (size_t)c->ns * c->R_O * std::max(1, c->R_T - 1);
+  return {{c->d_perm, sizeof(int) * n_perm},
+          {c->d_beta, sizeof(float) * c->ns * (size_t)c->Wp},
+          {c->d_E, sizeof(double) * c->ns * (size_t)c->Wp},
+          {c->d_acc, sizeof(unsigned long long) * n_acc},
+          {c->d_counters, sizeof(unsigned long long) * 2},
+          {c->d_moved, sizeof(unsigned long long) * n_perm},
+          {c->d_tstate, sizeof(unsigned char) * n_perm},
+          {c->d_tunnel, sizeof(unsigned int) * n_perm}};
+}
+
+size_t chain_state_bytes(hsg_ctx* c) {
+  size_t n = 0;
+  for (auto& r : chain_regions(c)) n += r.second;
+  return n;
+}
+
+// Copy the chain-state regions to or from consecutive host bytes (stream-ordered).
+hsg_status copy_chain_state(hsg_ctx* c, unsigned char* host, bool to_host) {
+  size_t off = 0;
+  for (auto& r : chain_regions(c)) {
+    if (to_host)
+      HSG_CUDA(c, cudaMemcpyAsync(host + off, r.first, r.second, cudaMemcpyDeviceToHost, c->stream));
+    else
+      HSG_CUDA(c, cudaMemcpyAsync(r.first, host + off, r.second, cudaMemcpyHostToDevice, c->stream));
+    off += r.second;
+  }
+  return HSG_OK;
+}
+
 // Autotuner: the schedules and chunks-per-thread settings compute identical
 // results, so they are timed on the live context (2 steps each, after a warm-up
 // step) and the fastest is kept; the state is saved before and restored after,
@@ -468,19 +510,11 @@ hsg_status autotune(hsg_ctx* c) {
   // save the state the trial steps will change
   void* spins_copy = nullptr;
   HSG_CUDA(c, cudaMalloc(&spins_copy, c->spin_bytes));
-  const size_t n_perm = (size_t)c->ns * c->R_O * c->R_T;
-  const size_t n_acc = (size_t)c->ns * c->R_O * std::max(1, c->R_T - 1);
-  std::vector<int> perm(n_perm);
-  std::vector<float> beta((size_t)c->ns * c->Wp);
-  std::vector<double> E((size_t)c->ns * c->Wp);
-  std::vector<unsigned long long> acc(n_acc), cnt(2);
+  std::vector<unsigned char> saved(chain_state_bytes(c));
   cudaStream_t st = c->stream;
+  const bool e_valid = c->e_valid;
   HSG_CUDA(c, cudaMemcpyAsync(spins_copy, c->spins, c->spin_bytes, cudaMemcpyDeviceToDevice, st));
-  HSG_CUDA(c, cudaMemcpyAsync(perm.data(), c->d_perm, sizeof(int) * n_perm, cudaMemcpyDeviceToHost, st));
-  HSG_CUDA(c, cudaMemcpyAsync(beta.data(), c->d_beta, sizeof(float) * beta.size(), cudaMemcpyDeviceToHost, st));
-  HSG_CUDA(c, cudaMemcpyAsync(E.data(), c->d_E, sizeof(double) * E.size(), cudaMemcpyDeviceToHost, st));
-  HSG_CUDA(c, cudaMemcpyAsync(acc.data(), c->d_acc, sizeof(unsigned long long) * n_acc, cudaMemcpyDeviceToHost, st));
-  HSG_CUDA(c, cudaMemcpyAsync(cnt.data(), c->d_counters, sizeof(unsigned long long) * 2, cudaMemcpyDeviceToHost, st));
+  HSG_TRY(copy_chain_state(c, saved.data(), true));
   HSG_CUDA(c, cudaStreamSynchronize(st));
 
   std::vector<int> gpts;
@@ -529,13 +563,10 @@ hsg_status autotune(hsg_ctx* c) {
   cudaEventDestroy(e1);
   // restore
   HSG_CUDA(c, cudaMemcpyAsync(c->spins, spins_copy, c->spin_bytes, cudaMemcpyDeviceToDevice, st));
-  HSG_CUDA(c, cudaMemcpyAsync(c->d_perm, perm.data(), sizeof(int) * n_perm, cudaMemcpyHostToDevice, st));
-  HSG_CUDA(c, cudaMemcpyAsync(c->d_beta, beta.data(), sizeof(float) * beta.size(), cudaMemcpyHostToDevice, st));
-  HSG_CUDA(c, cudaMemcpyAsync(c->d_E, E.data(), sizeof(double) * E.size(), cudaMemcpyHostToDevice, st));
-  HSG_CUDA(c, cudaMemcpyAsync(c->d_acc, acc.data(), sizeof(unsigned long long) * n_acc, cudaMemcpyHostToDevice, st));
-  HSG_CUDA(c, cudaMemcpyAsync(c->d_counters, cnt.data(), sizeof(unsigned long long) * 2, cudaMemcpyHostToDevice, st));
+  HSG_TRY(copy_chain_state(c, saved.data(), false));
   HSG_CUDA(c, cudaStreamSynchronize(st));
   HSG_CUDA(c, cudaFree(spins_copy));
+  c->e_valid = e_valid;
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune_cache[key] = bestc;
@@ -723,6 +754,9 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   HSG_ALLOC(c->d_acc, sizeof(unsigned long long) * n_samples * n_replicas * std::max(1, n_temps - 1));
   HSG_ALLOC(c->d_counters, sizeof(unsigned long long) * 2);
   HSG_ALLOC(c->d_bar, sizeof(unsigned int) * 4);
+  HSG_ALLOC(c->d_moved, sizeof(unsigned long long) * n_samples * n_replicas * n_temps);
+  HSG_ALLOC(c->d_tstate, sizeof(unsigned char) * n_samples * n_replicas * n_temps);
+  HSG_ALLOC(c->d_tunnel, sizeof(unsigned int) * n_samples * n_replicas * n_temps);
 #undef HSG_ALLOC
 
   std::vector<double> inv(n_samples * (size_t)n_temps);
@@ -736,7 +770,26 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
         beta[(size_t)s * Wp + r * n_temps + t] = (float)inv[(size_t)s * n_temps + t];
       }
   }
+  // tunnelling state: the configuration at T_1 (memory slot 0 of each chain) starts at that end
+  std::vector<unsigned char> tstate(perm.size(), 0);
+  for (size_t k = 0; k < tstate.size(); k += n_temps) tstate[k] = 1;
   const unsigned long long zero2[2] = {0ull, 0ull};
+  c->seed = seed;
+  {
+    // FNV-1a over what a checkpoint must agree on: sizes, temperatures, records
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&h](const void* d, size_t n) {
+      const unsigned char* b = (const unsigned char*)d;
+      for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    };
+    mix(L, sizeof(int) * n_samples);
+    mix(temps, sizeof(double) * n_samples * n_temps);
+    const int dims[4] = {n_temps, n_replicas, opt.precision, opt.j_fp16 ? 1 : 0};
+    mix(dims, sizeof(dims));
+    if (c->j16) mix(rech.data(), rech.size() * sizeof(__half));
+    else mix(recf.data(), recf.size() * sizeof(float));
+    c->shape_hash = h;
+  }
 #define HSG_UP(dst, src, bytes)                                                     \
   e = cudaMemcpy((dst), (src), (bytes), cudaMemcpyHostToDevice);                   \
   if (e != cudaSuccess) {                                                          \
@@ -751,8 +804,11 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   HSG_UP(c->d_perm, perm.data(), sizeof(int) * perm.size());
   HSG_UP(c->d_beta, beta.data(), sizeof(float) * beta.size());
   HSG_UP(c->d_counters, zero2, sizeof(zero2));
+  HSG_UP(c->d_tstate, tstate.data(), tstate.size());
 #undef HSG_UP
   e = cudaMemset(c->d_acc, 0, sizeof(unsigned long long) * n_samples * n_replicas * std::max(1, n_temps - 1));
+  if (e == cudaSuccess) e = cudaMemset(c->d_moved, 0, sizeof(unsigned long long) * perm.size());
+  if (e == cudaSuccess) e = cudaMemset(c->d_tunnel, 0, sizeof(unsigned int) * perm.size());
   if (e == cudaSuccess) e = cudaMemset(c->d_E, 0, sizeof(double) * n_samples * Wp);
   if (e == cudaSuccess) e = cudaMemset(c->d_bar, 0, sizeof(unsigned int) * 4);
   if (e == cudaSuccess) e = cudaMemset(c->spins, 0, c->spin_bytes);
@@ -1066,6 +1122,96 @@ hsg_status hsg_get_pt_stats(hsg_ctx* c, uint64_t* accepted, uint64_t* n_calls) {
   HSG_CUDA(c, cudaStreamSynchronize(c->stream));
   HSG_TRY(poll_device_error(c));
   if (n_calls) *n_calls = cnt[1];
+  return HSG_OK;
+}
+
+hsg_status hsg_get_pt_diagnostics(hsg_ctx* c, uint64_t* moved, uint32_t* tunnel, uint64_t* n_passes) {
+  HSG_CHECK_CTX(c);
+  HSG_CUDA(c, cudaSetDevice(c->device));
+  const size_t n = (size_t)c->ns * c->R_O * c->R_T;
+  unsigned long long cnt[2];
+  if (moved)
+    HSG_CUDA(c, cudaMemcpyAsync(moved, c->d_moved, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, c->stream));
+  if (tunnel)
+    HSG_CUDA(c, cudaMemcpyAsync(tunnel, c->d_tunnel, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost, c->stream));
+  HSG_CUDA(c, cudaMemcpyAsync(cnt, c->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+  HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  HSG_TRY(poll_device_error(c));
+  if (n_passes) *n_passes = cnt[1];
+  return HSG_OK;
+}
+
+namespace {
+// checkpoint blob: this header, the stored spins as they are in device memory,
+// then the chain-state regions in chain_regions order
+struct CheckpointHeader {
+  char magic[8];
+  uint32_t version;
+  uint32_t fmt, j16, ns, R_O, R_T, W, Wp, e_valid;
+  uint64_t seed, shape_hash, spin_bytes, state_bytes;
+};
+const char kMagic[8] = {'H', 'S', 'G', 'C', 'K', 'P', 'T', '1'};
+}  // namespace
+
+hsg_status hsg_checkpoint_size(hsg_ctx* c, size_t* bytes) {
+  HSG_CHECK_CTX(c);
+  if (!bytes) return bad_arg(c, "bytes is NULL");
+  *bytes = sizeof(CheckpointHeader) + c->spin_bytes + chain_state_bytes(c);
+  return HSG_OK;
+}
+
+hsg_status hsg_checkpoint_save(hsg_ctx* c, void* buf, size_t bytes) {
+  HSG_CHECK_CTX(c);
+  if (!buf) return bad_arg(c, "buf is NULL");
+  const size_t need = sizeof(CheckpointHeader) + c->spin_bytes + chain_state_bytes(c);
+  if (bytes < need) return bad_arg(c, "checkpoint buffer too small");
+  HSG_CUDA(c, cudaSetDevice(c->device));
+  CheckpointHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, kMagic, 8);
+  h.version = 1;
+  h.fmt = (uint32_t)c->fmt;
+  h.j16 = c->j16 ? 1u : 0u;
+  h.ns = (uint32_t)c->ns;
+  h.R_O = (uint32_t)c->R_O;
+  h.R_T = (uint32_t)c->R_T;
+  h.W = (uint32_t)c->W;
+  h.Wp = (uint32_t)c->Wp;
+  h.e_valid = c->e_valid ? 1u : 0u;
+  h.seed = c->seed;
+  h.shape_hash = c->shape_hash;
+  h.spin_bytes = c->spin_bytes;
+  h.state_bytes = chain_state_bytes(c);
+  unsigned char* out = (unsigned char*)buf;
+  std::memcpy(out, &h, sizeof(h));
+  HSG_CUDA(c, cudaMemcpyAsync(out + sizeof(h), c->spins, c->spin_bytes, cudaMemcpyDeviceToHost, c->stream));
+  HSG_TRY(copy_chain_state(c, out + sizeof(h) + c->spin_bytes, true));
+  HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  HSG_TRY(poll_device_error(c));
+  return HSG_OK;
+}
+
+hsg_status hsg_checkpoint_load(hsg_ctx* c, const void* buf, size_t bytes) {
+  HSG_CHECK_CTX(c);
+  if (!buf) return bad_arg(c, "buf is NULL");
+  if (bytes < sizeof(CheckpointHeader)) return bad_arg(c, "checkpoint too short");
+  CheckpointHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  if (std::memcmp(h.magic, kMagic, 8) != 0 || h.version != 1) return bad_arg(c, "not a checkpoint");
+  if (h.fmt != (uint32_t)c->fmt || h.j16 != (c->j16 ? 1u : 0u) || h.ns != (uint32_t)c->ns ||
+      h.R_O != (uint32_t)c->R_O || h.R_T != (uint32_t)c->R_T || h.W != (uint32_t)c->W ||
+      h.Wp != (uint32_t)c->Wp || h.seed != c->seed || h.shape_hash != c->shape_hash ||
+      h.spin_bytes != c->spin_bytes || h.state_bytes != chain_state_bytes(c))
+    return bad_arg(c, "checkpoint of a different context shape, disorder, precision or seed");
+  if (bytes < sizeof(h) + h.spin_bytes + h.state_bytes) return bad_arg(c, "checkpoint truncated");
+  HSG_CUDA(c, cudaSetDevice(c->device));
+  const unsigned char* in = (const unsigned char*)buf;
+  HSG_CUDA(c, cudaMemcpyAsync(c->spins, in + sizeof(h), c->spin_bytes, cudaMemcpyHostToDevice, c->stream));
+  HSG_TRY(copy_chain_state(c, const_cast<unsigned char*>(in) + sizeof(h) + c->spin_bytes, false));
+  // the host buffer may be released on return
+  HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  HSG_TRY(poll_device_error(c));
+  c->e_valid = h.e_valid != 0;
   return HSG_OK;
 }
 

@@ -79,6 +79,9 @@ struct PTParams {
   int* perm;                // [n_samples][R_O][R_T]
   float* beta;              // [n_samples][Wp]
   unsigned long long* accepted;   // [n_samples][R_O][R_T-1]
+  unsigned long long* moved;      // [n_samples][R_O][R_T]: passes after which the slot's configuration moved
+  unsigned char* tstate;          // [n_samples][R_O][R_T] by memory slot: 0 none, 1 last end T_1, 2 then T_R
+  unsigned int* tunnel;           // [n_samples][R_O][R_T] by memory slot: closed loops T_1 -> T_R -> T_1
   unsigned long long* counters;
   int n_samples, R_O, R_T, Wp;
   uint32_t seed_lo, seed_hi;

@@ -229,10 +229,6 @@ __device__ __forceinline__ void energy_final2_warp(const EnergyParams& p, int s,
   if (lane == 0) p.E[(long long)s * p.Wp + w] = e;
 }
 
-// Parallel tempering, Eq. (4), for chain c = (sample, replica): pairs (k, k+1)
-// from the lowest temperature up, accepted with min[1, exp(dbeta dE)]; an
-// accepted exchange swaps the temperatures of the two configurations; then
-// the chain's systems get their new inverse temperatures.
 // Metropolis decision of a PT pair (Eq. 4): accept iff x >= 0 or u < exp(x),
 // decided exactly as in binary64.  u >= 2^-24 > exp(-17), so x < -17 always
 // rejects.  Otherwise exp is evaluated in FP32 (expf: within 2 ulp; rounding
@@ -248,6 +244,13 @@ __device__ __forceinline__ bool pt_accept(double x, float u) {
   return (double)u < exp(x);
 }
 
+// Parallel tempering, Eq. (4), for chain c = (sample, replica): pairs (k, k+1)
+// from the lowest temperature up, accepted with min[1, exp(dbeta dE)]; an
+// accepted exchange swaps the temperatures of the two configurations; then
+// the chain's systems get their new inverse temperatures.  Diagnostics of the
+// temperature random walk (Sec. 4): per slot, the passes after which the
+// configuration that held it has moved (p_diff = moved / passes), and per
+// configuration the closed loops T_1 -> T_R -> T_1 (tunnelling events).
 template <bool CG>
 __device__ __forceinline__ void pt_chain(const PTParams& p, int c, uint32_t step) {
   const int s = c / p.R_O, r = c - s * p.R_O;
@@ -255,6 +258,8 @@ __device__ __forceinline__ void pt_chain(const PTParams& p, int c, uint32_t step
   const double* E = p.E + (long long)s * p.Wp + r * p.R_T;
   const double* ib = p.inv_temps + (long long)s * p.R_T;
   if (p.bump_pt) {
+    unsigned long long* moved = p.moved + (long long)c * p.R_T;
+    bool prev_acc = false;
     // the uniforms do not depend on the decisions: they are drawn 32 pairs at a
     // time ahead of the sequential chain, so the Philox evaluations overlap
     float uk[32];
@@ -272,11 +277,25 @@ __device__ __forceinline__ void pt_chain(const PTParams& p, int c, uint32_t step
       const double dE = (CG ? __ldcg(E + b) : E[b]) - (CG ? __ldcg(E + a) : E[a]);
       const double x = dbeta * dE;
       const bool acc = pt_accept(x, uk[k & 31]);
+      // the configuration that held slot k before the pass moved iff pair (k-1, k)
+      // moved it down or, failing that, pair (k, k+1) moved it up
+      if (acc || prev_acc) moved[k] += 1ull;
+      prev_acc = acc;
       if (acc) {
         perm[k] = b;
         perm[k + 1] = a;
         p.accepted[(long long)c * (p.R_T - 1) + k] += 1ull;
       }
+    }
+    if (p.R_T > 1) {
+      if (prev_acc) moved[p.R_T - 1] += 1ull;
+      // tunnelling: a configuration that reaches T_1 after T_R after T_1 closes a loop
+      unsigned char* ts = p.tstate + (long long)c * p.R_T;
+      unsigned int* tn = p.tunnel + (long long)c * p.R_T;
+      const int bottom = perm[0], top = perm[p.R_T - 1];
+      if (ts[bottom] == 2) tn[bottom] += 1u;
+      ts[bottom] = 1;
+      if (ts[top] == 1) ts[top] = 2;
     }
   }
   float* beta = p.beta + (long long)s * p.Wp + r * p.R_T;

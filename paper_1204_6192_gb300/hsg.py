@@ -91,6 +91,11 @@ def lib() -> ctypes.CDLL:
         "hsg_get_perm": (ip, [vp, ctypes.POINTER(ctypes.c_int32)]),
         "hsg_get_pt_stats": (ip, [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
         "hsg_get_info": (ip, [vp, ctypes.POINTER(Info)]),
+        "hsg_get_pt_diagnostics": (ip, [vp, ctypes.POINTER(ctypes.c_uint64),
+                                        ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint64)]),
+        "hsg_checkpoint_size": (ip, [vp, ctypes.POINTER(ctypes.c_size_t)]),
+        "hsg_checkpoint_save": (ip, [vp, vp, ctypes.c_size_t]),
+        "hsg_checkpoint_load": (ip, [vp, vp, ctypes.c_size_t]),
         "hsg_sync": (ip, [vp]),
         "hsg_last_error": (ctypes.c_char_p, [vp]),
         "hsg_status_string": (ctypes.c_char_p, [ip]),
@@ -292,6 +297,28 @@ class Context:
         self._check(lib().hsg_get_pt_stats(self._ctx, _ptr(acc, ctypes.c_uint64), ctypes.byref(n)))
         return acc, int(n.value)
 
+    def pt_diagnostics(self):
+        """(moved [ns, R_O, R_T] uint64, tunnel [ns, R_O, R_T] uint32 by memory slot, passes)."""
+        shape = (self.n_samples, self.n_replicas, self.n_temps)
+        moved = np.zeros(shape, dtype=np.uint64)
+        tunnel = np.zeros(shape, dtype=np.uint32)
+        n = ctypes.c_uint64()
+        self._check(lib().hsg_get_pt_diagnostics(self._ctx, _ptr(moved, ctypes.c_uint64),
+                                                 _ptr(tunnel, ctypes.c_uint32), ctypes.byref(n)))
+        return moved, tunnel, int(n.value)
+
+    def checkpoint(self) -> bytes:
+        """The chain's state as a bytes blob (hsg_checkpoint_save)."""
+        n = ctypes.c_size_t()
+        self._check(lib().hsg_checkpoint_size(self._ctx, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        self._check(lib().hsg_checkpoint_save(self._ctx, buf, n.value))
+        return buf.raw
+
+    def restore(self, blob: bytes):
+        """Load a blob from checkpoint() (hsg_checkpoint_load)."""
+        self._check(lib().hsg_checkpoint_load(self._ctx, blob, len(blob)))
+
     def info(self) -> Info:
         i = Info()
         self._check(lib().hsg_get_info(self._ctx, ctypes.byref(i)))
@@ -348,5 +375,8 @@ hsg_set_spins_dev = Context.set_spins_dev
 hsg_get_perm = Context.get_perm
 hsg_get_pt_stats = Context.pt_stats
 hsg_get_info = Context.info
+hsg_get_pt_diagnostics = Context.pt_diagnostics
+hsg_checkpoint_save = Context.checkpoint
+hsg_checkpoint_load = Context.restore
 hsg_sync = Context.sync
 hsg_destroy = Context.close

@@ -209,7 +209,92 @@ def test_pt_with_injected_energies_bit_exact():
             np.testing.assert_array_equal(perm[s], o.perm)
     acc, n = ctx.pt_stats()
     assert n == 20 and acc.sum() > 0
+    moved, tunnel, passes = ctx.pt_diagnostics()
+    assert passes == 20
+    for s, o in enumerate(orc.samples):
+        np.testing.assert_array_equal(moved[s], o.moved)
+        np.testing.assert_array_equal(tunnel[s], o.tunnel)
     ctx.close()
+
+
+def test_pt_diagnostics_hand_worked_gpu():
+    """tests/golden/pt_tunnelling.txt on the device: four forced passes with the
+    energies injected; permutations, moved counts and the tunnelling loop agree
+    with the hand-worked values."""
+    import os
+    g = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "pt_tunnelling.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, *v = line.split()
+                g[k] = np.array([float(x) for x in v])
+    smp = inputs.Sample(L=4, J=np.zeros((64, 3)), H=None, temps=g["temps"])
+    ctx = hsg.Context([smp], 1, 5)
+    for k in range(4):
+        ctx.pt_exchange_energies(g[f"energies_{k}"][None, :])
+        np.testing.assert_array_equal(ctx.get_perm()[0, 0], g[f"perm_{k}"])
+    moved, tunnel, passes = ctx.pt_diagnostics()
+    assert passes == 4
+    np.testing.assert_array_equal(moved[0, 0], g["moved"])
+    np.testing.assert_array_equal(tunnel[0, 0], g["tunnel"])
+    ctx.close()
+
+
+@pytest.mark.parametrize("variant", [hsg.VARIANT_TWO_PASS, hsg.VARIANT_PERSISTENT])
+def test_checkpoint_resume_is_bit_identical(variant):
+    """Steps, checkpoint, more steps; a fresh context restored from the
+    checkpoint (with the other schedule) and run for the same steps ends in the
+    identical state: spins, energies, permutations, counters, PT statistics and
+    diagnostics."""
+    samples = [inputs.small_sample(L, n_temps=6, h_r=0.2, disorder_seed=L) for L in (4, 8)]
+    other = hsg.VARIANT_PERSISTENT if variant == hsg.VARIANT_TWO_PASS else hsg.VARIANT_TWO_PASS
+
+    def state(c):
+        return ([x.copy() for x in c.get_spins()], c.last_energies(), c.get_perm(), c.pt_stats()[0],
+                c.pt_diagnostics(), c.info().sweep_count, c.info().pt_count)
+
+    a = hsg.Context(samples, 2, 4, precision="fp16", j_fp16=True, variant=variant)
+    a.step(3)
+    blob = a.checkpoint()
+    a.step(2)
+    ref = state(a)
+    a.close()
+    b = hsg.Context(samples, 2, 4, precision="fp16", j_fp16=True, variant=other)
+    b.step(1)                       # a different state, overwritten by the restore
+    b.restore(blob)
+    b.step(2)
+    got = state(b)
+    b.close()
+    for x, y in zip(ref[0], got[0]):
+        np.testing.assert_array_equal(x, y)
+    np.testing.assert_array_equal(ref[1], got[1])
+    np.testing.assert_array_equal(ref[2], got[2])
+    np.testing.assert_array_equal(ref[3], got[3])
+    for x, y in zip(ref[4], got[4]):
+        np.testing.assert_array_equal(x, y)
+    assert ref[5:] == got[5:] == (30, 5)
+
+
+def test_checkpoint_rejects_other_contexts():
+    smp = inputs.small_sample(6, n_temps=4, disorder_seed=1)
+    a = hsg.Context([smp], 2, 3)
+    a.step(1)
+    blob = a.checkpoint()
+    perm = a.get_perm()
+    for make in (lambda: hsg.Context([smp], 2, 4),                                   # seed
+                 lambda: hsg.Context([inputs.small_sample(6, n_temps=4, disorder_seed=2)], 2, 3),
+                 lambda: hsg.Context([smp], 2, 3, precision="fp16")):
+        c = make()
+        with pytest.raises(hsg.HsgError) as ei:
+            c.restore(blob)
+        assert ei.value.status == 1
+        c.close()
+    for bad in (blob[:100], b"x" * len(blob), blob[:-8]):
+        with pytest.raises(hsg.HsgError):
+            a.restore(bad)
+    np.testing.assert_array_equal(a.get_perm(), perm)     # untouched by the failed loads
+    a.restore(blob)
+    a.close()
 
 
 def test_step_with_pt_matches_oracle():

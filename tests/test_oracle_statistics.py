@@ -228,3 +228,33 @@ def test_oracle_matches_its_recorded_run():
     np.testing.assert_array_equal(now["perm"], g["perm"])
     np.testing.assert_allclose(now["E"], g["E"], rtol=1e-10)
     np.testing.assert_allclose(now["q"], g["q"], rtol=0, atol=1e-10)
+
+
+def test_pt_diagnostics_hand_worked(orc):
+    """tests/golden/pt_tunnelling.txt: four forced passes; the oracle's moved
+    counts (by comparing the permutation before and after each pass) and its
+    tunnelling count match the hand-worked values."""
+    g = read_golden("pt_tunnelling.txt")
+    o = orc.OracleSample(4, np.zeros((64, 3)), None, g["temps"], 1, 0, 0, 5, 0)
+    for k in range(4):
+        o.pt(g[f"energies_{k}"], k)
+        np.testing.assert_array_equal(o.perm[0], g[f"perm_{k}"])
+    np.testing.assert_array_equal(o.moved[0], g["moved"])
+    np.testing.assert_array_equal(o.tunnel[0], g["tunnel"])
+
+
+def test_pt_diagnostics_consistent_with_acceptances(orc):
+    """Random passes: with the pairs visited upward, the configuration at slot t
+    moves iff pair (t-1, t) or pair (t, t+1) accepts, so the oracle's moved
+    counts (taken from the permutations) equal the sums of a_{t-1} | a_t over
+    the passes (taken from the acceptances)."""
+    rng = np.random.default_rng(3)
+    temps = np.array([0.4, 0.5, 0.62, 0.77, 0.95])
+    o = orc.OracleSample(4, np.zeros((64, 3)), None, temps, 2, 0, 0, 9, 0)
+    expect = np.zeros((2, 5), dtype=np.int64)
+    for k in range(300):
+        E = rng.normal(scale=3.0, size=10)
+        acc = o.pt(E, k)
+        a = np.pad(acc.astype(bool), ((0, 0), (1, 1)))
+        expect += a[:, :-1] | a[:, 1:]
+    np.testing.assert_array_equal(o.moved, expect)
