@@ -218,8 +218,21 @@ hsg_status hsg_set_spins_dev(hsg_ctx* ctx, const float* xyz_dev);
 hsg_status hsg_get_perm(hsg_ctx* ctx, int32_t* perm);
 
 /* Accepted PT exchanges per pair since creation, host
-   uint64[n_samples][n_replicas][n_temps - 1]; and the number of PT calls. */
+   uint64[n_samples][n_replicas][n_temps - 1]; and the number of PT passes
+   sample 0 has done. */
 hsg_status hsg_get_pt_stats(hsg_ctx* ctx, uint64_t* accepted, uint64_t* n_calls);
+
+/* Per-sample run lengths.  active: host uint8[n_samples], nonzero = the sample
+   takes part in later hsg_step / hsg_sweep_* / hsg_pt_exchange* calls; a
+   frozen sample keeps its spins, temperatures, energies and counters.  NULL
+   makes every sample active (the state after creation).  Each sample's sweep
+   and PT counters key its own random numbers, so a sample's chain depends
+   only on how many steps it took, not on the other samples.  Synchronises. */
+hsg_status hsg_set_active(hsg_ctx* ctx, const uint8_t* active);
+
+/* Sweeps and PT passes each sample has done, host uint64[n_samples] each
+   (either may be NULL).  Synchronises. */
+hsg_status hsg_get_counters(hsg_ctx* ctx, uint64_t* sweeps, uint64_t* pt_passes);
 
 /* Diagnostics of the temperature random walk (Sec. 4), since creation (or as
    restored from a checkpoint), host buffers (either may be NULL):
@@ -229,7 +242,7 @@ hsg_status hsg_get_pt_stats(hsg_ctx* ctx, uint64_t* accepted, uint64_t* n_calls)
      tunnel  uint32[n_samples][n_replicas][n_temps] by memory slot: closed loops
              T_1 -> T_{n_temps} -> T_1 the configuration has travelled
              (tunnelling events); it starts at T_1 if it starts in slot 0
-   n_passes: PT passes done.  Synchronises. */
+   n_passes: PT passes sample 0 has done.  Synchronises. */
 hsg_status hsg_get_pt_diagnostics(hsg_ctx* ctx, uint64_t* moved, uint32_t* tunnel,
                                   uint64_t* n_passes);
 
@@ -256,8 +269,8 @@ typedef struct {
   long long total_spins;   /* total_sites * W */
   long long spin_bytes;    /* device bytes of stored spins */
   long long rec_bytes;     /* device bytes of coupling/field records */
-  uint64_t sweep_count;    /* sweeps done (the HB counter word) */
-  uint64_t pt_count;       /* PT passes done */
+  uint64_t sweep_count;    /* sweeps sample 0 has done (hsg_get_counters: every sample) */
+  uint64_t pt_count;       /* PT passes sample 0 has done */
   void* stream;            /* the cudaStream_t the context runs on */
   int chunks_per_thread;   /* sweep kernels: chunks of 4 systems one thread walks */
   int n_passes;            /* system-blocked passes per step (1: no blocking) */

@@ -271,23 +271,31 @@ class OracleSim:
         for k, smp in enumerate(samples):
             o = OracleSample(smp.L, smp.J, smp.H, smp.temps, n_replicas, k * Wp, k * n_replicas,
                              seed, self.codec)
+            o.sweep = 0         # the sample's own sweep counter (keys its heat-bath numbers)
+            o.pt_step = 0       # and PT pass counter
             self.samples.append(o)
-        self.sweep = 0
-        self.pt_step = 0
+        self.active = [True] * len(self.samples)
+
+    def set_active(self, active=None):
+        """Samples with a False entry are frozen in later sweeps, steps and PT passes."""
+        self.active = [True] * len(self.samples) if active is None else [bool(a) for a in active]
+
+    def _running(self):
+        return [o for o, a in zip(self.samples, self.active) if a]
 
     def sweep_or(self, n: int = 1):
         for _ in range(n):
-            for o in self.samples:
+            for o in self._running():
                 o.or_half(0)
                 o.or_half(1)
-            self.sweep += 1
+                o.sweep += 1
 
     def sweep_hb(self, n: int = 1):
         for _ in range(n):
-            for o in self.samples:
-                o.hb_half(0, self.sweep)
-                o.hb_half(1, self.sweep)
-            self.sweep += 1
+            for o in self._running():
+                o.hb_half(0, o.sweep)
+                o.hb_half(1, o.sweep)
+                o.sweep += 1
 
     def energies(self) -> List[np.ndarray]:
         return [o.energies() for o in self.samples]
@@ -295,8 +303,13 @@ class OracleSim:
     def pt_exchange(self, energies: Optional[List[np.ndarray]] = None):
         if energies is None:
             energies = self.energies()
-        acc = [o.pt(E, self.pt_step) for o, E in zip(self.samples, energies)]
-        self.pt_step += 1
+        acc = []
+        for o, E, a in zip(self.samples, energies, self.active):
+            if a:
+                acc.append(o.pt(E, o.pt_step))
+                o.pt_step += 1
+            else:
+                acc.append(np.zeros((o.R_O, max(o.R_T - 1, 1)), dtype=np.int32))
         return acc
 
     def step(self, n: int = 1, n_hb: int = 1, n_or: int = 5):

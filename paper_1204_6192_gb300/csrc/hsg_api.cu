@@ -64,7 +64,8 @@ struct hsg_ctx {
   unsigned int* d_tunnel = nullptr;
   uint64_t seed = 0;
   uint64_t shape_hash = 0;            // lattice sizes, temperatures and records (checkpoints)
-  unsigned long long* d_counters = nullptr;
+  unsigned long long* d_counters = nullptr;   // [ns][2]: sweeps done, PT passes done
+  unsigned char* d_active = nullptr;          // [ns]: 0 = sample frozen
   double* d_mpart = nullptr;
   double* d_opart = nullptr;          // overlap partials (allocated at first use)
   bool e_valid = false;               // d_E holds the energies of the current state
@@ -174,6 +175,7 @@ SweepParams sweep_params(hsg_ctx* c, int parity, int sweep_offset) {
   p.blocks = c->d_sweep_blocks;
   p.beta = c->d_beta;
   p.counters = c->d_counters;
+  p.active = c->d_active;
   p.G = c->G;
   p.Wp = c->Wp;
   p.GPT = c->GPT;
@@ -202,6 +204,7 @@ EnergyParams energy_params(hsg_ctx* c) {
   p.blocks = c->d_sweep_blocks;
   p.partials = c->d_epart;
   p.partials2 = c->d_epart2;
+  p.active = c->d_active;
   p.splits = c->e_splits;
   p.E = c->d_E;
   p.G = c->G;
@@ -223,6 +226,7 @@ PTParams pt_params(hsg_ctx* c, int sweeps_per_call, int bump_pt) {
   p.tstate = c->d_tstate;
   p.tunnel = c->d_tunnel;
   p.counters = c->d_counters;
+  p.active = c->d_active;
   p.n_samples = c->ns;
   p.R_O = c->R_O;
   p.R_T = c->R_T;
@@ -451,7 +455,7 @@ std::vector<std::pair<void*, size_t>> chain_regions(hsg_ctx* c) {
           {c->d_beta, sizeof(float) * c->ns * (size_t)c->Wp},
           {c->d_E, sizeof(double) * c->ns * (size_t)c->Wp},
           {c->d_acc, sizeof(unsigned long long) * n_acc},
-          {c->d_counters, sizeof(unsigned long long) * 2},
+          {c->d_counters, sizeof(unsigned long long) * 2 * c->ns},
           {c->d_moved, sizeof(unsigned long long) * n_perm},
           {c->d_tstate, sizeof(unsigned char) * n_perm},
           {c->d_tunnel, sizeof(unsigned int) * n_perm}};
@@ -752,7 +756,8 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   HSG_ALLOC(c->d_perm, sizeof(int) * n_samples * n_replicas * n_temps);
   HSG_ALLOC(c->d_E, sizeof(double) * n_samples * Wp);
   HSG_ALLOC(c->d_acc, sizeof(unsigned long long) * n_samples * n_replicas * std::max(1, n_temps - 1));
-  HSG_ALLOC(c->d_counters, sizeof(unsigned long long) * 2);
+  HSG_ALLOC(c->d_counters, sizeof(unsigned long long) * 2 * n_samples);
+  HSG_ALLOC(c->d_active, sizeof(unsigned char) * n_samples);
   HSG_ALLOC(c->d_bar, sizeof(unsigned int) * 4);
   HSG_ALLOC(c->d_moved, sizeof(unsigned long long) * n_samples * n_replicas * n_temps);
   HSG_ALLOC(c->d_tstate, sizeof(unsigned char) * n_samples * n_replicas * n_temps);
@@ -773,7 +778,6 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   // tunnelling state: the configuration at T_1 (memory slot 0 of each chain) starts at that end
   std::vector<unsigned char> tstate(perm.size(), 0);
   for (size_t k = 0; k < tstate.size(); k += n_temps) tstate[k] = 1;
-  const unsigned long long zero2[2] = {0ull, 0ull};
   c->seed = seed;
   {
     // FNV-1a over what a checkpoint must agree on: sizes, temperatures, records
@@ -803,7 +807,12 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   HSG_UP(c->d_inv_temps, inv.data(), sizeof(double) * inv.size());
   HSG_UP(c->d_perm, perm.data(), sizeof(int) * perm.size());
   HSG_UP(c->d_beta, beta.data(), sizeof(float) * beta.size());
-  HSG_UP(c->d_counters, zero2, sizeof(zero2));
+  {
+    const std::vector<unsigned long long> zeros(2 * (size_t)n_samples, 0ull);
+    const std::vector<unsigned char> ones((size_t)n_samples, 1);
+    HSG_UP(c->d_counters, zeros.data(), sizeof(unsigned long long) * zeros.size());
+    HSG_UP(c->d_active, ones.data(), ones.size());
+  }
   HSG_UP(c->d_tstate, tstate.data(), tstate.size());
 #undef HSG_UP
   e = cudaMemset(c->d_acc, 0, sizeof(unsigned long long) * n_samples * n_replicas * std::max(1, n_temps - 1));
@@ -876,7 +885,7 @@ hsg_status hsg_sweep_or(hsg_ctx* c, int n) {
   HSG_CUDA(c, cudaSetDevice(c->device));
   c->e_valid = false;
   for (int k = 0; k < n; ++k) HSG_TRY(half_sweeps(c, false, k));
-  HSG_CUDA(c, launch_bump(c->d_counters, n, 0, c->stream));
+  HSG_CUDA(c, launch_bump(c->d_counters, c->d_active, c->ns, n, 0, c->stream));
   return HSG_OK;
 }
 
@@ -887,7 +896,7 @@ hsg_status hsg_sweep_hb(hsg_ctx* c, int n) {
   HSG_CUDA(c, cudaSetDevice(c->device));
   c->e_valid = false;
   for (int k = 0; k < n; ++k) HSG_TRY(half_sweeps(c, true, k));
-  HSG_CUDA(c, launch_bump(c->d_counters, n, 0, c->stream));
+  HSG_CUDA(c, launch_bump(c->d_counters, c->d_active, c->ns, n, 0, c->stream));
   return HSG_OK;
 }
 
@@ -1122,6 +1131,34 @@ hsg_status hsg_get_pt_stats(hsg_ctx* c, uint64_t* accepted, uint64_t* n_calls) {
   HSG_CUDA(c, cudaStreamSynchronize(c->stream));
   HSG_TRY(poll_device_error(c));
   if (n_calls) *n_calls = cnt[1];
+  return HSG_OK;
+}
+
+hsg_status hsg_set_active(hsg_ctx* c, const uint8_t* active) {
+  HSG_CHECK_CTX(c);
+  HSG_CUDA(c, cudaSetDevice(c->device));
+  std::vector<unsigned char> a((size_t)c->ns, 1);
+  if (active)
+    for (int s = 0; s < c->ns; ++s) a[s] = active[s] ? 1 : 0;
+  HSG_CUDA(c, cudaMemcpyAsync(c->d_active, a.data(), a.size(), cudaMemcpyHostToDevice, c->stream));
+  // the host array may be released on return
+  HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  HSG_TRY(poll_device_error(c));
+  return HSG_OK;
+}
+
+hsg_status hsg_get_counters(hsg_ctx* c, uint64_t* sweeps, uint64_t* pt_passes) {
+  HSG_CHECK_CTX(c);
+  HSG_CUDA(c, cudaSetDevice(c->device));
+  std::vector<unsigned long long> cnt(2 * (size_t)c->ns);
+  HSG_CUDA(c, cudaMemcpyAsync(cnt.data(), c->d_counters, sizeof(unsigned long long) * cnt.size(),
+                              cudaMemcpyDeviceToHost, c->stream));
+  HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  HSG_TRY(poll_device_error(c));
+  for (int s = 0; s < c->ns; ++s) {
+    if (sweeps) sweeps[s] = cnt[2 * (size_t)s];
+    if (pt_passes) pt_passes[s] = cnt[2 * (size_t)s + 1];
+  }
   return HSG_OK;
 }
 

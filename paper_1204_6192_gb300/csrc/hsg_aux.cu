@@ -169,12 +169,12 @@ cudaError_t launch_energy(int fmt, bool j16, const EnergyParams& p, cudaStream_t
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_pt(const PTParams p) {
   const int n_chains = p.n_samples * p.R_O;
-  const uint32_t step = (uint32_t)p.counters[1];
-  for (int c = threadIdx.x; c < n_chains; c += blockDim.x) pt_chain<false>(p, c, step);
+  for (int c = threadIdx.x; c < n_chains; c += blockDim.x) pt_chain<false>(p, c);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    p.counters[0] += (unsigned long long)p.sweeps_per_call;
-    p.counters[1] += (unsigned long long)p.bump_pt;
+  for (int s = threadIdx.x; s < p.n_samples; s += blockDim.x) {
+    if (!p.active[s]) continue;
+    p.counters[2 * s] += (unsigned long long)p.sweeps_per_call;
+    p.counters[2 * s + 1] += (unsigned long long)p.bump_pt;
   }
 }
 
@@ -185,13 +185,18 @@ cudaError_t launch_pt(const PTParams& p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-__global__ void k_bump(unsigned long long* counters, int sweeps, int pts) {
-  counters[0] += (unsigned long long)sweeps;
-  counters[1] += (unsigned long long)pts;
+__global__ void k_bump(unsigned long long* counters, const unsigned char* active, int n_samples,
+                       int sweeps, int pts) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_samples; s += gridDim.x * blockDim.x) {
+    if (!active[s]) continue;
+    counters[2 * s] += (unsigned long long)sweeps;
+    counters[2 * s + 1] += (unsigned long long)pts;
+  }
 }
 
-cudaError_t launch_bump(unsigned long long* counters, int sweeps, int pts, cudaStream_t st) {
-  k_bump<<<1, 1, 0, st>>>(counters, sweeps, pts);
+cudaError_t launch_bump(unsigned long long* counters, const unsigned char* active, int n_samples,
+                        int sweeps, int pts, cudaStream_t st) {
+  k_bump<<<(n_samples + 255) / 256, 256, 0, st>>>(counters, active, n_samples, sweeps, pts);
   return cudaGetLastError();
 }
 

@@ -51,7 +51,8 @@ struct SweepParams {
   const SampleDev* samples;
   const int4* blocks;       // (sample, chunk group, first half-site) per block
   const float* beta;        // [n_samples][Wp]
-  const unsigned long long* counters;   // [0] sweeps done, [1] PT passes done
+  const unsigned long long* counters;   // [n_samples][2]: sweeps done, PT passes done
+  const unsigned char* active;          // [n_samples]: 0 = the sample is frozen
   int G, Wp, GPT;            // chunks per site, padded systems, chunks per thread
   uint32_t seed_lo, seed_hi;
   int parity;
@@ -70,6 +71,7 @@ struct EnergyParams {
   double* partials;         // [2][n_blocks][Wp]: even-site and odd-site terms per block
   double* partials2;        // [n_samples][splits][Wp]: second reduction level
   double* E;                // [n_samples][Wp]
+  const unsigned char* active;   // [n_samples]: frozen samples keep their energies
   int G, Wp, GPT, n_samples, n_blocks, splits;
 };
 
@@ -82,11 +84,12 @@ struct PTParams {
   unsigned long long* moved;      // [n_samples][R_O][R_T]: passes after which the slot's configuration moved
   unsigned char* tstate;          // [n_samples][R_O][R_T] by memory slot: 0 none, 1 last end T_1, 2 then T_R
   unsigned int* tunnel;           // [n_samples][R_O][R_T] by memory slot: closed loops T_1 -> T_R -> T_1
-  unsigned long long* counters;
+  unsigned long long* counters;   // [n_samples][2]: sweeps done, PT passes done
+  const unsigned char* active;    // [n_samples]: frozen samples are skipped
   int n_samples, R_O, R_T, Wp;
   uint32_t seed_lo, seed_hi;
-  int sweeps_per_call;      // added to counters[0] after the pass
-  int bump_pt;              // 1: this is a PT pass (counters[1] += 1)
+  int sweeps_per_call;      // added to each active sample's sweep counter after the pass
+  int bump_pt;              // 1: this is a PT pass (each active sample's PT counter += 1)
 };
 
 
@@ -135,7 +138,9 @@ cudaError_t launch_half_sweep(int fmt, bool hb, bool j16, bool fast, bool energy
 cudaError_t launch_energy(int fmt, bool j16, const EnergyParams& p, cudaStream_t st);
 cudaError_t launch_energy_final(const EnergyParams& p, cudaStream_t st);
 cudaError_t launch_pt(const PTParams& p, cudaStream_t st);
-cudaError_t launch_bump(unsigned long long* counters, int sweeps, int pts, cudaStream_t st);
+// counters of the active samples += (sweeps, pts)
+cudaError_t launch_bump(unsigned long long* counters, const unsigned char* active, int n_samples,
+                        int sweeps, int pts, cudaStream_t st);
 cudaError_t launch_overlaps(int fmt, const OverlapParams& p, bool chiral, cudaStream_t st);
 // q^{mu nu}(k) of replicas 0 and 1: p.D = q, p.C = qk, partials [ns][R_T][3][n_blocks][21]
 cudaError_t launch_qtensor(int fmt, const OverlapParams& p, cudaStream_t st);

@@ -17,6 +17,7 @@ __device__ __forceinline__ void sweep_block(const SweepParams& p, int bidx, floa
   constexpr int VEC = FmtInfo<F>::VEC, PL = FmtInfo<F>::PLANES;
   using Chunk = typename FmtInfo<F>::Chunk;
   const int4 blk = p.blocks[bidx];
+  if (!p.active[blk.x]) return;   // a frozen sample (the whole block belongs to it)
   const SampleDev& sd = p.samples[blk.x];
   const uint32_t h = (uint32_t)blk.z + threadIdx.x;
   const uint32_t half_n = (uint32_t)sd.N >> 1;
@@ -43,7 +44,8 @@ __device__ __forceinline__ void sweep_block(const SweepParams& p, int bidx, floa
     own_off = chunk_offset<F>(sd, g0, gm.own);
   }
   const uint32_t sweep =
-      HB ? (uint32_t)((CG ? __ldcg(p.counters) : p.counters[0]) + (unsigned long long)p.sweep_offset)
+      HB ? (uint32_t)((CG ? __ldcg(p.counters + 2 * blk.x) : p.counters[2 * blk.x]) +
+                      (unsigned long long)p.sweep_offset)
          : 0u;
 
   for (int g = g0; g < g1; ++g) {
@@ -189,6 +191,7 @@ __device__ __forceinline__ void sweep_block(const SweepParams& p, int bidx, floa
 template <bool CG>
 __device__ __forceinline__ void energy_final1_unit(const EnergyParams& p, int s, int wg, int split,
                                                    double (*red)[32]) {
+  if (!p.active[s]) return;   // frozen sample: its energies stand (block-uniform)
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int w = wg * 32 + tx;
   const SampleDev& sd = p.samples[s];
@@ -219,6 +222,7 @@ __device__ __forceinline__ void energy_final1_unit(const EnergyParams& p, int s,
 // in order, then the lanes are added by a fixed shuffle tree.
 template <bool CG>
 __device__ __forceinline__ void energy_final2_warp(const EnergyParams& p, int s, int w, int lane) {
+  if (!p.active[s]) return;
   double e = 0.0;
   for (int k = lane; k < p.splits; k += 32) {
     const double* a = p.partials2 + ((long long)s * p.splits + k) * p.Wp + w;
@@ -252,8 +256,11 @@ __device__ __forceinline__ bool pt_accept(double x, float u) {
 // configuration that held it has moved (p_diff = moved / passes), and per
 // configuration the closed loops T_1 -> T_R -> T_1 (tunnelling events).
 template <bool CG>
-__device__ __forceinline__ void pt_chain(const PTParams& p, int c, uint32_t step) {
+__device__ __forceinline__ void pt_chain(const PTParams& p, int c) {
   const int s = c / p.R_O, r = c - s * p.R_O;
+  if (!p.active[s]) return;
+  // the sample's own PT pass counter keys its random numbers
+  const uint32_t step = (uint32_t)(CG ? __ldcg(p.counters + 2 * s + 1) : p.counters[2 * s + 1]);
   int* perm = p.perm + (long long)c * p.R_T;
   const double* E = p.E + (long long)s * p.Wp + r * p.R_T;
   const double* ib = p.inv_temps + (long long)s * p.R_T;

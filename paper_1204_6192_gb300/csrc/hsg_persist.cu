@@ -92,12 +92,12 @@ __global__ void __launch_bounds__(SWEEP_BS) k_persistent(const PersistParams P) 
     for (int gw = tid >> 5; gw < ep.n_samples * ep.Wp; gw += nth >> 5)
       energy_final2_warp<true>(ep, gw / ep.Wp, gw % ep.Wp, threadIdx.x & 31);
     if (!sync()) return;
-    const uint32_t pstep = (uint32_t)__ldcg(P.pt.counters + 1);
-    for (int c = tid; c < P.pt.n_samples * P.pt.R_O; c += nth) pt_chain<true>(P.pt, c, pstep);
+    for (int c = tid; c < P.pt.n_samples * P.pt.R_O; c += nth) pt_chain<true>(P.pt, c);
     if (!sync()) return;
-    if (tid == 0) {
-      P.pt.counters[0] += (unsigned long long)nsw;
-      P.pt.counters[1] += 1ull;
+    for (int s = tid; s < P.pt.n_samples; s += nth) {
+      if (!P.pt.active[s]) continue;
+      P.pt.counters[2 * s] += (unsigned long long)nsw;
+      P.pt.counters[2 * s + 1] += 1ull;
     }
     if (!sync()) return;
   }

@@ -93,6 +93,8 @@ def lib() -> ctypes.CDLL:
         "hsg_get_info": (ip, [vp, ctypes.POINTER(Info)]),
         "hsg_get_pt_diagnostics": (ip, [vp, ctypes.POINTER(ctypes.c_uint64),
                                         ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint64)]),
+        "hsg_set_active": (ip, [vp, ctypes.POINTER(ctypes.c_uint8)]),
+        "hsg_get_counters": (ip, [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
         "hsg_checkpoint_size": (ip, [vp, ctypes.POINTER(ctypes.c_size_t)]),
         "hsg_checkpoint_save": (ip, [vp, vp, ctypes.c_size_t]),
         "hsg_checkpoint_load": (ip, [vp, vp, ctypes.c_size_t]),
@@ -297,6 +299,22 @@ class Context:
         self._check(lib().hsg_get_pt_stats(self._ctx, _ptr(acc, ctypes.c_uint64), ctypes.byref(n)))
         return acc, int(n.value)
 
+    def set_active(self, active=None):
+        """Freeze (0) or run (nonzero) each sample in later steps and sweeps; None: all run."""
+        if active is None:
+            self._check(lib().hsg_set_active(self._ctx, ctypes.POINTER(ctypes.c_uint8)()))
+            return
+        a = np.ascontiguousarray(np.asarray(active).astype(np.uint8))
+        assert a.size == self.n_samples
+        self._check(lib().hsg_set_active(self._ctx, _ptr(a, ctypes.c_uint8)))
+
+    def counters(self):
+        """(sweeps [n_samples], pt_passes [n_samples]) each sample has done."""
+        sw = np.zeros(self.n_samples, dtype=np.uint64)
+        pt = np.zeros(self.n_samples, dtype=np.uint64)
+        self._check(lib().hsg_get_counters(self._ctx, _ptr(sw, ctypes.c_uint64), _ptr(pt, ctypes.c_uint64)))
+        return sw, pt
+
     def pt_diagnostics(self):
         """(moved [ns, R_O, R_T] uint64, tunnel [ns, R_O, R_T] uint32 by memory slot, passes)."""
         shape = (self.n_samples, self.n_replicas, self.n_temps)
@@ -376,6 +394,8 @@ hsg_get_perm = Context.get_perm
 hsg_get_pt_stats = Context.pt_stats
 hsg_get_info = Context.info
 hsg_get_pt_diagnostics = Context.pt_diagnostics
+hsg_set_active = Context.set_active
+hsg_get_counters = Context.counters
 hsg_checkpoint_save = Context.checkpoint
 hsg_checkpoint_load = Context.restore
 hsg_sync = Context.sync

@@ -513,3 +513,64 @@ def test_autotuned_schedule_matches_fixed_schedule():
         np.testing.assert_array_equal(x, y)
     np.testing.assert_array_equal(runs[0][1], runs[1][1])
     np.testing.assert_array_equal(runs[0][2], runs[1][2])
+
+
+@pytest.mark.parametrize("variant", [hsg.VARIANT_TWO_PASS, hsg.VARIANT_PERSISTENT])
+def test_per_sample_run_lengths(variant):
+    """Samples frozen in turn: after sample 0 runs 1 + 2 steps and sample 1 runs
+    3 steps (interleaved), the batch is bit-identical to one where both ran 3
+    steps together (each sample's counters key its random numbers)."""
+    samples = [inputs.small_sample(L, n_temps=6, h_r=0.1, disorder_seed=L) for L in (6, 8)]
+
+    def state(c):
+        sw, pt = c.counters()
+        return ([x.copy() for x in c.get_spins()], c.last_energies(), c.get_perm(), c.pt_stats()[0],
+                c.pt_diagnostics()[:2], list(sw), list(pt))
+
+    a = hsg.Context(samples, 2, 5, variant=variant)
+    a.step(3)
+    ref = state(a)
+    a.close()
+    b = hsg.Context(samples, 2, 5, variant=variant)
+    b.set_active([1, 0])
+    b.step(1)
+    b.set_active([0, 1])
+    b.step(3)
+    b.set_active([1, 0])
+    b.step(2)
+    got = state(b)
+    b.close()
+    for x, y in zip(ref[0], got[0]):
+        np.testing.assert_array_equal(x, y)
+    for k in (1, 2, 3):
+        np.testing.assert_array_equal(ref[k], got[k])
+    for x, y in zip(ref[4], got[4]):
+        np.testing.assert_array_equal(x, y)
+    assert ref[5] == got[5] == [18, 18] and ref[6] == got[6] == [3, 3]
+
+
+def test_frozen_samples_follow_the_oracle():
+    """Masks applied to sweeps, PT passes and steps on the device and in the
+    oracle: permutations equal at every step, frozen samples untouched."""
+    samples = [f32(inputs.small_sample(L, n_temps=5, disorder_seed=L + 1)) for L in (4, 6, 4)]
+    ctx = hsg.Context(samples, 2, 3)
+    orc = oracle.OracleSim(samples, 2, 3)
+    for mask in ([1, 0, 1], [0, 1, 1], [1, 1, 0], [0, 0, 1]):
+        before = [x.copy() for x in ctx.get_spins()]
+        ctx.set_active(mask)
+        orc.set_active(mask)
+        ctx.step(1)
+        orc.step(1)
+        perm = ctx.get_perm()
+        spins = ctx.get_spins()
+        for s, o in enumerate(orc.samples):
+            np.testing.assert_array_equal(perm[s], o.perm)
+            if not mask[s]:
+                np.testing.assert_array_equal(spins[s], before[s])
+    sw, pt = ctx.counters()
+    assert list(pt) == [o.pt_step for o in orc.samples] == [2, 2, 3]
+    assert list(sw) == [o.sweep for o in orc.samples]
+    ctx.set_active(None)
+    ctx.sweep_or(1)
+    assert list(ctx.counters()[0]) == [x + 1 for x in sw]
+    ctx.close()
