@@ -131,7 +131,7 @@ def algorithmic_half_sweep_bytes(ctx, wl):
     spin its own read + write and one read of the opposite-parity spin it sees
     (3 S per update), plus the 6 bonds and 3 field components of every updated
     site (shared by the W systems of the sample)."""
-    S = {"fp32": 12, "fp16": 6, "bf16": 6, "angle16": 4, "oct16": 4}[wl.precision]
+    S = {"fp32": 12, "fp16": 6, "bf16": 6, "angle16": 4, "oct16": 4, "yx4": 8}[wl.precision]
     jb = 2 if wl.j_fp16 else 4
     sites = sum(s.L ** 3 for s in wl.samples) // 2
     return sites * (3 * S * ctx.W + 9 * jb)
@@ -419,8 +419,10 @@ def main():
     ctx.close()
 
     if not args.no_extras and world == 1:
-        extras = {}
-        for name, flush in (("L128_fp32", False), ("L32_fp32", True)):
+        extras = {"plain_fp32": {}, "other_storage": {}}
+        for name, flush, group in (("L128_fp32", False, "plain_fp32"), ("L32_fp32", True, "plain_fp32"),
+                                   ("L128_yx4", False, "other_storage"),
+                                   ("L128_oct16", False, "other_storage")):
             w2 = inputs.workload(name)
             r2, sp2, sw2 = run_ours(args, w2, torch, dev, rank, world, args.measure_every)
             buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev) if flush else None
@@ -428,13 +430,13 @@ def main():
             ms2, _ = timed_steps(r2["ctx"], r2["stream"], torch, k2, args.measure_every, flush=buf)
             mh2, _ = roofline(r2["ctx"], r2["stream"], torch, w2)
             A2 = algorithmic_half_sweep_bytes(r2["ctx"], w2)
-            extras[name] = {"value": round(ms2 * 1e6 / (sw2 * sp2 * k2), 6), "unit": UNIT,
+            extras[group][name] = {"value": round(ms2 * 1e6 / (sw2 * sp2 * k2), 6), "unit": UNIT,
                             "steps": k2, "l2": "flushed between steps" if flush else "state > L2",
                             "or_half_sweep_GBps": round(A2 / (mh2 * 1e-3) / 1e9, 1),
                             "or_half_sweep_frac": round(A2 / (mh2 * 1e-3) / 1e9 / peak, 4)}
             r2["ctx"].close()
             del buf
-        line["plain_fp32"] = extras
+        line.update(extras)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(wl)

@@ -76,7 +76,9 @@ typedef enum {
   HSG_FP16 = 1,       /* 3 x binary16, round to nearest even (6 bytes) */
   HSG_BF16 = 2,       /* 3 x bfloat16, round to nearest even (6 bytes) */
   HSG_ANGLE16 = 3,    /* polar angle and azimuth, 16 bits each (4 bytes) */
-  HSG_OCT16 = 4       /* octahedral map (Cigolle et al. 2014), 16 bits each (4 bytes) */
+  HSG_OCT16 = 4,      /* octahedral map (Cigolle et al. 2014), 16 bits each (4 bytes) */
+  HSG_YX4 = 5         /* the paper's packing (Sec. 3.3): binary32 s_y and binary32
+                         s_x + 4 sign(s_z) (8 bytes); s_z = sign sqrt(1 - s_x^2 - s_y^2) */
 } hsg_precision;
 
 typedef struct {

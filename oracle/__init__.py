@@ -25,7 +25,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hsg_oracle.c")
 _LIB = os.path.join(_HERE, "libhsg_oracle.so")
 
-CODECS = {"none": 0, "fp16": 1, "bf16": 2, "angle16": 3, "oct16": 4, "fp32": 5}
+CODECS = {"none": 0, "fp16": 1, "bf16": 2, "angle16": 3, "oct16": 4, "fp32": 5, "yx4": 6}
 
 _lib = None
 

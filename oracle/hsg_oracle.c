@@ -159,6 +159,19 @@ void orc_codec_roundtrip(double v[3], int codec) {
       v[0] = vx / n; v[1] = vy / n; v[2] = vz / n;
       return;
     }
+    case ORC_CODEC_YX4: {
+      /* the paper's packing (Sec. 3.3): binary32 s_y and binary32 s_x + 4 sign(s_z)
+         (sign(0) = +1); decoded with s_z = sign sqrt(1 - s_x^2 - s_y^2) */
+      double y = (double)(float)v[1];
+      double p = (double)(float)(v[0] + (v[2] >= 0.0 ? 4.0 : -4.0));
+      double sg = p > 2.0 ? 1.0 : -1.0;
+      double x = p - 4.0 * sg;
+      double r = 1.0 - x * x - y * y;
+      v[0] = x;
+      v[1] = y;
+      v[2] = sg * sqrt(r > 0.0 ? r : 0.0);
+      return;
+    }
     default:
       return;
   }

@@ -37,7 +37,7 @@ extern "C" {
 enum { ORC_TAG_INIT = 0, ORC_TAG_HB = 1, ORC_TAG_PT = 2 };
 enum { ORC_CODEC_NONE = 0, ORC_CODEC_FP16 = 1, ORC_CODEC_BF16 = 2,
        ORC_CODEC_ANGLE16 = 3, ORC_CODEC_OCT16 = 4,
-       ORC_CODEC_FP32 = 5 };
+       ORC_CODEC_FP32 = 5, ORC_CODEC_YX4 = 6 };
 
 void   orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 void   orc_philox_many(const uint32_t* ctr, long n, uint64_t seed, uint32_t* out);

@@ -164,7 +164,7 @@ hsg_status dev_alloc(hsg_ctx* c, T** p, size_t bytes) {
   } while (0)
 
 int fmt_vec(int) { return 4; }
-int fmt_planes(int f) { return (f == FMT_ANG16 || f == FMT_OCT16) ? 1 : 3; }
+int fmt_planes(int f) { return (f == FMT_ANG16 || f == FMT_OCT16) ? 1 : (f == FMT_YX4 ? 2 : 3); }
 int fmt_elem(int f) { return (f == FMT_F16 || f == FMT_BF16) ? 2 : 4; }
 
 SweepParams sweep_params(hsg_ctx* c, int parity, int sweep_offset) {
@@ -590,7 +590,7 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   if (!L || !temps || !J) return bad_arg(nullptr, "L, temps and J must not be NULL");
   if (n_temps < 1 || n_temps > 256) return bad_arg(nullptr, "n_temps must be in [1, 256]");
   if (n_replicas < 1) return bad_arg(nullptr, "n_replicas < 1");
-  if (opt.precision < HSG_FP32 || opt.precision > HSG_OCT16)
+  if (opt.precision < HSG_FP32 || opt.precision > HSG_YX4)
     return bad_arg(nullptr, "unknown precision");
   if (opt.n_hb_per_step < 0 || opt.n_or_per_step < 0)
     return bad_arg(nullptr, "negative sweeps per step");

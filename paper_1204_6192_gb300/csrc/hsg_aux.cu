@@ -157,6 +157,7 @@ cudaError_t launch_energy(int fmt, bool j16, const EnergyParams& p, cudaStream_t
     case FMT_BF16: return j16 ? energy_fmt<FMT_BF16, true>(p, st) : energy_fmt<FMT_BF16, false>(p, st);
     case FMT_ANG16: return j16 ? energy_fmt<FMT_ANG16, true>(p, st) : energy_fmt<FMT_ANG16, false>(p, st);
     case FMT_OCT16: return j16 ? energy_fmt<FMT_OCT16, true>(p, st) : energy_fmt<FMT_OCT16, false>(p, st);
+    case FMT_YX4: return j16 ? energy_fmt<FMT_YX4, true>(p, st) : energy_fmt<FMT_YX4, false>(p, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -347,6 +348,7 @@ cudaError_t launch_philox(const uint4* ctr, long long n, const SweepParams& p, u
     case FMT_BF16: KERNEL<FMT_BF16><<<nb, 256, 0, st>>>(p); break;                      \
     case FMT_ANG16: KERNEL<FMT_ANG16><<<nb, 256, 0, st>>>(p); break;                    \
     case FMT_OCT16: KERNEL<FMT_OCT16><<<nb, 256, 0, st>>>(p); break;                    \
+    case FMT_YX4: KERNEL<FMT_YX4><<<nb, 256, 0, st>>>(p); break;                        \
     default: return cudaErrorInvalidValue;                                              \
   }                                                                                     \
   return cudaGetLastError();

@@ -88,7 +88,8 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
 // Storage formats.  A chunk holds VEC = 4 systems of one site in one "plane":
 // 16 bytes (uint4) for FP32 components and for the packed 32-bit formats,
 // 8 bytes (uint2) for FP16/BF16 components.  Component formats store three
-// planes (x, y, z), packed formats one.
+// planes (x, y, z), the 16-bit pair formats one, the paper's (s_y, s_x + 4
+// sign s_z) packing two (binary32 each).
 // ----------------------------------------------------------------------------
 template <int F> struct FmtInfo;
 template <> struct FmtInfo<FMT_F32>   { static constexpr int VEC = 4, PLANES = 3, ELEM = 4, CHUNK = 16; using Chunk = uint4; };
@@ -96,6 +97,7 @@ template <> struct FmtInfo<FMT_F16>   { static constexpr int VEC = 4, PLANES = 3
 template <> struct FmtInfo<FMT_BF16>  { static constexpr int VEC = 4, PLANES = 3, ELEM = 2, CHUNK = 8;  using Chunk = uint2; };
 template <> struct FmtInfo<FMT_ANG16> { static constexpr int VEC = 4, PLANES = 1, ELEM = 4, CHUNK = 16; using Chunk = uint4; };
 template <> struct FmtInfo<FMT_OCT16> { static constexpr int VEC = 4, PLANES = 1, ELEM = 4, CHUNK = 16; using Chunk = uint4; };
+template <> struct FmtInfo<FMT_YX4>   { static constexpr int VEC = 4, PLANES = 2, ELEM = 4, CHUNK = 16; using Chunk = uint4; };
 
 // VEC systems of one site as FP32 pairs.
 template <int VEC> struct Spins {
@@ -175,6 +177,35 @@ __device__ __forceinline__ uint32_t oct16_encode(float x, float y, float z) {
   return ((uint32_t)qx & 0xffffu) | (((uint32_t)qy & 0xffffu) << 16);
 }
 
+// --- the paper's packing (Sec. 3.3): s_y and s_x + 4 sign(s_z), binary32 ----
+// p lies in [3, 5] for s_z >= 0 and in [-5, -3] otherwise, so s_x = p - 4 sign
+// is exact (Sterbenz).  s_z^2 = 1 - s_x^2 - s_y^2 is formed to about one ulp of
+// its own size even near the equator: the squares as exact head + tail pairs
+// (FMA), the two subtractions as error-free sums (Knuth), the error terms
+// added last; then one square root.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void yx4_decode(float sy, float p, float& x, float& y, float& z) {
+  const float sg = p > 2.0f ? 1.0f : -1.0f;
+  const float sx = __fsub_rn(p, __fmul_rn(4.0f, sg));
+  const float hx = __fmul_rn(sx, sx), lx = __fmaf_rn(sx, sx, -hx);
+  const float hy = __fmul_rn(sy, sy), ly = __fmaf_rn(sy, sy, -hy);
+  float s1, e1, s2, e2;
+  two_sum(1.0f, -hx, s1, e1);
+  two_sum(s1, -hy, s2, e2);
+  const float r = __fadd_rn(s2, __fsub_rn(__fadd_rn(e1, e2), __fadd_rn(lx, ly)));
+  x = sx;
+  y = sy;
+  z = __fmul_rn(sg, __fsqrt_rn(fmaxf(r, 0.0f)));
+}
+__device__ __forceinline__ void yx4_encode(float x, float y, float z, float& sy, float& p) {
+  sy = y;
+  p = __fadd_rn(x, z >= 0.0f ? 4.0f : -4.0f);
+}
+
 // Decode the PLANES chunks of one site into VEC = 4 FP32 spins.
 template <int F>
 __device__ __forceinline__ void decode(const typename FmtInfo<F>::Chunk* c, Spins<4>& s) {
@@ -190,6 +221,17 @@ __device__ __forceinline__ void decode(const typename FmtInfo<F>::Chunk* c, Spin
     s.x[0] = b2f(c[0].x); s.x[1] = b2f(c[0].y);
     s.y[0] = b2f(c[1].x); s.y[1] = b2f(c[1].y);
     s.z[0] = b2f(c[2].x); s.z[1] = b2f(c[2].y);
+  } else if constexpr (F == FMT_YX4) {
+    const uint32_t a[4] = {c[0].x, c[0].y, c[0].z, c[0].w}, b[4] = {c[1].x, c[1].y, c[1].z, c[1].w};
+    float x[4], y[4], z[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) yx4_decode(__uint_as_float(a[v]), __uint_as_float(b[v]), x[v], y[v], z[v]);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      s.x[k] = make_float2(x[2 * k], x[2 * k + 1]);
+      s.y[k] = make_float2(y[2 * k], y[2 * k + 1]);
+      s.z[k] = make_float2(z[2 * k], z[2 * k + 1]);
+    }
   } else {
     const uint32_t p[4] = {c[0].x, c[0].y, c[0].z, c[0].w};
 #pragma unroll
@@ -226,6 +268,15 @@ __device__ __forceinline__ void encode(const Spins<4>& s, typename FmtInfo<F>::C
     c[0] = make_uint2(f2b(s.x[0]), f2b(s.x[1]));
     c[1] = make_uint2(f2b(s.y[0]), f2b(s.y[1]));
     c[2] = make_uint2(f2b(s.z[0]), f2b(s.z[1]));
+  } else if constexpr (F == FMT_YX4) {
+    float a[4], b[4];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      yx4_encode(s.x[k].x, s.y[k].x, s.z[k].x, a[2 * k], b[2 * k]);
+      yx4_encode(s.x[k].y, s.y[k].y, s.z[k].y, a[2 * k + 1], b[2 * k + 1]);
+    }
+    c[0] = make_uint4(__float_as_uint(a[0]), __float_as_uint(a[1]), __float_as_uint(a[2]), __float_as_uint(a[3]));
+    c[1] = make_uint4(__float_as_uint(b[0]), __float_as_uint(b[1]), __float_as_uint(b[2]), __float_as_uint(b[3]));
   } else {
     uint32_t w[4];
 #pragma unroll
@@ -283,6 +334,9 @@ __device__ __forceinline__ void decode_one(const unsigned char* plane0, long lon
     x = __uint_as_float((uint32_t)reinterpret_cast<const uint16_t*>(plane0)[w] << 16);
     y = __uint_as_float((uint32_t)reinterpret_cast<const uint16_t*>(plane0 + plane_stride)[w] << 16);
     z = __uint_as_float((uint32_t)reinterpret_cast<const uint16_t*>(plane0 + 2 * plane_stride)[w] << 16);
+  } else if constexpr (F == FMT_YX4) {
+    yx4_decode(reinterpret_cast<const float*>(plane0)[w], reinterpret_cast<const float*>(plane0 + plane_stride)[w],
+               x, y, z);
   } else if constexpr (F == FMT_ANG16) {
     ang16_decode(reinterpret_cast<const uint32_t*>(plane0)[w], x, y, z);
   } else {

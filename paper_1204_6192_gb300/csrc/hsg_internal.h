@@ -25,7 +25,7 @@
 namespace hsg {
 
 // spin storage formats (values of hsg_precision)
-enum Fmt { FMT_F32 = 0, FMT_F16 = 1, FMT_BF16 = 2, FMT_ANG16 = 3, FMT_OCT16 = 4 };
+enum Fmt { FMT_F32 = 0, FMT_F16 = 1, FMT_BF16 = 2, FMT_ANG16 = 3, FMT_OCT16 = 4, FMT_YX4 = 5 };
 
 constexpr int SWEEP_BS = 256;
 constexpr int MAX_E_SPLITS = 256;   // first-level units per sample of the energy sums     // threads per block, streaming sweep kernels

@@ -252,6 +252,7 @@ static cudaError_t meas_dispatch(int fmt, const OverlapParams& p, int mode, cuda
     case FMT_BF16: return meas_fmt<FMT_BF16>(p, mode, st);
     case FMT_ANG16: return meas_fmt<FMT_ANG16>(p, mode, st);
     case FMT_OCT16: return meas_fmt<FMT_OCT16>(p, mode, st);
+    case FMT_YX4: return meas_fmt<FMT_YX4>(p, mode, st);
   }
   return cudaErrorInvalidValue;
 }

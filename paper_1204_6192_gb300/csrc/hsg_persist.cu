@@ -133,6 +133,8 @@ static cudaError_t persist_grid(int* grid, size_t smem) {
                                : (fast ? CALL(FMT_ANG16, false, true) : CALL(FMT_ANG16, false, false)); \
     case FMT_OCT16: return j16 ? (fast ? CALL(FMT_OCT16, true, true) : CALL(FMT_OCT16, true, false)) \
                                : (fast ? CALL(FMT_OCT16, false, true) : CALL(FMT_OCT16, false, false)); \
+    case FMT_YX4: return j16 ? (fast ? CALL(FMT_YX4, true, true) : CALL(FMT_YX4, true, false))       \
+                             : (fast ? CALL(FMT_YX4, false, true) : CALL(FMT_YX4, false, false));   \
   }                                                                             \
   return cudaErrorInvalidValue;
 

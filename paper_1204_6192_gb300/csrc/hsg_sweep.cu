@@ -53,6 +53,7 @@ cudaError_t launch_half_sweep(int fmt, bool hb, bool j16, bool fast, bool en,
     case FMT_BF16: return launch_fmt<FMT_BF16>(hb, j16, fast, en, p, n_blocks, st);
     case FMT_ANG16: return launch_fmt<FMT_ANG16>(hb, j16, fast, en, p, n_blocks, st);
     case FMT_OCT16: return launch_fmt<FMT_OCT16>(hb, j16, fast, en, p, n_blocks, st);
+    case FMT_YX4: return launch_fmt<FMT_YX4>(hb, j16, fast, en, p, n_blocks, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -18,7 +18,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libhsg.so")
 
-PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2, "angle16": 3, "oct16": 4}
+PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2, "angle16": 3, "oct16": 4, "yx4": 5}
 STATUS = {0: "HSG_OK", 1: "HSG_EINVAL", 2: "HSG_ENOMEM", 3: "HSG_ECUDA", 4: "HSG_ETIMEOUT",
           5: "HSG_ESTATE"}
 VARIANT_AUTO, VARIANT_TWO_PASS, VARIANT_PERSISTENT = 0, 1, 2

@@ -137,7 +137,7 @@ def workload(name: str, steps: Optional[int] = None) -> Workload:
         prec = name.split("_")[1]
         w = Workload(name, [s], n_replicas=2, seed=1, precision=prec, j_fp16=True,
                      steps=5_000)
-    elif name in ("L128_fp16", "L128_fp32", "L128_oct16", "L128_bf16"):
+    elif name in ("L128_fp16", "L128_fp32", "L128_oct16", "L128_bf16", "L128_yx4"):
         t = geometric_temperatures(0.08, 0.3, 24)
         s = make_sample(128, t, 0.1, disorder_seed=5)
         prec = name.split("_")[1]

@@ -48,7 +48,7 @@ def test_overlaps_match_oracle_batch(R_O):
     ctx.close()
 
 
-@pytest.mark.parametrize("precision", ["fp16", "bf16", "angle16", "oct16"])
+@pytest.mark.parametrize("precision", ["fp16", "bf16", "angle16", "oct16", "yx4"])
 def test_overlaps_match_oracle_compressed(precision):
     samples = [inputs.small_sample(8, n_temps=6, h_r=0.1, disorder_seed=2)]
     ctx = hsg.Context(samples, 4, 5, precision=precision, j_fp16=True)

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 TOL_FP32 = 1e-5
 # storage quantum of one component (max over unit vectors): fp16 2^-11, bf16 2^-8,
 # angle16 ~5e-5, oct16 ~6e-5
-QUANT = {"fp16": 2.0 ** -11, "bf16": 2.0 ** -8, "angle16": 1.1e-4, "oct16": 1.3e-4}
+QUANT = {"fp16": 2.0 ** -11, "bf16": 2.0 ** -8, "angle16": 1.1e-4, "oct16": 1.3e-4, "yx4": 2.0 ** -22}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -338,7 +338,7 @@ def test_measure_matches_oracle_on_seeded_state():
     ctx.close()
 
 
-@pytest.mark.parametrize("precision", ["fp16", "bf16", "angle16", "oct16"])
+@pytest.mark.parametrize("precision", ["fp16", "bf16", "angle16", "oct16", "yx4"])
 def test_codec_roundtrip_matches_oracle(precision):
     rng = np.random.default_rng(4)
     smp = inputs.small_sample(6, n_temps=4)
@@ -366,6 +366,72 @@ def test_codec_one_sweep_matches_oracle(precision, op):
     # equal up to one storage quantum; a site whose field is small amplifies it
     assert np.quantile(d, 0.99) < 3 * QUANT[precision], (op, np.quantile(d, 0.99))
     assert np.median(d) < QUANT[precision] and d.max() < 0.05, (op, d.max())
+
+
+def yx4_ulp_spread(o, base, parity_of_site, op, rng):
+    """The format's own sensitivity: the oracle's even half-sweep, then the odd
+    half-sweep once as is and once with every even site's stored s_x + 4 moved by
+    one unit in the last place; returns the odd sites' differences (x, y)."""
+    out = []
+    for perturb in (False, True):
+        o.s = base.copy()
+        o.or_half(0) if op == "sweep_or" else o.hb_half(0, 1)
+        if perturb:
+            ev = parity_of_site == 0
+            for w in range(o.W):
+                sx, sy, sz = o.s[w, ev, 0], o.s[w, ev, 1], o.s[w, ev, 2]
+                sg = np.where(sz >= 0, 1.0, -1.0)
+                p = (sx + 4 * sg).astype(np.float32)
+                up = rng.random(p.size) < 0.5
+                p2 = np.nextafter(p, np.where(up, np.float32(10), np.float32(-10))).astype(np.float64)
+                x2 = p2 - 4 * sg
+                o.s[w, ev, 0] = x2
+                o.s[w, ev, 2] = sg * np.sqrt(np.maximum(0.0, 1 - x2 * x2 - sy * sy))
+        o.or_half(1) if op == "sweep_or" else o.hb_half(1, 1)
+        out.append(o.s.copy())
+    return np.abs(out[0] - out[1])[:, parity_of_site == 1, :2].ravel()
+
+
+@pytest.mark.parametrize("op", ["sweep_or", "sweep_hb"])
+def test_yx4_one_sweep_matches_oracle(op):
+    """One sweep with the paper's packing (binary32 s_y and s_x + 4 sign s_z) from
+    the same seeded state, the oracle applying the same storage in FP64.  The
+    format stores s_x, s_y and the sign of s_z; s_z is derived, and one unit in
+    the last place of the stored s_x + 4 moves s_z by up to 2^-21 |s_x| / |s_z|.
+    Even sites come out of the even half-sweep from identical inputs: s_x and s_y
+    within 1e-5, s_z^2 within 2e-5, the sign of s_z wherever |s_z| > 1e-3.  Odd
+    sites see their even neighbours through that amplification: their
+    differences stay within 4x the spread the oracle itself shows when the even
+    sites' stored words move by one unit in the last place."""
+    smp = inputs.small_sample(8, n_temps=4, h_r=0.2, disorder_seed=3)
+    samples = [f32(smp)]
+    rng = np.random.default_rng(21)
+    states = [seeded_state(rng, 8, 512)]
+    ctx = hsg.Context(samples, 2, 21, precision="yx4")
+    orc = oracle.OracleSim(samples, 2, 21, codec="yx4")
+    ctx.sweep_or(1)
+    orc.sweep_or(1)
+    ctx.set_spins(states)
+    base = oracle.codec_roundtrip(states[0].astype(np.float64).reshape(-1, 3),
+                                  "yx4").reshape(states[0].shape)
+    orc.samples[0].s = base.copy()
+    getattr(ctx, op)(1)
+    getattr(orc, op)(1)
+    g = ctx.get_spins()[0].astype(np.float64)
+    o = orc.spins()[0]
+    ctx.close()
+    i = np.arange(512)
+    par = (i % 8 + (i // 8) % 8 + i // 64) & 1
+    ev, od = par == 0, par == 1
+    assert np.abs(g[:, ev, :2] - o[:, ev, :2]).max() < 1e-5
+    assert np.abs(g[:, ev, 2] ** 2 - o[:, ev, 2] ** 2).max() < 2e-5
+    far = np.abs(o[:, ev, 2]) > 1e-3
+    np.testing.assert_array_equal(np.sign(g[:, ev, 2][far]), np.sign(o[:, ev, 2][far]))
+    d = np.abs(g[:, od, :2] - o[:, od, :2]).ravel()
+    ref = yx4_ulp_spread(orc.samples[0], base, par, op, np.random.default_rng(5))
+    for q in (0.5, 0.9, 0.99, 1.0):
+        assert np.quantile(d, q) <= 4 * np.quantile(ref, q) + 1e-6, (q, np.quantile(d, q),
+                                                                    np.quantile(ref, q))
 
 
 def test_or_conserves_energy_gpu():
@@ -573,4 +639,23 @@ def test_frozen_samples_follow_the_oracle():
     ctx.set_active(None)
     ctx.sweep_or(1)
     assert list(ctx.counters()[0]) == [x + 1 for x in sw]
+    ctx.close()
+
+
+@pytest.mark.parametrize("n_hb,n_or", [(1, 10), (1, 100), (2, 0), (0, 3)])
+def test_step_ratios_of_table1_match_oracle(n_hb, n_or):
+    """Steps with other heat-bath / over-relaxation ratios (Table 1 uses 1 HB +
+    10 OR and 1 HB + 100 OR; with no OR sweep the step takes its energies from
+    the standalone energy kernel): the PT permutations follow the oracle's step
+    exactly and the step's energies equal a fresh FP64 evaluation."""
+    smp = f32(inputs.small_sample(6, n_temps=5, h_r=0.1, disorder_seed=9))
+    ctx = hsg.Context([smp], 2, 13, n_hb=n_hb, n_or=n_or)
+    orc = oracle.OracleSim([smp], 2, 13)
+    for _ in range(2):
+        ctx.step(1)
+        orc.step(1, n_hb=n_hb, n_or=n_or)
+        np.testing.assert_array_equal(ctx.get_perm()[0], orc.samples[0].perm)
+    np.testing.assert_allclose(ctx.last_energies(), ctx.energies(), rtol=1e-9)
+    sw, pt = ctx.counters()
+    assert list(sw) == [2 * (n_hb + n_or)] and list(pt) == [2]
     ctx.close()

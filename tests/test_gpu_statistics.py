@@ -101,7 +101,7 @@ def test_equilibrium_observables_fp32(oracle_fp32_couplings):
     compare(gpu, ref, "fp32", 3.0)
 
 
-@pytest.mark.parametrize("precision", ["fp16", "bf16", "angle16", "oct16"])
+@pytest.mark.parametrize("precision", ["fp16", "bf16", "angle16", "oct16", "yx4"])
 def test_compressed_storage_error_against_fp64(oracle_fp16_couplings, precision):
     """Compressed spins with FP16 couplings against the FP64 oracle (no storage
     rounding): the storage error stays within the statistical error."""

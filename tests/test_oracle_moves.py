@@ -162,3 +162,35 @@ def test_component_codecs_bound(orc):
     for codec, eps in (("fp16", 2.0 ** -11), ("bf16", 2.0 ** -8)):
         r = orc.codec_roundtrip(v, codec)
         assert np.all(np.abs(r - v) <= eps * np.maximum(np.abs(v), 2.0 ** -14) + 1e-300)
+
+
+def test_yx4_codec_exact_on_grid(orc):
+    """The paper's packing (Sec. 3.3), binary32 s_y and s_x + 4 sign(s_z): for s_x,
+    s_y on a 2^-12 grid both stored numbers are exact, so the round trip gives
+    s_x, s_y back unchanged, keeps the sign of s_z and restores a unit vector."""
+    rng = np.random.default_rng(12)
+    x = rng.integers(-2896, 2897, 4000) / 4096.0
+    y = rng.integers(-2896, 2897, 4000) / 4096.0
+    keep = x * x + y * y < 1.0
+    x, y = x[keep], y[keep]
+    z = np.sqrt(1.0 - x * x - y * y) * rng.choice([-1.0, 1.0], x.size)
+    v = np.stack([x, y, z], axis=1)
+    r = orc.codec_roundtrip(v, "yx4")
+    np.testing.assert_array_equal(r[:, :2], v[:, :2])
+    np.testing.assert_array_equal(np.sign(r[:, 2]), np.sign(z))
+    np.testing.assert_allclose(np.linalg.norm(r, axis=1), 1.0, atol=1e-15)
+
+
+def test_yx4_codec_bounds(orc):
+    """Unit spins: s_x is stored as s_x + 4 in binary32 (half an ulp of [2, 8) is
+    at most 2^-22), s_y in binary32 (at most 2^-25 for |s_y| < 1); the sign of s_z
+    survives; decoding then re-encoding is the identity away from s_z = 0."""
+    rng = np.random.default_rng(13)
+    v = unit(rng, 40000)
+    r = orc.codec_roundtrip(v, "yx4")
+    assert np.abs(r[:, 0] - v[:, 0]).max() <= 2.0 ** -22
+    assert np.abs(r[:, 1] - v[:, 1]).max() <= 2.0 ** -25
+    nz = r[:, 2] != 0.0
+    np.testing.assert_array_equal(np.sign(r[nz, 2]), np.sign(v[nz, 2]))
+    assert np.abs(np.linalg.norm(r, axis=1) - 1.0).max() < 1e-6
+    np.testing.assert_array_equal(orc.codec_roundtrip(r[nz], "yx4"), r[nz])
