@@ -168,3 +168,17 @@ def test_init_uniform_on_sphere(orc):
     assert stats.kstest(s[:, 2], "uniform", args=(-1, 2)).pvalue > 1e-4
     phi = np.arctan2(s[:, 1], s[:, 0])
     assert stats.kstest(phi, "uniform", args=(-np.pi, 2 * np.pi)).pvalue > 1e-4
+
+
+def test_paper_field_has_fixed_length_and_uniform_direction():
+    """The paper's random field (Sec. 2): fixed |H| and a uniformly random
+    direction (inputs.make_sample(field="sphere")): |H_i| = H_r at every site,
+    cos(theta) uniform on [-1, 1] (Kolmogorov-Smirnov) and no preferred axis."""
+    from scipy import stats
+    from paper_1204_6192_gb300 import inputs
+    smp = inputs.make_sample(16, np.array([0.5, 1.0]), 0.3, disorder_seed=4, field="sphere")
+    n = np.linalg.norm(smp.H, axis=1)
+    np.testing.assert_allclose(n, 0.3, rtol=1e-12)
+    c = smp.H[:, 2] / n
+    assert stats.kstest(c, stats.uniform(loc=-1, scale=2).cdf).pvalue > 1e-3
+    assert np.abs(smp.H.mean(axis=0)).max() < 5 * 0.3 / np.sqrt(3 * len(n))
