@@ -437,6 +437,20 @@ def main():
             r2["ctx"].close()
             del buf
         line.update(extras)
+        # the paper's own benchmark (Table 1: 256 systems of L = 32 at T = 100, FP32), with its
+        # GTX 480 figures beside ours for context
+        paper = {"table1_hb100or": 0.29, "table1_hb10or": 0.45, "table1_hb": 2.23, "table1_or": 1.30}
+        t1 = {}
+        for name, ref_ns in paper.items():
+            w2 = inputs.workload(name)
+            r2, sp2, sw2 = run_ours(args, w2, torch, dev, rank, world, 0)
+            k2 = 10 if w2.n_or >= 100 else 30
+            ms2, _ = timed_steps(r2["ctx"], r2["stream"], torch, k2, 0)
+            v = ms2 * 1e6 / (sw2 * sp2 * k2)
+            t1[name] = {"step": f"{w2.n_hb} HB + {w2.n_or} OR", "value": round(v, 6), "unit": UNIT,
+                        "paper_gtx480_ns": ref_ns, "ratio_paper_over_ours": round(ref_ns / v, 1)}
+            r2["ctx"].close()
+        line["paper_table1_config"] = t1
 
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(wl)

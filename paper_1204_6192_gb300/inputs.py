@@ -127,6 +127,15 @@ def workload(name: str, steps: Optional[int] = None) -> Workload:
         t = geometric_temperatures(0.15, 0.6, 8)
         s = make_sample(8, t, 0.0, disorder_seed=1)
         w = Workload(name, [s], n_replicas=2, seed=1, steps=200)
+    elif name.startswith("table1_"):
+        # the paper's benchmark of Table 1: R = 256 systems of L = 32 at T = 100
+        # (where the result does not depend on the disorder), FP32 spins; the
+        # suffix names the step: table1_hb100or = 1 HB + 100 OR, table1_hb10or =
+        # 1 HB + 10 OR, table1_hb = 1 HB, table1_or = 1 OR.
+        n_hb, n_or = {"table1_hb100or": (1, 100), "table1_hb10or": (1, 10), "table1_hb": (1, 0),
+                      "table1_or": (0, 1)}[name]
+        s = make_sample(32, np.array([100.0]), 0.0, disorder_seed=6)
+        w = Workload(name, [s], n_replicas=256, seed=1, n_hb=n_hb, n_or=n_or, steps=20)
     elif name == "L32_fp32":
         t = geometric_temperatures(0.1, 0.4, 32)
         s = make_sample(32, t, 0.05, disorder_seed=2)
