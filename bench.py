@@ -58,6 +58,32 @@ def dist_env():
     return world, rank, local
 
 
+def shard_samples(wl, rank):
+    """Rank r > 0 runs its own disorder sample (independent problems, no
+    collective on the data path): fresh couplings from a rank-keyed generator."""
+    if rank:
+        import numpy as np
+        from paper_1204_6192_gb300 import inputs
+        rng = np.random.default_rng(1000 + rank)
+        for s in wl.samples:
+            s.J = inputs.gaussian_couplings(s.L, rng)
+    return wl
+
+
+def max_over_ranks(x, torch, device):
+    """The slowest rank's value (every rank gets it)."""
+    if not torch.distributed.is_available() or not torch.distributed.is_initialized():
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(ms, updates_per_rank, world):
+    """ns per spin update of the whole job: every rank's updates over the slowest rank's time."""
+    return ms * 1e6 / (updates_per_rank * world)
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -341,13 +367,7 @@ def main():
     dev = torch.device("cuda", local)
     cuda_build.build()
 
-    wl = inputs.workload(args.workload)
-    # every rank runs its own disorder sample (independent problems, no collective)
-    if rank:
-        import numpy as np
-        rng = np.random.default_rng(1000 + rank)
-        for s in wl.samples:
-            s.J = inputs.gaussian_couplings(s.L, rng)
+    wl = shard_samples(inputs.workload(args.workload), rank)
     res, spins, sweeps = run_ours(args, wl, torch, dev, rank, world, args.measure_every)
     ctx, stream = res["ctx"], res["stream"]
 
@@ -369,10 +389,7 @@ def main():
     ms_half, ms_hb = roofline(ctx, stream, torch, wl)
     clocks.stop()
     observables_ms = time_observables(ctx)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, torch, dev)
 
     info = ctx.info()
     persistent = info.variant == 2
@@ -381,7 +398,7 @@ def main():
                 "chunks_per_thread": info.chunks_per_thread, "passes": info.n_passes}
     updates_rank = sweeps * spins * args.steps
     updates = updates_rank * world
-    value = ms * 1e6 / updates
+    value = whole_job_value(ms, updates_rank, world)
     peak, peak_kind = measured_peak()
     A = algorithmic_half_sweep_bytes(ctx, wl)
     achieved = A / (ms_half * 1e-3) / 1e9
