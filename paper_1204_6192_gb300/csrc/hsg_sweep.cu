@@ -15,8 +15,18 @@
 
 namespace hsg {
 
+// Both sweep kernels are latency-bound: the more warps resident per SM, the more
+// loads in flight.  Bounded to 64 registers, i.e. 4 blocks (32 warps) per SM,
+// every storage format but YX4 compiles with at most a few bytes of spill and
+// runs 2-15 % faster than at its natural 74-104 registers (2-3 blocks per SM).
+// The YX4 decode needs ~120 registers and spills heavily under any bound.
+template <int F, bool HB, bool J16, bool EN>
+constexpr int sweep_min_blocks() {
+  return F == FMT_YX4 ? 0 : 4;
+}
+
 template <int F, bool HB, bool J16, bool FAST, bool EN>
-__global__ void __launch_bounds__(SWEEP_BS) k_half_sweep(const SweepParams p) {
+__global__ void __launch_bounds__(SWEEP_BS, sweep_min_blocks<F, HB, J16, EN>()) k_half_sweep(const SweepParams p) {
   extern __shared__ float esum[];
   sweep_block<F, HB, J16, FAST, EN, false>(p, p.blk_base + (int)blockIdx.x, esum);
 }
