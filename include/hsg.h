@@ -90,9 +90,11 @@ typedef struct {
   int device;         /* CUDA device ordinal (default 0) */
   void* stream;       /* cudaStream_t to use; NULL: the library creates a non-blocking stream */
   int variant;        /* step schedule: 0 = automatic, else an HSG_VARIANT_* value */
-  int barrier_timeout_ms;   /* bound of every grid-barrier wait of the persistent schedule
-                               (default 2000); a wait that runs out ends the launch and the
-                               next synchronising call returns HSG_ETIMEOUT */
+  int barrier_timeout_ms;   /* bound of every device wait: the grid barriers of the
+                               persistent schedule and the waits of the measurement kernels
+                               for their staged spin copies (default 2000); a wait that runs
+                               out ends the launch and the next synchronising call returns
+                               HSG_ETIMEOUT */
   int inject_barrier_fault; /* testing only: nonzero makes one block skip the first grid
                                barrier of the next persistent launch, so the others time out */
   long long pass_bytes;     /* system blocking of hsg_step: the systems are cut into passes
@@ -179,7 +181,9 @@ hsg_status hsg_last_energies(hsg_ctx* ctx, double* E_sys);
  *   qk   double[n_samples][n_temps][3][3][3][2]   q^{mu nu}(k) for k = (2 pi/L) e_a,
  *                                                 a = x, y, z; [re, im]; sign e^{+i k.R}
  *   perm int32[n_samples][n_replicas][n_temps]
- * q and qk need n_replicas >= 2 (else they are left untouched).  Synchronises. */
+ * q and qk need n_replicas >= 2 (else they are left untouched).  The spins are read
+ * as stored; per-thread partial sums are FP32 (a few hundred terms at most), the
+ * rest FP64.  HSG_ETIMEOUT if a wait for staged spins ran out.  Synchronises. */
 typedef struct {
   double* E;
   double* q;
@@ -205,7 +209,8 @@ hsg_status hsg_measure(hsg_ctx* ctx, hsg_obs* out);
  * 1: chi_1(k) = N^2 |D_12|^2, chi_2(k) = N^2 D_13 conj(D_14),
  * chi_3(k) = N^2 D_13 conj(D_24).  Caller-owned host buffers; either may be NULL
  * (not both).  HSG_EINVAL when n_replicas < 2.  The spins are read as stored;
- * row sums are FP32, the rest FP64.  Synchronises. */
+ * per-thread partial sums are FP32 (a few hundred terms at most), the rest FP64.
+ * HSG_ETIMEOUT if a wait for staged spins ran out.  Synchronises. */
 hsg_status hsg_measure_overlaps(hsg_ctx* ctx, double* D, double* C);
 
 /* Spins as FP32 (x, y, z), layout described above.  *_dev take device

@@ -85,7 +85,7 @@ struct hsg_ctx {
   int variant = HSG_VARIANT_TWO_PASS;   // resolved step schedule
   bool tune_pending = false;            // automatic schedule not yet tuned
   long long max_sweep_blocks = 0;       // sweep table capacity (one chunk per thread)
-  unsigned int* d_bar = nullptr;        // grid barrier: arrivals, generation, error word
+  unsigned int* d_bar = nullptr;        // grid barrier: arrivals, generation, error word; [3] measurement error word
   int persist_grid = 0;
   size_t persist_smem = 0;
   bool inject_fault = false;
@@ -297,12 +297,13 @@ hsg_status enqueue_step(hsg_ctx* c) {
   return HSG_OK;
 }
 
-// A bounded device wait that ran out (persistent schedule) is reported here,
+// A bounded device wait that ran out (persistent schedule, staged measurement)
 // after the stream has been synchronised.
 hsg_status poll_device_error(hsg_ctx* c) {
-  unsigned int err = 0;
-  HSG_CUDA(c, cudaMemcpy(&err, c->d_bar + 2, sizeof(err), cudaMemcpyDeviceToHost));
-  if (err) return fail(c, HSG_ETIMEOUT, "a grid barrier wait of the persistent step kernel timed out");
+  unsigned int err[2] = {0u, 0u};
+  HSG_CUDA(c, cudaMemcpy(err, c->d_bar + 2, sizeof(err), cudaMemcpyDeviceToHost));
+  if (err[0]) return fail(c, HSG_ETIMEOUT, "a grid barrier wait of the persistent step kernel timed out");
+  if (err[1]) return fail(c, HSG_ETIMEOUT, "a wait for a staged spin copy of a measurement kernel timed out");
   return HSG_OK;
 }
 
@@ -958,6 +959,28 @@ hsg_status hsg_last_energies(hsg_ctx* c, double* E_sys) {
   return HSG_OK;
 }
 
+// Parameters common to the measurement launches; g.ok selects the staged
+// kernels (geometry from staged_geometry), otherwise the direct ones.
+static OverlapParams overlap_params(hsg_ctx* c, const StagedGeom& g) {
+  OverlapParams p{};
+  p.spins = c->spins;
+  p.samples = c->d_sd;
+  p.perm = c->d_perm;
+  p.n_samples = c->ns;
+  p.R_O = c->R_O;
+  p.R_T = c->R_T;
+  p.Wp = c->Wp;
+  if (g.ok) {
+    p.sub = g.sub;
+    p.tile_ss = g.tile_ss;
+    p.Gu = g.Gu;
+    p.grow = g.grow;
+  }
+  p.err = c->d_bar + 3;
+  p.timeout_ns = (unsigned long long)std::max(1, c->opt.barrier_timeout_ms) * 1000000ull;
+  return p;
+}
+
 hsg_status hsg_measure(hsg_ctx* c, hsg_obs* o) {
   HSG_CHECK_CTX(c);
   if (!o) return bad_arg(c, "obs is NULL");
@@ -968,25 +991,20 @@ hsg_status hsg_measure(hsg_ctx* c, hsg_obs* o) {
   const bool pairs = c->R_O >= 2 && (o->q || o->qk);
   if (pairs) {
     const long long nmax = (long long)c->Lmax * c->Lmax * c->Lmax;
-    const int n_tiles = (int)((nmax + MEAS_TILE - 1) / MEAS_TILE);
+    const StagedGeom g = staged_geometry(c->fmt, true, c->R_O, c->R_T, nmax, c->total_sites);
+    const int n_tiles = g.ok ? g.n_tiles : (int)((nmax + MEAS_TILE - 1) / MEAS_TILE);
     if (!c->d_mpart) {
-      HSG_TRY(dev_alloc(c, &c->d_mpart, sizeof(double) * c->ns * 3 * (size_t)n_tiles * c->R_T *
-                                            meas_partial_values(true, false)));
+      const size_t vals = g.ok ? (size_t)n_tiles * g.values
+                               : (size_t)3 * n_tiles * meas_partial_values(true, false);
+      HSG_TRY(dev_alloc(c, &c->d_mpart, sizeof(double) * c->ns * (size_t)c->R_T * vals));
       HSG_TRY(dev_alloc(c, &c->d_q, sizeof(double) * c->ns * (size_t)c->R_T * 9));
       HSG_TRY(dev_alloc(c, &c->d_qk, sizeof(double) * c->ns * (size_t)c->R_T * 54));
     }
-    OverlapParams p;
-    p.spins = c->spins;
-    p.samples = c->d_sd;
-    p.perm = c->d_perm;
+    OverlapParams p = overlap_params(c, g);
     p.partials = c->d_mpart;
     p.D = c->d_q;
     p.C = c->d_qk;
-    p.n_samples = c->ns;
-    p.R_O = c->R_O;
-    p.R_T = c->R_T;
-    p.Wp = c->Wp;
-    p.n_pairs = 3;          // units: the rows mu of the tensor
+    p.n_pairs = 3;          // direct kernel: units are the rows mu of the tensor
     p.n_tiles = n_tiles;
     HSG_CUDA(c, launch_qtensor(c->fmt, p, c->stream));
   }
@@ -1049,25 +1067,22 @@ hsg_status hsg_measure_overlaps(hsg_ctx* c, double* D, double* C) {
   const int n_pairs = overlap_pairs(c->R_O);
   const long long nmax = (long long)c->Lmax * c->Lmax * c->Lmax;
   const int n_tiles = (int)((nmax + MEAS_TILE - 1) / MEAS_TILE);
+  // the chiral overlaps read neighbours: direct kernel; D alone: staged kernel
+  const StagedGeom g = staged_geometry(c->fmt, false, c->R_O, c->R_T, nmax, c->total_sites);
   if (!c->d_opart) {
-    HSG_TRY(dev_alloc(c, &c->d_opart, sizeof(double) * c->ns * (size_t)n_pairs * n_tiles * c->R_T *
-                                          meas_partial_values(false, true)));
+    const size_t direct = (size_t)n_pairs * n_tiles * meas_partial_values(false, true);
+    const size_t staged = g.ok ? (size_t)g.n_tiles * g.values : 0;
+    HSG_TRY(dev_alloc(c, &c->d_opart, sizeof(double) * c->ns * (size_t)c->R_T * std::max(direct, staged)));
     HSG_TRY(dev_alloc(c, &c->d_D, sizeof(double) * c->ns * (size_t)c->R_T * n_pairs * 8));
     HSG_TRY(dev_alloc(c, &c->d_C, sizeof(double) * c->ns * (size_t)c->R_T * n_pairs * 24));
   }
-  OverlapParams p;
-  p.spins = c->spins;
-  p.samples = c->d_sd;
-  p.perm = c->d_perm;
+  const bool staged = g.ok && !C;
+  OverlapParams p = overlap_params(c, staged ? g : StagedGeom{});
   p.partials = c->d_opart;
   p.D = c->d_D;
   p.C = C ? c->d_C : nullptr;
-  p.n_samples = c->ns;
-  p.R_O = c->R_O;
-  p.R_T = c->R_T;
-  p.Wp = c->Wp;
   p.n_pairs = n_pairs;
-  p.n_tiles = n_tiles;
+  p.n_tiles = staged ? g.n_tiles : n_tiles;
   HSG_CUDA(c, launch_overlaps(c->fmt, p, C != nullptr, c->stream));
   if (D)
     HSG_CUDA(c, cudaMemcpyAsync(D, c->d_D, sizeof(double) * c->ns * c->R_T * n_pairs * 8,

@@ -103,11 +103,27 @@ struct OverlapParams {
   double* D;                // q [ns][R_T][3][3], or D [ns][R_T][n_pairs][4][2]; may be null
   double* C;                // qk [ns][R_T][3][3][3][2], or C [ns][R_T][n_pairs][3][4][2]; may be null
   int n_samples, R_O, R_T, Wp, n_pairs, n_tiles;
+  // staged kernels only (sub > 0): storage sites per stage and per block, chunk
+  // groups staged, padded bytes per staged (plane, group) row; bounded waits
+  int sub, tile_ss, Gu, grow;
+  unsigned int* err;        // set when a wait for a staged copy ran out
+  unsigned long long timeout_ns;
 };
 constexpr int MEAS_BS = 256;       // threads per block of the measurement kernels
-constexpr int MEAS_TILE = 1024;    // sites per block of the measurement kernels
-// FP64 partial values per (unit, tile, slot): 21 per tensor row, 28 (7 without chirality) per pair
+constexpr int MEAS_TILE = 1024;    // sites per block of the direct (unstaged) kernels
+// FP64 partial values per (unit, tile, slot) of the direct kernels: 21 per
+// tensor row, 28 (7 without chirality) per pair
 int meas_partial_values(bool qtensor, bool chiral);
+
+// Geometry of the staged kernels (tensor q(k) and scalar pair overlaps): the
+// spins of a block's run of storage sites reach shared memory by bulk copies
+// in stages of `sub` sites.  ok = 0 when even 8 sites of the staged systems do
+// not fit; the direct kernels serve that case.
+struct StagedGeom {
+  int ok, sub, tile_ss, Gu, grow, n_tiles, rounds, smem, values;
+};
+StagedGeom staged_geometry(int fmt, bool qtensor, int R_O, int R_T, long long n_max,
+                           long long n_total);
 
 struct ConvParams {
   unsigned char* spins;

@@ -18,8 +18,25 @@
 // its sites of the tile per slot in FP32 (loading several sites' spins before
 // using any, for memory-level parallelism), the warp adds its lanes in FP32 and writes
 // one FP64 partial per (tile, slot); the final kernel adds the tiles in FP64 in
-// tile order.  (GB300's FP64 rate is a small fraction of its FP32 rate, so FP64
-// work is kept per tile, not per site.)
+// a fixed order.  (GB300's FP64 rate is a small fraction of its FP32 rate, so FP64
+// work is kept per tile, not per site.)  These direct kernels serve the chiral
+// overlaps, whose neighbours lie outside any run of storage sites, and
+// contexts whose staged systems do not fit shared memory.
+//
+// The staged kernels (tensor q(k) and scalar D_ab(k)) read each spin once: a
+// block owns a run of consecutive storage sites of one sample (both parity
+// halves are such runs, and a site's coordinates follow from its index).  Its
+// thread 0 brings the spins of the measured replicas into shared memory with
+// bulk asynchronous copies (one contiguous copy per plane and chunk group),
+// `sub` sites per stage and three stages in flight, each completing on its
+// own mbarrier.  The lanes of a warp are slots: lane t decodes, from shared
+// memory, the spins its replicas hold at slot t (memory slots through perm),
+// so one warp step covers one storage site for up to 32 slots (32 / TL sites
+// for TL < 32 slots).  A lane keeps its slot's sums in FP32 over the block's
+// run; the block adds its warps in FP32 in warp order and writes one FP64
+// partial per (block, slot, value), which the final kernel adds in FP64 in a
+// fixed order.  Every wait on a stage is bounded by the context's barrier timeout;
+// one that runs out sets the error word, which the host reports.
 #include "hsg_kernels.cuh"
 
 namespace hsg {
@@ -179,30 +196,27 @@ __global__ void __launch_bounds__(MEAS_BS) k_meas_tiles(const OverlapParams p) {
   }
 }
 
-// One block per (sample, unit, slot): value v of the slot is the sum of the
-// tiles' partials in tile order (4 threads per value, each a contiguous range
-// of tiles, then added in range order), times 1/N.
+// One warp per (sample, unit, slot, value): lane l adds the tiles' partials
+// l, l + 32, ... in that order, then the lanes are added in a fixed butterfly;
+// the total times 1/N.  Eight values per block of 256 threads.
 template <int MODE>
 __global__ void __launch_bounds__(256) k_meas_final(const OverlapParams p) {
   constexpr int NP = n_products<MODE>();
   constexpr int NVAL = NP * NM;
   const int t = blockIdx.x % p.R_T, su = blockIdx.x / p.R_T;
   const int unit = su % p.n_pairs, s = su / p.n_pairs;
+  const int v = blockIdx.y * 8 + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (v >= NVAL) return;
   const SampleDev& sd = p.samples[s];
   const int n_tiles = (int)(((long long)sd.N + MEAS_TILE - 1) / MEAS_TILE);
-  __shared__ double part[4][64];
-  const int v = threadIdx.x % 64, q4 = threadIdx.x / 64;
-  double acc = 0.0;
-  if (v < NVAL) {
-    const int per = (n_tiles + 3) / 4;
-    const double* src = p.partials + ((long long)s * p.n_pairs + unit) * p.n_tiles * p.R_T * NVAL +
-                        (long long)t * NVAL + v;
-    for (int k = q4 * per; k < min(n_tiles, (q4 + 1) * per); ++k) acc += src[(long long)k * p.R_T * NVAL];
-  }
-  part[q4][v] = acc;
-  __syncthreads();
-  if (threadIdx.x >= NVAL) return;
-  const double sum = ((part[0][v] + part[1][v]) + part[2][v]) + part[3][v];
+  const long long stride = (long long)p.R_T * NVAL;
+  const double* src = p.partials + ((long long)s * p.n_pairs + unit) * p.n_tiles * stride +
+                      (long long)t * NVAL + v;
+  double sum = 0.0;
+#pragma unroll 4
+  for (int k = lane; k < n_tiles; k += 32) sum += src[k * stride];
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if (lane != 0) return;
   const double val = sum / (double)sd.N;
   const int q = v / NM, m = v % NM;
   if constexpr (MODE == MEAS_QTENSOR) {
@@ -225,18 +239,332 @@ __global__ void __launch_bounds__(256) k_meas_final(const OverlapParams p) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Staged kernels
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int MS_STAGES = 3;   // stages in flight per block
+
+__device__ __forceinline__ uint32_t smem_addr(const void* ptr) {
+  return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// one arrival that also announces the bytes the stage's copies will deliver
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred P;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, P;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0u;
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the phase of a stage's barrier with the given parity, at most limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long limit_ns) {
+  if (mbar_test(bar, parity)) return true;
+  const unsigned long long t0 = now_ns();
+  while (!mbar_test(bar, parity))
+    if (now_ns() - t0 > limit_ns) return false;
+  return true;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)), "l"(f2u(c)));
+  return u2f(r);
+}
+
+// products per site: the nine A^mu B^nu of replicas 0 and 1, or the pair dot
+// products of NR replicas
+template <int MODE, int NR>
+__host__ __device__ constexpr int staged_products() {
+  return MODE == MEAS_QTENSOR ? 9 : NR * (NR - 1) / 2;
+}
+
+}  // namespace
+
+template <int F, int MODE, int NR>
+__global__ void __launch_bounds__(MEAS_BS) k_meas_staged(const OverlapParams p) {
+  using FI = FmtInfo<F>;
+  constexpr int NQ = staged_products<MODE, NR>();
+  constexpr int NV = NQ * NM;
+  constexpr int NW = MEAS_BS / 32;
+  extern __shared__ __align__(128) unsigned char stage[];
+  __shared__ uint64_t full[MS_STAGES];   // a stage's copies have landed
+  __shared__ uint64_t empty[MS_STAGES];  // every warp is done with a stage's buffer
+  __shared__ float2 tw[512];             // (cos, sin)(2 pi x / L)
+  __shared__ float red[NV][32];          // the block's sums per (value, slot of the round)
+  const int s = blockIdx.z, round = blockIdx.y;
+  // the sample's geometry in registers: the loop's barrier operations are
+  // memory clobbers, which would otherwise reload it every site
+  const SampleDev sd = p.samples[s];
+  const uint32_t N = (uint32_t)sd.N, Nh = N >> 1;
+  const uint32_t b0 = blockIdx.x * (uint32_t)p.tile_ss;
+  if (b0 >= N) return;
+  const uint32_t b1 = min(N, b0 + (uint32_t)p.tile_ss);
+  const int sub = p.sub;
+  const int n_sub = (int)((b1 - b0 + (uint32_t)sub - 1) / (uint32_t)sub);
+  const long long PS = (long long)p.Gu * p.grow;           // shared bytes between planes
+  const int stage_bytes = FI::PLANES * (int)PS;
+  const unsigned char* gsp = p.spins + sd.spin_off;
+  const int L = sd.L, R_T = p.R_T;
+
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < MS_STAGES; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], NW);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int x = threadIdx.x; x < L; x += blockDim.x) {
+    float sn, cs;
+    sincospif(2.0f * (float)x / (float)L, &sn, &cs);
+    tw[x] = make_float2(cs, sn);
+  }
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // stage k of the run: sub-run k into buffer k % MS_STAGES, one copy per
+  // (plane, chunk group) row, issued by the lanes of warp 0 after lane 0 has
+  // announced the stage's bytes
+  const int rows = FI::PLANES * p.Gu;
+  auto issue = [&](int k) {
+    const int b = k % MS_STAGES;
+    const uint32_t ss0 = b0 + (uint32_t)k * (uint32_t)sub;
+    const uint32_t bytes = min((uint32_t)sub, b1 - ss0) * (uint32_t)FI::CHUNK;
+    if (lane == 0) mbar_expect_tx(&full[b], bytes * (uint32_t)rows);
+    __syncwarp();
+    unsigned char* dst = stage + b * stage_bytes;
+    for (int row = lane; row < rows; row += 32) {
+      const int pl = row / p.Gu, g = row - pl * p.Gu;
+      bulk_copy_g2s(dst + pl * PS + (long long)g * p.grow,
+                    gsp + pl * sd.plane_stride + ((long long)g * N + ss0) * FI::CHUNK, bytes, &full[b]);
+    }
+  };
+  int issued = min(MS_STAGES, n_sub);   // stages issued so far (warp 0)
+  if (warp == 0)
+    for (int k = 0; k < issued; ++k) issue(k);
+
+  // lanes: TL slots per site group, 32 / TL site groups per warp
+  const int nt = min(32, R_T - 32 * round);
+  int TL = 1;
+  while (TL < nt) TL <<= 1;
+  const int tl = lane & (TL - 1), grp = lane / TL, SPW = 32 / TL;
+  const bool live = tl < nt;
+  const int t = 32 * round + tl;
+  int off[NR], jw[NR];
+  const int* perm = p.perm + (long long)s * p.R_O * R_T;
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    const int w = live ? r * R_T + perm[r * R_T + t] : 0;
+    off[r] = (w >> 2) * p.grow;
+    jw[r] = w & 3;
+  }
+  float a0[NQ];
+  float2 ak[NQ][3];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    a0[q] = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) ak[q][d] = make_float2(0.0f, 0.0f);
+  }
+
+  // No block-wide barrier in the loop: a warp waits for a stage's copies
+  // (full) and, after its sites, arrives on the stage's empty barrier; warp 0
+  // refills a buffer once every warp has arrived.  Decisions on a wait that
+  // ran out are taken per warp, so a warp leaves the loop as a whole.
+  bool ok = true;
+  int k = 0;
+  for (; k < n_sub; ++k) {
+    const int b = k % MS_STAGES;
+    const uint32_t ph = (uint32_t)(k / MS_STAGES) & 1u;
+    if (!__all_sync(0xffffffffu, mbar_wait(&full[b], ph, p.timeout_ns))) {
+      ok = false;
+      break;
+    }
+    const uint32_t ss0 = b0 + (uint32_t)k * (uint32_t)sub;
+    const int n = (int)min((uint32_t)sub, b1 - ss0);
+    const unsigned char* st = stage + b * stage_bytes;
+    for (int j = warp * SPW + grp; j < n; j += NW * SPW) {
+      const uint32_t ss = ss0 + (uint32_t)j;
+      const uint32_t par = ss >= Nh ? 1u : 0u;
+      const uint32_t h = ss - par * Nh;                                  // site >> 1
+      const uint32_t r = (__umulhi(h, sd.fdLh_m) + h) >> sd.fdLh_s;       // h / (L / 2)
+      const uint32_t zz = (__umulhi(r, sd.fdL_m) + r) >> sd.fdL_s;        // r / L
+      const uint32_t y = r - zz * (uint32_t)L;
+      const uint32_t x = 2u * (h - r * (uint32_t)sd.Lh) + ((par + y + zz) & 1u);
+      const float2 tk[3] = {tw[x], tw[y], tw[zz]};
+      if (!live) continue;
+      V3 S[NR];
+#pragma unroll
+      for (int rr = 0; rr < NR; ++rr)
+        decode_one<F>(st + off[rr] + j * FI::CHUNK, PS, jw[rr], S[rr].x, S[rr].y, S[rr].z);
+      float P[NQ];
+      if constexpr (MODE == MEAS_QTENSOR) {
+        const float A[3] = {S[0].x, S[0].y, S[0].z}, B[3] = {S[1].x, S[1].y, S[1].z};
+#pragma unroll
+        for (int mu = 0; mu < 3; ++mu)
+#pragma unroll
+          for (int nu = 0; nu < 3; ++nu) P[3 * mu + nu] = __fmul_rn(A[mu], B[nu]);
+      } else {
+        // pairs in the order (0,1) (0,2) (1,2) (0,3) (1,3) (2,3)
+        int q = 0;
+#pragma unroll
+        for (int bb = 1; bb < NR; ++bb)
+#pragma unroll
+          for (int aa = 0; aa < bb; ++aa) P[q++] = dot3(S[aa], S[bb]);
+      }
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        a0[q] = __fadd_rn(a0[q], P[q]);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) ak[q][d] = fma2(f2(P[q]), tk[d], ak[q][d]);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[b]);
+    if (warp == 0 && k + MS_STAGES < n_sub) {
+      if (!__all_sync(0xffffffffu, mbar_wait(&empty[b], ph, p.timeout_ns))) {
+        ok = false;
+        break;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(k + MS_STAGES);
+      issued = k + MS_STAGES + 1;
+    }
+  }
+  if (!ok) {
+    // a wait ran out: flag it and give the copies this block issued a
+    // bounded time to land; the block's partials are not used
+    if (lane == 0) atomicExch(p.err, 1u);
+    if (warp == 0)
+      for (int q = k; q < issued; ++q)
+        mbar_wait(&full[q % MS_STAGES], (uint32_t)(q / MS_STAGES) & 1u, p.timeout_ns);
+  }
+
+  // site groups of a warp share slots: add them (fixed butterfly order)
+  for (int o = TL; o < 32; o <<= 1) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      a0[q] += __shfl_xor_sync(0xffffffffu, a0[q], o);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        ak[q][d].x += __shfl_xor_sync(0xffffffffu, ak[q][d].x, o);
+        ak[q][d].y += __shfl_xor_sync(0xffffffffu, ak[q][d].y, o);
+      }
+    }
+  }
+  // warps in order, FP32 (GB300's FP64 rate is a small fraction of its FP32
+  // rate); the block's sums leave as FP64
+  for (int w = 0; w < NW; ++w) {
+    if (warp == w && grp == 0 && live) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        float* rv = &red[q * NM][lane];
+        const float v[NM] = {a0[q], ak[q][0].x, ak[q][0].y, ak[q][1].x, ak[q][1].y, ak[q][2].x, ak[q][2].y};
+#pragma unroll
+        for (int m = 0; m < NM; ++m) rv[m * 32] = (w == 0 ? 0.0f : rv[m * 32]) + v[m];
+      }
+    }
+    __syncthreads();
+  }
+  double* out = p.partials + (((long long)s * p.n_tiles + blockIdx.x) * R_T + 32 * round) * NV;
+  for (int i = threadIdx.x; i < nt * NV; i += MEAS_BS) out[i] = (double)red[i % NV][i / NV];
+}
+
+// One warp per (sample, slot, value): lane l adds the partials of blocks
+// l, l + 32, ... in that order, then the lanes are added in a fixed butterfly;
+// the total times 1/N.  Eight values per block of 256 threads.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_meas_final_staged(const OverlapParams p, int NV) {
+  const int t = blockIdx.x % p.R_T, s = blockIdx.x / p.R_T;
+  const int v = blockIdx.y * 8 + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (v >= NV) return;
+  const SampleDev& sd = p.samples[s];
+  const int n_tiles = (int)(((long long)sd.N + p.tile_ss - 1) / p.tile_ss);
+  const long long stride = (long long)p.R_T * NV;
+  const double* src = p.partials + ((long long)s * p.n_tiles * p.R_T + t) * NV + v;
+  double acc = 0.0;
+#pragma unroll 4
+  for (int k = lane; k < n_tiles; k += 32) acc += src[k * stride];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane != 0) return;
+  const double val = acc / (double)sd.N;
+  const int q = v / NM, m = v % NM;
+  if constexpr (MODE == MEAS_QTENSOR) {
+    if (m == 0) {
+      if (p.D) p.D[((long long)s * p.R_T + t) * 9 + q] = val;
+    } else if (p.C) {
+      const int d = (m - 1) / 2, ri = (m - 1) % 2;
+      p.C[(((long long)s * p.R_T + t) * 3 + d) * 18 + q * 2 + ri] = val;
+    }
+  } else if (p.D) {
+    const int mode = m == 0 ? 0 : 1 + (m - 1) / 2, ri = m == 0 ? 0 : (m - 1) % 2;
+    double* dst = p.D + (((long long)s * p.R_T + t) * p.n_pairs + q) * 8;
+    dst[2 * mode + ri] = val;
+    if (m == 0) dst[1] = 0.0;
+  }
+}
+
+template <int F, int MODE, int NR>
+static cudaError_t staged_launch(const OverlapParams& p, cudaStream_t st) {
+  constexpr int NV = staged_products<MODE, NR>() * NM;
+  const int smem = MS_STAGES * FmtInfo<F>::PLANES * p.Gu * p.grow;
+  cudaError_t e = cudaFuncSetAttribute(k_meas_staged<F, MODE, NR>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid(p.n_tiles, (p.R_T + 31) / 32, p.n_samples);
+  k_meas_staged<F, MODE, NR><<<grid, MEAS_BS, smem, st>>>(p);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_meas_final_staged<MODE><<<dim3(p.n_samples * p.R_T, (NV + 7) / 8), 256, 0, st>>>(p, NV);
+  return cudaGetLastError();
+}
+
 template <int F, int MODE>
 static cudaError_t meas_launch(const OverlapParams& p, cudaStream_t st) {
   const dim3 grid(p.n_tiles * p.n_pairs, p.n_samples);
   k_meas_tiles<F, MODE><<<grid, MEAS_BS, 0, st>>>(p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_meas_final<MODE><<<p.n_samples * p.n_pairs * p.R_T, 256, 0, st>>>(p);
+  constexpr int NVAL = n_products<MODE>() * NM;
+  k_meas_final<MODE><<<dim3(p.n_samples * p.n_pairs * p.R_T, (NVAL + 7) / 8), 256, 0, st>>>(p);
   return cudaGetLastError();
 }
 
 template <int F>
 static cudaError_t meas_fmt(const OverlapParams& p, int mode, cudaStream_t st) {
+  if (p.sub > 0 && mode == MEAS_QTENSOR) return staged_launch<F, MEAS_QTENSOR, 2>(p, st);
+  if (p.sub > 0 && mode == MEAS_PAIRS) {
+    switch (min(p.R_O, 4)) {
+      case 2: return staged_launch<F, MEAS_PAIRS, 2>(p, st);
+      case 3: return staged_launch<F, MEAS_PAIRS, 3>(p, st);
+      case 4: return staged_launch<F, MEAS_PAIRS, 4>(p, st);
+    }
+    return cudaErrorInvalidValue;
+  }
   switch (mode) {
     case MEAS_QTENSOR: return meas_launch<F, MEAS_QTENSOR>(p, st);
     case MEAS_PAIRS: return meas_launch<F, MEAS_PAIRS>(p, st);
@@ -259,6 +587,45 @@ static cudaError_t meas_dispatch(int fmt, const OverlapParams& p, int mode, cuda
 
 int meas_partial_values(bool qtensor, bool chiral) {
   return (qtensor ? 3 : (chiral ? 4 : 1)) * NM;
+}
+
+StagedGeom staged_geometry(int fmt, bool qtensor, int R_O, int R_T, long long n_max,
+                           long long n_total) {
+  StagedGeom g{};
+  int planes = 3, chunk = 8;
+  switch (fmt) {
+    case FMT_F32: planes = FmtInfo<FMT_F32>::PLANES; chunk = FmtInfo<FMT_F32>::CHUNK; break;
+    case FMT_F16: planes = FmtInfo<FMT_F16>::PLANES; chunk = FmtInfo<FMT_F16>::CHUNK; break;
+    case FMT_BF16: planes = FmtInfo<FMT_BF16>::PLANES; chunk = FmtInfo<FMT_BF16>::CHUNK; break;
+    case FMT_ANG16: planes = FmtInfo<FMT_ANG16>::PLANES; chunk = FmtInfo<FMT_ANG16>::CHUNK; break;
+    case FMT_OCT16: planes = FmtInfo<FMT_OCT16>::PLANES; chunk = FmtInfo<FMT_OCT16>::CHUNK; break;
+    case FMT_YX4: planes = FmtInfo<FMT_YX4>::PLANES; chunk = FmtInfo<FMT_YX4>::CHUNK; break;
+    default: return g;
+  }
+  const int r_use = qtensor ? 2 : std::min(R_O, 4);
+  if (r_use < 2) return g;
+  g.Gu = (r_use * R_T + 3) / 4;               // chunk groups of memory slots [0, r_use R_T)
+  g.values = (qtensor ? 9 : r_use * (r_use - 1) / 2) * NM;
+  // rows padded by 16 bytes put consecutive chunk groups 4 banks apart
+  constexpr long long budget = 96 * 1024;
+  for (int sub = 64; sub >= 8 && !g.ok; sub >>= 1) {
+    const int grow = sub * chunk + 16;
+    const long long bytes = (long long)MS_STAGES * planes * g.Gu * grow;
+    if (bytes <= budget) {
+      g.ok = 1;
+      g.sub = sub;
+      g.grow = grow;
+      g.smem = (int)bytes;
+    }
+  }
+  if (!g.ok) return g;
+  g.rounds = (R_T + 31) / 32;
+  // about 8 blocks per SM over the whole call; a lane's FP32 sums stay short
+  long long per = (n_total * g.rounds + 1215) / 1216;
+  per = (per + g.sub - 1) / g.sub * g.sub;
+  g.tile_ss = (int)std::min<long long>(8192, std::max<long long>(g.sub, per));
+  g.n_tiles = (int)((n_max + g.tile_ss - 1) / g.tile_ss);
+  return g;
 }
 
 cudaError_t launch_overlaps(int fmt, const OverlapParams& p, bool chiral, cudaStream_t st) {

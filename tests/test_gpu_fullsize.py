@@ -102,9 +102,10 @@ def test_fullsize_step_matches_oracle_on_sampled_systems(full):
 def test_fullsize_overlaps_on_sampled_slots(full):
     """hsg_measure_overlaps at full size: the spin and chiral pair overlaps of
     two temperature slots, recomputed by the oracle from the two configurations
-    alone (FP32 row sums of 128 terms)."""
+    alone (FP32 partial sums of at most a few hundred terms)."""
     w, smp16, ctx = full
     out = ctx.measure_overlaps()
+    out_d = ctx.measure_overlaps(chiral=False)      # D alone: the staged kernel
     spins = ctx.get_spins()[0]
     perm = ctx.get_perm()[0]
     R_T = len(smp16.temps)
@@ -113,3 +114,4 @@ def test_fullsize_overlaps_on_sampled_slots(full):
         D, C = oracle.overlaps(sub, smp16.L, 2, 1, np.zeros((2, 1), dtype=np.int32))
         np.testing.assert_allclose(out["D"][0, t], D[0], rtol=0, atol=2e-6)
         np.testing.assert_allclose(out["C"][0, t], C[0], rtol=0, atol=2e-6)
+        np.testing.assert_allclose(out_d["D"][0, t], D[0], rtol=0, atol=2e-6)
