@@ -69,6 +69,8 @@ def lib():
             "orc_hb_many": (None, [dp, dp, dp, dp, dp, c_long]),
             "orc_or_half": (None, [dp, dp, dp, c_int, c_int, c_int, c_int]),
             "orc_hb_half": (None, [dp, dp, dp, c_int, c_int, c_int, dp, u64, u64, u32, c_int]),
+            "orc_multihit": (None, [dp, dp, dp, c_int, c_int, c_int, c_int, c_int, c_int, c_int,
+                                     dp, u64, u64, u32, c_int]),
             "orc_energy": (None, [dp, dp, dp, c_int, c_int, dp]),
             "orc_pt": (None, [dp, dp, i32p, c_int, c_int, u64, u64, u32, i32p]),
             "orc_measure": (None, [dp, c_int, c_int, i32p, dp, dp]),
@@ -229,6 +231,13 @@ class OracleSample:
         lib().orc_hb_half(_dp(self.s), _dp(self.J), _dp(self.H), self.L, self.W, parity, _dp(beta),
                           self.sys_base, self.seed, sweep, self.codec)
 
+    def multihit(self, tile, n_rounds, n_or, n_hb, sweep0, colors=3):
+        """Tile-local updates of the double checkerboard (Sec. 3.2): see orc_multihit."""
+        beta = self.beta_sys()
+        lib().orc_multihit(_dp(self.s), _dp(self.J), _dp(self.H), self.L, self.W, tile, colors,
+                           n_rounds, n_or, n_hb, _dp(beta), self.sys_base, self.seed, sweep0,
+                           self.codec)
+
     def energies(self) -> np.ndarray:
         E = np.zeros(self.W)
         lib().orc_energy(_dp(self.s), _dp(self.J), _dp(self.H), self.L, self.W, _dp(E))
@@ -316,6 +325,17 @@ class OracleSim:
         for _ in range(n):
             self.sweep_hb(n_hb)
             self.sweep_or(n_or)
+            self.pt_exchange()
+
+    def step_multihit(self, n: int = 1, tile: int = 8, n_rounds: int = 10, n_or: int = 10,
+                      n_hb: int = 1):
+        """n steps of the multi-hit schedule: per step both tile colours with
+        n_rounds x (n_or OR + n_hb HB) tile sweeps each, then the energies and
+        one PT pass; every sample's sweep counter advances by n_rounds (n_or + n_hb)."""
+        for _ in range(n):
+            for o in self._running():
+                o.multihit(tile, n_rounds, n_or, n_hb, o.sweep)
+                o.sweep += n_rounds * (n_or + n_hb)
             self.pt_exchange()
 
     def measure(self):

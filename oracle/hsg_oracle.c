@@ -330,6 +330,59 @@ void orc_hb_half(double* s, const double* J, const double* H, int L, int W, int 
   }
 }
 
+/* Multi-hit tile schedule (Sec. 3.2, the double checkerboard; Table 1's
+   "10 x (1 HB + 10 OR)").  The lattice is cut into cubic tiles of edge T
+   (T even, L / T even), coloured by the parity of their tile coordinates, so
+   that no two tiles of one colour share a bond.  For colour 0, then colour 1
+   (the bits of `colors` select them), every tile of that colour is updated
+   n_rounds times by n_or over-relaxation sweeps and then n_hb heat-bath
+   sweeps of its own sites, while every spin outside it stays as it is; a
+   tile sweep visits the tile's sites of parity 0, then those of parity 1.
+   The k-th tile sweep of the call (k = 0 .. n_rounds (n_or + n_hb) - 1, in
+   that order) draws its heat-bath numbers with sweep counter sweep0 + k.
+   Tiles of one colour do not interact, so their order does not matter. */
+void orc_multihit(double* s, const double* J, const double* H, int L, int W, int T, int colors,
+                  int n_rounds, int n_or, int n_hb, const double* beta, uint64_t sys_base,
+                  uint64_t seed, uint32_t sweep0, int codec) {
+  const long N = (long)L * L * L;
+  const int B = L / T, per_round = n_or + n_hb;
+#pragma omp parallel for schedule(static)
+  for (int w = 0; w < W; ++w) {
+    double* sw = s + 3 * (long)w * N;
+    for (int color = 0; color < 2; ++color) {
+      if (!((colors >> color) & 1)) continue;
+      for (int Z = 0; Z < B; ++Z)
+        for (int Y = 0; Y < B; ++Y)
+          for (int X = 0; X < B; ++X) {
+            if (((X + Y + Z) & 1) != color) continue;
+            for (int r = 0; r < n_rounds; ++r)
+              for (int k = 0; k < per_round; ++k) {
+                const int hb = k >= n_or;
+                const uint32_t sweep = sweep0 + (uint32_t)(r * per_round + k);
+                for (int parity = 0; parity < 2; ++parity)
+                  for (int z = Z * T; z < Z * T + T; ++z)
+                    for (int y = Y * T; y < Y * T + T; ++y)
+                      for (int x = X * T; x < X * T + T; ++x) {
+                        const long i = site_of(L, x, y, z);
+                        if (parity_of(L, i) != parity) continue;
+                        double h[3];
+                        orc_local_field(sw, J, H, L, i, h);
+                        if (hb) {
+                          double u1, u2;
+                          pair_uniforms((uint32_t)i, sys_base + (uint64_t)w, sweep, ORC_TAG_HB,
+                                        seed, &u1, &u2);
+                          orc_hb_move(sw + 3 * i, h, beta[w], u1, u2);
+                        } else {
+                          orc_or_move(sw + 3 * i, h);
+                        }
+                        orc_codec_roundtrip(sw + 3 * i, codec);
+                      }
+              }
+          }
+    }
+  }
+}
+
 /* Eq. (1), each bond once: E = - sum_i sum_a J_i,a s_i.s_{i+e_a} - sum_i H_i.s_i */
 void orc_energy(const double* s, const double* J, const double* H, int L, int W, double* E) {
   long N = (long)L * L * L;

@@ -62,6 +62,14 @@ void   orc_or_half(double* s, const double* J, const double* H, int L, int W, in
 void   orc_hb_half(double* s, const double* J, const double* H, int L, int W, int parity,
                    const double* beta, uint64_t sys_base, uint64_t seed, uint32_t sweep,
                    int codec);
+/* Multi-hit tile schedule (Sec. 3.2, Table 1): tiles of edge T coloured by the
+   parity of their tile coordinates; per colour, every tile gets n_rounds x
+   (n_or OR + n_hb HB) tile sweeps with the rest of the lattice fixed; the
+   k-th tile sweep keys its heat-bath numbers with sweep0 + k.  colors: bit 0
+   colour 0, bit 1 colour 1.  T even, L / T even. */
+void   orc_multihit(double* s, const double* J, const double* H, int L, int W, int T, int colors,
+                    int n_rounds, int n_or, int n_hb, const double* beta, uint64_t sys_base,
+                    uint64_t seed, uint32_t sweep0, int codec);
 void   orc_energy(const double* s, const double* J, const double* H, int L, int W, double* E);
 void   orc_pt(const double* E, const double* temps, int32_t* perm, int R_O, int R_T,
               uint64_t chain_base, uint64_t seed, uint32_t pt_step, int32_t* accepted);
