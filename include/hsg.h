@@ -135,11 +135,28 @@ hsg_status hsg_create(hsg_ctx** out, int L, const double* temps, int n_temps, in
  * its own L[s], temperatures temps[s * n_temps + t], J[s] and H[s] (H[s] or H
  * itself may be NULL).  All samples share n_temps, n_replicas, the seed and
  * the options; they are updated together by every call (Sec. 3.2, the
- * disorder average as trivial parallelism).
+ * disorder average as trivial parallelism).  1 <= n_samples <= 65535, else
+ * HSG_EINVAL.
  */
 hsg_status hsg_create_batch(hsg_ctx** out, int n_samples, const int* L, const double* temps,
                             int n_temps, int n_replicas, const float* const* J,
                             const float* const* H, uint64_t seed, const hsg_options* opt);
+
+/* n_steps steps of the multi-hit tile schedule, the paper's double
+ * checkerboard (Sec. 3.2; Table 1, "10 x (1 HB + 10 OR)").  The lattice is cut
+ * into cubic tiles of edge `tile` (4 or 8), coloured by the parity of their
+ * tile coordinates.  Per step: every tile of colour 0, then every tile of
+ * colour 1, gets n_rounds x (n_or OR sweeps, then n_hb HB sweeps) of its own
+ * sites (even sites, then odd sites) while the rest of the lattice stays
+ * fixed; then the energies (Eq. 1) and one PT pass (Eq. 4).  The k-th tile
+ * sweep of a step keys its heat-bath numbers with the sample's sweep counter
+ * + k; the counter advances by n_rounds (n_or + n_hb) per step.  This is a
+ * different Markov chain from hsg_step's lattice sweeps (the same equilibrium
+ * distribution, other autocorrelations).  HSG_EINVAL unless tile is 4 or 8,
+ * every L is a multiple of 2 * tile, n_rounds >= 1 and n_or + n_hb >= 1.
+ * Asynchronous. */
+hsg_status hsg_step_multihit(hsg_ctx* ctx, int n_steps, int tile, int n_rounds, int n_or,
+                             int n_hb);
 
 /* n_sweeps full OR sweeps (Eq. 3), each an even then an odd half-sweep. */
 hsg_status hsg_sweep_or(hsg_ctx* ctx, int n_sweeps);

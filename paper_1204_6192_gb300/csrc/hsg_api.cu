@@ -92,6 +92,11 @@ struct hsg_ctx {
 
   // system-blocked passes: a step sweeps one range of the block table (a group
   // of systems) through all its sweeps before the next range
+  // multi-hit tile schedule: block tables (sample, tile, chunk group), colour 0
+  // first, built at first use for tile edges 4 and 8
+  int4* d_mh_blocks[2] = {nullptr, nullptr};
+  int mh_count[2][2] = {{0, 0}, {0, 0}};
+
   std::vector<int> pass_bound{0, 0};    // [n_passes + 1] block table bounds
   int* d_pass_bound = nullptr;
   long long pass_bytes = 0;             // resolved footprint bound (0: one pass)
@@ -587,7 +592,8 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   hsg_options opt;
   hsg_default_options(&opt);
   if (optp) opt = *optp;
-  if (n_samples < 1) return bad_arg(nullptr, "n_samples < 1");
+  // samples index a grid dimension of the energy and measurement launches
+  if (n_samples < 1 || n_samples > 65535) return bad_arg(nullptr, "n_samples must be in [1, 65535]");
   if (!L || !temps || !J) return bad_arg(nullptr, "L, temps and J must not be NULL");
   if (n_temps < 1 || n_temps > 256) return bad_arg(nullptr, "n_temps must be in [1, 256]");
   if (n_replicas < 1) return bad_arg(nullptr, "n_replicas < 1");
@@ -921,6 +927,69 @@ hsg_status hsg_pt_exchange_energies(hsg_ctx* c, const double* E_sys) {
   // the host array may be released by the caller on return
   HSG_CUDA(c, cudaStreamSynchronize(c->stream));
   HSG_TRY(poll_device_error(c));
+  return HSG_OK;
+}
+
+// The block table of the multi-hit schedule for tile edge T (index 0: T = 4,
+// 1: T = 8): every (tile, chunk group) of colour 0 of every sample, then those
+// of colour 1.
+static hsg_status multihit_table(hsg_ctx* c, int T) {
+  const int ti = T == 4 ? 0 : 1;
+  if (c->d_mh_blocks[ti]) return HSG_OK;
+  std::vector<int4> blocks;
+  for (int color = 0; color < 2; ++color) {
+    const size_t before = blocks.size();
+    for (int s = 0; s < c->ns; ++s) {
+      const int B = c->L[s] / T;
+      for (int t = 0; t < B * B * B; ++t) {
+        if (((t % B + (t / B) % B + t / (B * B)) & 1) != color) continue;
+        for (int g = 0; g < c->G; ++g) blocks.push_back(make_int4(s, t, g, 0));
+      }
+    }
+    c->mh_count[ti][color] = (int)(blocks.size() - before);
+  }
+  HSG_TRY(dev_alloc(c, &c->d_mh_blocks[ti], sizeof(int4) * blocks.size()));
+  HSG_CUDA(c, cudaMemcpy(c->d_mh_blocks[ti], blocks.data(), sizeof(int4) * blocks.size(),
+                         cudaMemcpyHostToDevice));
+  return HSG_OK;
+}
+
+hsg_status hsg_step_multihit(hsg_ctx* c, int n_steps, int tile, int n_rounds, int n_or, int n_hb) {
+  HSG_CHECK_CTX(c);
+  if (n_steps < 0) return bad_arg(c, "n_steps < 0");
+  if (tile != 4 && tile != 8) return bad_arg(c, "tile must be 4 or 8");
+  if (n_rounds < 1 || n_or < 0 || n_hb < 0 || n_or + n_hb < 1)
+    return bad_arg(c, "need n_rounds >= 1, n_or >= 0, n_hb >= 0 and n_or + n_hb >= 1");
+  for (int s = 0; s < c->ns; ++s)
+    if (c->L[s] % (2 * tile) != 0) return bad_arg(c, "every L must be a multiple of 2 * tile");
+  if (n_steps == 0) return HSG_OK;
+  HSG_CUDA(c, cudaSetDevice(c->device));
+  HSG_TRY(multihit_table(c, tile));
+  const int ti = tile == 4 ? 0 : 1;
+  MultihitParams p;
+  p.spins = c->spins;
+  p.rec = c->rec;
+  p.samples = c->d_sd;
+  p.blocks = c->d_mh_blocks[ti];
+  p.beta = c->d_beta;
+  p.counters = c->d_counters;
+  p.active = c->d_active;
+  p.Wp = c->Wp;
+  p.n_rounds = n_rounds;
+  p.n_or = n_or;
+  p.n_hb = n_hb;
+  const SweepParams sp = sweep_params(c, 0, 0);
+  for (int r = 0; r < 20; ++r) p.rk[r] = sp.rk[r];
+  const bool fast = c->opt.fast_math != 0;
+  for (int k = 0; k < n_steps; ++k) {
+    for (int color = 0; color < 2; ++color) {
+      p.blk_base = color == 0 ? 0 : c->mh_count[ti][0];
+      HSG_CUDA(c, launch_multihit(c->fmt, c->j16, fast, tile, p, c->mh_count[ti][color], c->stream));
+    }
+    HSG_TRY(enqueue_energy(c));
+    HSG_CUDA(c, launch_pt(pt_params(c, n_rounds * (n_or + n_hb), 1), c->stream));
+  }
+  c->e_valid = true;
   return HSG_OK;
 }
 

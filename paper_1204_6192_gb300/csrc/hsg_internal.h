@@ -148,6 +148,23 @@ struct PersistParams {
   int n_passes;
 };
 
+// Multi-hit tile updates (hsg_multihit.cu): one launch per tile colour.
+struct MultihitParams {
+  unsigned char* spins;
+  const void* rec;
+  const SampleDev* samples;
+  const int4* blocks;       // (sample, tile, chunk group, 0); colour 0 tiles first
+  const float* beta;        // [n_samples][Wp]
+  const unsigned long long* counters;   // [n_samples][2]: sweeps done, PT passes done
+  const unsigned char* active;          // [n_samples]
+  int Wp;
+  int n_rounds, n_or, n_hb;             // per tile: n_rounds x (n_or OR + n_hb HB) tile sweeps
+  int blk_base;             // block table entry of launch block 0
+  uint32_t rk[20];          // Philox round keys of the seed
+};
+cudaError_t launch_multihit(int fmt, bool j16, bool fast, int tile, const MultihitParams& p,
+                            int n_blocks, cudaStream_t st);
+
 // launchers (hsg_kernels*.cu)
 cudaError_t launch_half_sweep(int fmt, bool hb, bool j16, bool fast, bool energy,
                               const SweepParams& p, int n_blocks, cudaStream_t st);

@@ -80,6 +80,7 @@ def lib() -> ctypes.CDLL:
         "hsg_pt_exchange": (ip, [vp]),
         "hsg_pt_exchange_energies": (ip, [vp, dp]),
         "hsg_step": (ip, [vp, ip]),
+        "hsg_step_multihit": (ip, [vp, ip, ip, ip, ip, ip]),
         "hsg_energies": (ip, [vp, dp]),
         "hsg_last_energies": (ip, [vp, dp]),
         "hsg_measure": (ip, [vp, ctypes.POINTER(Obs)]),
@@ -213,6 +214,11 @@ class Context:
     def pt_exchange_energies(self, E_sys: np.ndarray):
         E = np.ascontiguousarray(E_sys, dtype=np.float64).reshape(self.n_samples, self.W)
         self._check(lib().hsg_pt_exchange_energies(self._ctx, _ptr(E, ctypes.c_double)))
+
+    def step_multihit(self, n: int = 1, tile: int = 8, n_rounds: int = 10, n_or: int = 10,
+                      n_hb: int = 1):
+        """n steps of the multi-hit tile schedule (hsg_step_multihit)."""
+        self._check(lib().hsg_step_multihit(self._ctx, n, tile, n_rounds, n_or, n_hb))
 
     def step(self, n: int = 1):
         self._check(lib().hsg_step(self._ctx, n))
@@ -382,6 +388,7 @@ hsg_sweep_hb = Context.sweep_hb
 hsg_pt_exchange = Context.pt_exchange
 hsg_pt_exchange_energies = Context.pt_exchange_energies
 hsg_step = Context.step
+hsg_step_multihit = Context.step_multihit
 hsg_energies = Context.energies
 hsg_last_energies = Context.last_energies
 hsg_measure = Context.measure

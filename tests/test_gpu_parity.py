@@ -474,6 +474,13 @@ def test_invalid_arguments_rejected():
         with pytest.raises(hsg.HsgError) as ei:
             hsg.Context([smp], 2, 1, **kw)
         assert ei.value.status == 1
+    # more samples than a grid dimension holds: rejected before any argument is read
+    import ctypes
+    out = ctypes.c_void_p()
+    for n in (0, 65536):
+        assert hsg.lib().hsg_create_batch(ctypes.byref(out), n, None, None, 4, 2, None, None,
+                                          ctypes.c_uint64(1), None) == 1
+        assert out.value is None
     ctx = hsg.Context([smp], 2, 1)
     with pytest.raises(hsg.HsgError):
         ctx.sweep_or(-1)
