@@ -12,7 +12,8 @@ spins and couplings, H_r = 0.1 (100.7M spins, 604 MB of spin state, larger
 than L2, so no flush is needed between steps).  The line also carries the
 plain-FP32 form of the same lattice and the plain-FP32 L = 32 production
 shape (25 MB, L2 flushed between timed steps) for the compressed-vs-plain
-comparison.
+comparison, the paper's Table 1 configuration, and the multi-hit tile
+schedule (per-update time and the time to an uncorrelated sample).
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 """
@@ -237,6 +238,88 @@ def roofline(ctx, stream, torch, wl, reps=20):
     t1.synchronize()
     ms_hb = t0.elapsed_time(t1) / (2 * (reps // 4 or 1))
     return ms_half, ms_hb
+
+
+def multihit_extras(torch, dev, inputs, lattice_ns):
+    """The multi-hit tile schedule (hsg_step_multihit; Sec. 3.2, Table 1's last
+    rows): ns per spin update on the bench lattice (one round and ten rounds
+    per tile) and on Table 1's configuration; tau_int of the replica overlap
+    per schedule on a small lattice at one temperature (Sokal window); and the
+    time to an uncorrelated sample relative to the lattice schedule, taking
+    each schedule's per-update time on the bench lattice (`lattice_ns`: the
+    bench's own value) and its tau in sweeps."""
+    import numpy as np
+    from paper_1204_6192_gb300 import analysis, hsg
+    out = {}
+    mh1 = dict(tile=8, n_rounds=1, n_or=10, n_hb=1)
+    mh10 = dict(tile=8, n_rounds=10, n_or=10, n_hb=1)
+
+    def timed(stream, fn, k):
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        fn(k)
+        t1.record(stream)
+        t1.synchronize()
+        return t0.elapsed_time(t1) / k
+
+    per_update = {}
+    for name, label, mh, k, paper_ns in (
+            ("L128_fp16", "10 OR + 1 HB per 8^3 tile", mh1, 10, None),
+            ("L128_fp16", "10 x (1 HB + 10 OR) per 8^3 tile", mh10, 3, None),
+            ("table1_hb10or", "10 x (1 HB + 10 OR) per 8^3 tile", mh10, 3, 0.36)):
+        w = inputs.workload(name)
+        stream = torch.cuda.Stream(device=dev)
+        ctx = hsg.Context(w.samples, w.n_replicas, w.seed, precision=w.precision,
+                          j_fp16=w.j_fp16, device=dev.index, stream=stream.cuda_stream)
+        ctx.step_multihit(1, **mh)
+        ms = timed(stream, lambda n: ctx.step_multihit(n, **mh), k)
+        ns = ms * 1e6 / (ctx.info().total_spins * mh["n_rounds"] * (mh["n_or"] + mh["n_hb"]))
+        entry = {"step": label + ", then energies + PT", "value": round(ns, 6), "unit": UNIT,
+                 "ms_per_step": round(ms, 4)}
+        if paper_ns:
+            entry.update({"paper_gtx480_ns": paper_ns, "ratio_paper_over_ours": round(paper_ns / ns, 1)})
+        out[f"{name}: {label}"] = entry
+        if name == "L128_fp16":
+            per_update[label] = ns
+        ctx.close()
+
+    # tau_int of the squared overlaps q_ab^2 = D_ab(0)^2 of the six pairs of 4
+    # replicas, L = 16, one temperature (T = 0.2: no PT move mixes
+    # configurations), H_r = 0.05 (the energy is a fast observable:
+    # over-relaxation conserves it)
+    smp = inputs.make_sample(16, np.array([0.2]), 0.05, disorder_seed=7)
+    chains = (("lattice: 1 HB + 5 OR", None, 6000, lattice_ns),
+              ("tiles: 10 OR + 1 HB", mh1, 8000, per_update["10 OR + 1 HB per 8^3 tile"]),
+              ("tiles: 10 x (1 HB + 10 OR)", mh10, 8000,
+               per_update["10 x (1 HB + 10 OR) per 8^3 tile"]))
+    tau = {}
+    base = None
+    for label, mh, n, ns_l128 in chains:
+        stream = torch.cuda.Stream(device=dev)
+        ctx = hsg.Context([smp], 4, 3, device=dev.index, stream=stream.cuda_stream,
+                          variant=hsg.VARIANT_TWO_PASS)
+        step = (lambda k: ctx.step(k)) if mh is None else (lambda k: ctx.step_multihit(k, **mh))
+        sweeps = 6 if mh is None else mh["n_rounds"] * (mh["n_or"] + mh["n_hb"])
+        step(max(100, 6000 // sweeps))                 # equilibration: >= 6000 sweeps
+        q2 = np.empty((n, 6))
+        for i in range(n):
+            step(1)
+            q2[i] = ctx.measure_overlaps(chiral=False)["D"][0, 0, :, 0, 0] ** 2
+        ti, _ = analysis.integrated_autocorrelation_time(q2)
+        t_steps = float(np.mean(ti))
+        t_sweeps = t_steps * sweeps
+        cost = t_sweeps * ns_l128                      # per spin, in ns: sweeps x time per update
+        base = cost if base is None else base
+        tau[label] = {"sweeps_per_step": sweeps, "tau_int_steps": round(t_steps, 2),
+                      "tau_int_sweeps": round(t_sweeps, 1), "steps": n,
+                      "reliable": bool(n >= 50 * t_steps),
+                      "ns_per_update_L128": round(ns_l128, 6),
+                      "time_per_uncorrelated_sample_vs_lattice": round(cost / base, 2)}
+        ctx.close()
+    out["tau"] = {"observable": "q_ab^2 of the 6 pairs of 4 replicas, L = 16, T = 0.2, H_r = 0.05",
+                  "chains": tau}
+    return out
 
 
 def time_observables(ctx, reps=3):
@@ -468,6 +551,7 @@ def main():
                         "paper_gtx480_ns": ref_ns, "ratio_paper_over_ours": round(ref_ns / v, 1)}
             r2["ctx"].close()
         line["paper_table1_config"] = t1
+        line["multihit"] = multihit_extras(torch, dev, inputs, value)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(wl)

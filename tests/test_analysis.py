@@ -138,3 +138,28 @@ def test_specific_heat_of_two_level_series():
     np.testing.assert_allclose(u, (a + b) / 2 / Nn)
     np.testing.assert_allclose(c, (a - b) ** 2 / 4 / (T ** 2 * Nn))
     np.testing.assert_allclose(dc, 0.0, atol=1e-12)
+
+
+@pytest.mark.parametrize("phi", [0.0, 0.5, 0.9, 0.98])
+def test_tau_int_of_ar1_process(phi):
+    """x_t = phi x_{t-1} + e_t has rho(t) = phi^t, so tau_int = 1/2 + phi/(1 - phi)
+    = (1 + phi) / (2 (1 - phi)); the estimate's relative error is about
+    sqrt(2 (2W + 1) / n) (Sokal), here a few percent."""
+    rng = np.random.default_rng(int(phi * 100))
+    n = 400_000
+    e = rng.normal(size=n)
+    x = np.empty(n)
+    x[0] = e[0] / np.sqrt(1 - phi ** 2)
+    for t in range(1, n):
+        x[t] = phi * x[t - 1] + e[t]
+    tau, w = analysis.integrated_autocorrelation_time(x)
+    exact = (1 + phi) / (2 * (1 - phi))
+    rel = np.sqrt(2 * (2 * w + 1) / n)
+    assert abs(tau - exact) < 4 * rel * exact + 0.01, (tau, exact, w)
+
+
+def test_tau_int_columns_and_constant_series():
+    x = np.random.default_rng(1).normal(size=(5000, 3))
+    tau, w = analysis.integrated_autocorrelation_time(x)
+    assert tau.shape == (3,) and np.all(np.abs(tau - 0.5) < 0.1)
+    assert analysis.integrated_autocorrelation_time(np.ones(100)) == (0.5, 0)
