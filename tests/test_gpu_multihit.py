@@ -91,14 +91,14 @@ def test_one_tile_sweep(L, tile, n_or, n_hb):
     assert int(sweeps[0]) == n_or + n_hb and int(passes[0]) == 1
 
 
-@pytest.mark.parametrize("L,tile", [(8, 4), (16, 8)])
-def test_multihit_step_within_fp32_spread(L, tile):
+@pytest.mark.parametrize("Ls,tile", [((8, 8), 4), ((16, 16), 8), ((8, 16), 4)])
+def test_multihit_step_within_fp32_spread(Ls, tile):
     """Two rounds of (3 OR + 1 HB) per tile, then energies and PT, for a batch
-    of two samples: spins within the binary32 spread of the FP64 chain,
-    identical permutations and counters."""
+    of two samples (of equal or different size): spins within the binary32
+    spread of the FP64 chain, identical permutations and counters."""
     mh = dict(tile=tile, n_rounds=2, n_or=3, n_hb=1)
     samples = [f32(inputs.small_sample(L, n_temps=4, h_r=0.2, disorder_seed=L + k, t_min=0.3,
-                                       t_max=0.8)) for k in range(2)]
+                                       t_max=0.8)) for k, L in enumerate(Ls)]
     g, o, pg, po, cnt = from_seeded_state(samples, 2, 9, mh)
     d = np.concatenate([np.abs(a - b).ravel() for a, b in zip(g, o)])
     assert_within_fp32_spread(d, fp32_storage_reference(samples, 2, 9, mh))
