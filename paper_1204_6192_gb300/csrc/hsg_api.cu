@@ -602,6 +602,8 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   if (opt.n_hb_per_step < 0 || opt.n_or_per_step < 0)
     return bad_arg(nullptr, "negative sweeps per step");
   if (opt.pass_bytes < 0) return bad_arg(nullptr, "pass_bytes < 0");
+  if (opt.variant < HSG_VARIANT_AUTO || opt.variant > HSG_VARIANT_PERSISTENT)
+    return bad_arg(nullptr, "unknown variant");
   if (opt.chunks_per_thread < 0) return bad_arg(nullptr, "chunks_per_thread < 0");
   const int W = n_temps * n_replicas;
   if (W > 1024) return bad_arg(nullptr, "n_temps * n_replicas must be <= 1024");

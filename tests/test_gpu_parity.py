@@ -470,7 +470,7 @@ def test_invalid_arguments_rejected():
     J[3, 1] = np.nan
     with pytest.raises(hsg.HsgError):
         hsg.Context([inputs.Sample(L=8, J=J, H=smp.H, temps=smp.temps)], 2, 1)
-    for kw in ({"pass_bytes": -1}, {"chunks_per_thread": -2}):
+    for kw in ({"pass_bytes": -1}, {"chunks_per_thread": -2}, {"variant": 3}, {"variant": -1}):
         with pytest.raises(hsg.HsgError) as ei:
             hsg.Context([smp], 2, 1, **kw)
         assert ei.value.status == 1
