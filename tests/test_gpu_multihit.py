@@ -230,3 +230,33 @@ def test_multihit_checkpoint_round_trip_and_persistent_context():
         out.append(ref[0])
         ctx.close()
     np.testing.assert_array_equal(out[0], out[1])
+
+
+def test_multihit_samples_the_same_equilibrium():
+    """Tiles with a fixed halo are a different Markov chain with the same
+    stationary distribution: e(T) per temperature slot from the tile schedule
+    (one round of 5 OR + 1 HB per 4^3 tile, then PT) agrees with the lattice
+    step (1 HB + 5 OR + PT) within the statistical errors (second half of 2000
+    steps, 10 bins, L = 8, 2 replicas x 8 temperatures in [0.15, 0.6])."""
+    t = inputs.geometric_temperatures(0.15, 0.6, 8)
+    smp = inputs.make_sample(8, t, 0.0, disorder_seed=1)
+    steps, nb = 2000, 10
+
+    def e_of_T(multihit):
+        ctx = hsg.Context([smp], 2, 5)
+        E = []
+        for _ in range(steps):
+            if multihit:
+                ctx.step_multihit(1, tile=4, n_rounds=1, n_or=5, n_hb=1)
+            else:
+                ctx.step(1)
+            E.append(ctx.measure(q=False)["E"][0].mean(axis=0) / 512)   # per slot, replica mean
+        ctx.close()
+        x = np.array(E)[steps // 2:]
+        bins = np.array([b.mean(axis=0) for b in np.array_split(x, nb)])
+        return x.mean(axis=0), bins.std(axis=0, ddof=1) / np.sqrt(nb)
+
+    (m1, s1), (m2, s2) = e_of_T(False), e_of_T(True)
+    z = (m1 - m2) / np.sqrt(s1 ** 2 + s2 ** 2)
+    print("e(T) lattice", np.round(m1, 4), "tiles", np.round(m2, 4), "z", np.round(z, 2))
+    assert np.all(np.abs(z) < 4.5) and np.sum(np.abs(z) > 2.5) <= 2, z
