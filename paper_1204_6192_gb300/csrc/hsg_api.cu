@@ -71,6 +71,8 @@ struct hsg_ctx {
   bool e_valid = false;               // d_E holds the energies of the current state
   double* d_D = nullptr;
   double* d_C = nullptr;
+  unsigned char* d_kappa = nullptr;   // chiralities, binary32 chunk layout (at first use)
+  SampleDev* d_sd_k = nullptr;        // the sample table with the chirality buffer's offsets
   double* d_q = nullptr;
   double* d_qk = nullptr;
   float* d_xyz = nullptr;
@@ -1130,6 +1132,23 @@ int overlap_pairs(int R_O) {
   return r * (r - 1) / 2;
 }
 
+// The chirality buffer of the staged chiral overlaps: per sample three planes
+// (a = x, y, z) of Gu chunk groups x N sites x 16 bytes.
+static hsg_status ensure_kappa(hsg_ctx* c, int Gu) {
+  if (c->d_kappa) return HSG_OK;
+  std::vector<SampleDev> kd(c->sd);
+  size_t off = 0;
+  for (int s = 0; s < c->ns; ++s) {
+    kd[s].plane_stride = (long long)Gu * c->sd[s].N * 16;
+    kd[s].spin_off = (long long)off;
+    off += (size_t)(3 * kd[s].plane_stride + 255) / 256 * 256;
+  }
+  HSG_TRY(dev_alloc(c, &c->d_kappa, off));
+  HSG_TRY(dev_alloc(c, &c->d_sd_k, sizeof(SampleDev) * c->ns));
+  HSG_CUDA(c, cudaMemcpy(c->d_sd_k, kd.data(), sizeof(SampleDev) * c->ns, cudaMemcpyHostToDevice));
+  return HSG_OK;
+}
+
 hsg_status hsg_measure_overlaps(hsg_ctx* c, double* D, double* C) {
   HSG_CHECK_CTX(c);
   if (!D && !C) return bad_arg(c, "D and C are both NULL");
@@ -1138,23 +1157,55 @@ hsg_status hsg_measure_overlaps(hsg_ctx* c, double* D, double* C) {
   const int n_pairs = overlap_pairs(c->R_O);
   const long long nmax = (long long)c->Lmax * c->Lmax * c->Lmax;
   const int n_tiles = (int)((nmax + MEAS_TILE - 1) / MEAS_TILE);
-  // the chiral overlaps read neighbours: direct kernel; D alone: staged kernel
+  // D: the staged kernel over the spins.  C: the chiralities of every site
+  // into a binary32 buffer, then the staged kernel over that buffer.  Either
+  // falls back to the direct kernel when its staged systems exceed shared memory.
   const StagedGeom g = staged_geometry(c->fmt, false, c->R_O, c->R_T, nmax, c->total_sites);
+  const StagedGeom gk = staged_geometry(FMT_F32, false, c->R_O, c->R_T, nmax, c->total_sites);
   if (!c->d_opart) {
     const size_t direct = (size_t)n_pairs * n_tiles * meas_partial_values(false, true);
     const size_t staged = g.ok ? (size_t)g.n_tiles * g.values : 0;
-    HSG_TRY(dev_alloc(c, &c->d_opart, sizeof(double) * c->ns * (size_t)c->R_T * std::max(direct, staged)));
+    const size_t staged_c = gk.ok ? (size_t)gk.n_tiles * 3 * gk.values : 0;
+    HSG_TRY(dev_alloc(c, &c->d_opart, sizeof(double) * c->ns * (size_t)c->R_T *
+                                          std::max(direct, std::max(staged, staged_c))));
     HSG_TRY(dev_alloc(c, &c->d_D, sizeof(double) * c->ns * (size_t)c->R_T * n_pairs * 8));
     HSG_TRY(dev_alloc(c, &c->d_C, sizeof(double) * c->ns * (size_t)c->R_T * n_pairs * 24));
   }
-  const bool staged = g.ok && !C;
-  OverlapParams p = overlap_params(c, staged ? g : StagedGeom{});
-  p.partials = c->d_opart;
-  p.D = c->d_D;
-  p.C = C ? c->d_C : nullptr;
-  p.n_pairs = n_pairs;
-  p.n_tiles = staged ? g.n_tiles : n_tiles;
-  HSG_CUDA(c, launch_overlaps(c->fmt, p, C != nullptr, c->stream));
+  if (C && gk.ok) {
+    HSG_TRY(ensure_kappa(c, gk.Gu));
+    for (int parity = 0; parity < 2; ++parity) {
+      ChiralityParams kp;
+      kp.spins = c->spins;
+      kp.kappa = c->d_kappa;
+      kp.samples = c->d_sd;
+      kp.ksamples = c->d_sd_k;
+      kp.blocks = c->d_sweep_blocks;
+      kp.G = c->G;
+      kp.GPT = c->GPT;
+      kp.Gu = gk.Gu;
+      kp.parity = parity;
+      HSG_CUDA(c, launch_chirality(c->fmt, kp, c->n_sweep_blocks, c->stream));
+    }
+    OverlapParams pc = overlap_params(c, gk);
+    pc.spins = c->d_kappa;
+    pc.samples = c->d_sd_k;
+    pc.partials = c->d_opart;
+    pc.C = c->d_C;
+    pc.n_pairs = n_pairs;
+    pc.n_tiles = gk.n_tiles;
+    HSG_CUDA(c, launch_chiral_staged(pc, c->stream));
+  }
+  const bool direct_c = C && !gk.ok;       // the direct kernel gives D and C together
+  if (D || direct_c) {
+    const bool staged = g.ok && !direct_c;
+    OverlapParams p = overlap_params(c, staged ? g : StagedGeom{});
+    p.partials = c->d_opart;
+    p.D = c->d_D;
+    p.C = direct_c ? c->d_C : nullptr;
+    p.n_pairs = n_pairs;
+    p.n_tiles = staged ? g.n_tiles : n_tiles;
+    HSG_CUDA(c, launch_overlaps(c->fmt, p, direct_c, c->stream));
+  }
   if (D)
     HSG_CUDA(c, cudaMemcpyAsync(D, c->d_D, sizeof(double) * c->ns * c->R_T * n_pairs * 8,
                                 cudaMemcpyDeviceToHost, c->stream));

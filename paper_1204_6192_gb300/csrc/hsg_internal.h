@@ -125,6 +125,20 @@ struct StagedGeom {
 StagedGeom staged_geometry(int fmt, bool qtensor, int R_O, int R_T, long long n_max,
                            long long n_total);
 
+// Chiral overlaps in two stages: the chirality of every site into a binary32
+// buffer in the chunk layout ([a][g][ss][4], g < Gu), then the staged kernel
+// over that buffer.
+struct ChiralityParams {
+  const unsigned char* spins;
+  unsigned char* kappa;
+  const SampleDev* samples;     // the spins' sample table
+  const SampleDev* ksamples;    // the same samples with the buffer's offsets and plane strides
+  const int4* blocks;           // the sweep block table
+  int G, GPT, Gu, parity;
+};
+cudaError_t launch_chirality(int fmt, const ChiralityParams& p, int n_blocks, cudaStream_t st);
+cudaError_t launch_chiral_staged(const OverlapParams& p, cudaStream_t st);
+
 struct ConvParams {
   unsigned char* spins;
   const SampleDev* samples;

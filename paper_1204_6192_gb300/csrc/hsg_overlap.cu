@@ -82,7 +82,7 @@ __device__ __forceinline__ V3 spin_at(const unsigned char* base, const SampleDev
 constexpr int NM = 7;        // per product: k = 0, then (re, im) of kx, ky, kz
 
 // what a launch measures
-enum { MEAS_QTENSOR = 0, MEAS_PAIRS = 1, MEAS_PAIRS_CHIRAL = 2 };
+enum { MEAS_QTENSOR = 0, MEAS_PAIRS = 1, MEAS_PAIRS_CHIRAL = 2, MEAS_CHIRAL = 3 };
 
 // products per site of one launch unit: a row mu of the tensor (A^mu B^nu,
 // nu = x, y, z; three units), or D (and C^x, C^y, C^z) of one pair
@@ -257,7 +257,7 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
 // products of NR replicas
 template <int MODE, int NR>
 __host__ __device__ constexpr int staged_products() {
-  return MODE == MEAS_QTENSOR ? 9 : NR * (NR - 1) / 2;
+  return MODE == MEAS_QTENSOR ? 9 : (MODE == MEAS_CHIRAL ? 3 : 1) * (NR * (NR - 1) / 2);
 }
 
 }  // namespace
@@ -385,6 +385,18 @@ __global__ void __launch_bounds__(MEAS_BS) k_meas_staged(const OverlapParams p) 
         for (int mu = 0; mu < 3; ++mu)
 #pragma unroll
           for (int nu = 0; nu < 3; ++nu) P[3 * mu + nu] = __fmul_rn(A[mu], B[nu]);
+      } else if constexpr (MODE == MEAS_CHIRAL) {
+        // the staged "spins" are the chiralities (kappa^x, kappa^y, kappa^z):
+        // per pair, in the pair order below, the three products kappa^a kappa^b
+        int q = 0;
+#pragma unroll
+        for (int bb = 1; bb < NR; ++bb)
+#pragma unroll
+          for (int aa = 0; aa < bb; ++aa) {
+            P[q++] = __fmul_rn(S[aa].x, S[bb].x);
+            P[q++] = __fmul_rn(S[aa].y, S[bb].y);
+            P[q++] = __fmul_rn(S[aa].z, S[bb].z);
+          }
       } else {
         // pairs in the order (0,1) (0,2) (1,2) (0,3) (1,3) (2,3)
         int q = 0;
@@ -477,6 +489,13 @@ __global__ void __launch_bounds__(256) k_meas_final_staged(const OverlapParams p
       const int d = (m - 1) / 2, ri = (m - 1) % 2;
       p.C[(((long long)s * p.R_T + t) * 3 + d) * 18 + q * 2 + ri] = val;
     }
+  } else if constexpr (MODE == MEAS_CHIRAL) {
+    if (p.C) {
+      const int mode = m == 0 ? 0 : 1 + (m - 1) / 2, ri = m == 0 ? 0 : (m - 1) % 2;
+      double* dst = p.C + (((long long)s * p.R_T + t) * p.n_pairs + q / 3) * 24 + (q % 3) * 8;
+      dst[2 * mode + ri] = val;
+      if (m == 0) dst[1] = 0.0;
+    }
   } else if (p.D) {
     const int mode = m == 0 ? 0 : 1 + (m - 1) / 2, ri = m == 0 ? 0 : (m - 1) % 2;
     double* dst = p.D + (((long long)s * p.R_T + t) * p.n_pairs + q) * 8;
@@ -538,6 +557,80 @@ static cudaError_t meas_dispatch(int fmt, const OverlapParams& p, int mode, cuda
     case FMT_ANG16: return meas_fmt<FMT_ANG16>(p, mode, st);
     case FMT_OCT16: return meas_fmt<FMT_OCT16>(p, mode, st);
     case FMT_YX4: return meas_fmt<FMT_YX4>(p, mode, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Local chirality of every site for the chunk groups g < Gu (Sec. 2):
+// kappa_i^a = s_{i+a} . (s_i x s_{i-a}) along a = x, y, z, written as binary32
+// in the chunk layout of the spins ([a][g][ss][4 systems]), so that the staged
+// kernel forms the chiral pair overlaps from it as it forms D from spins.  One
+// launch per parity over the sweep block table; a thread owns one site and
+// walks its chunk groups, as the sweeps do.
+template <int F>
+__global__ void __launch_bounds__(SWEEP_BS) k_chirality(const ChiralityParams p) {
+  constexpr int VEC = 4, PL = FmtInfo<F>::PLANES;
+  using Chunk = typename FmtInfo<F>::Chunk;
+  const int4 blk = p.blocks[blockIdx.x];
+  const SampleDev& sd = p.samples[blk.x];
+  const uint32_t h = (uint32_t)blk.z + threadIdx.x;
+  if (h >= ((uint32_t)sd.N >> 1)) return;
+  const int g0 = blk.y * p.GPT, g1 = min(p.Gu, min(p.G, g0 + p.GPT));
+  if (g0 >= g1) return;
+  const SiteGeom gm = site_geom(sd, h, p.parity);        // neighbours +x, -x, +y, -y, +z, -z
+  const unsigned char* base = p.spins + sd.spin_off;
+  const long long ps = sd.plane_stride;
+  const SampleDev& kd = p.ksamples[blk.x];
+  unsigned char* kb = p.kappa + kd.spin_off;
+  const long long kps = kd.plane_stride;
+  for (int g = g0; g < g1; ++g) {
+    Chunk c[PL];
+    load_chunks<F, LD_RO>(base + chunk_offset<F>(sd, g, gm.own), ps, c);
+    Spins<VEC> s0;
+    decode<F>(c, s0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      Chunk cp[PL], cm[PL];
+      load_chunks<F, LD_RO>(base + chunk_offset<F>(sd, g, gm.nb[2 * a]), ps, cp);
+      load_chunks<F, LD_RO>(base + chunk_offset<F>(sd, g, gm.nb[2 * a + 1]), ps, cm);
+      Spins<VEC> sp, sm;
+      decode<F>(cp, sp);
+      decode<F>(cm, sm);
+      float k4[VEC];
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) {
+        const int q = v >> 1;
+        const bool hi = v & 1;
+        const V3 A = {hi ? sp.x[q].y : sp.x[q].x, hi ? sp.y[q].y : sp.y[q].x, hi ? sp.z[q].y : sp.z[q].x};
+        const V3 Bv = {hi ? s0.x[q].y : s0.x[q].x, hi ? s0.y[q].y : s0.y[q].x, hi ? s0.z[q].y : s0.z[q].x};
+        const V3 Cv = {hi ? sm.x[q].y : sm.x[q].x, hi ? sm.y[q].y : sm.y[q].x, hi ? sm.z[q].y : sm.z[q].x};
+        k4[v] = triple(A, Bv, Cv);
+      }
+      *reinterpret_cast<float4*>(kb + a * kps + ((long long)g * sd.N + gm.own) * 16) =
+          make_float4(k4[0], k4[1], k4[2], k4[3]);
+    }
+  }
+}
+
+cudaError_t launch_chirality(int fmt, const ChiralityParams& p, int n_blocks, cudaStream_t st) {
+  switch (fmt) {
+    case FMT_F32: k_chirality<FMT_F32><<<n_blocks, SWEEP_BS, 0, st>>>(p); break;
+    case FMT_F16: k_chirality<FMT_F16><<<n_blocks, SWEEP_BS, 0, st>>>(p); break;
+    case FMT_BF16: k_chirality<FMT_BF16><<<n_blocks, SWEEP_BS, 0, st>>>(p); break;
+    case FMT_ANG16: k_chirality<FMT_ANG16><<<n_blocks, SWEEP_BS, 0, st>>>(p); break;
+    case FMT_OCT16: k_chirality<FMT_OCT16><<<n_blocks, SWEEP_BS, 0, st>>>(p); break;
+    case FMT_YX4: k_chirality<FMT_YX4><<<n_blocks, SWEEP_BS, 0, st>>>(p); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// chiral pair overlaps from the binary32 chirality buffer (staged kernel)
+cudaError_t launch_chiral_staged(const OverlapParams& p, cudaStream_t st) {
+  switch (min(p.R_O, 4)) {
+    case 2: return staged_launch<FMT_F32, MEAS_CHIRAL, 2>(p, st);
+    case 3: return staged_launch<FMT_F32, MEAS_CHIRAL, 3>(p, st);
+    case 4: return staged_launch<FMT_F32, MEAS_CHIRAL, 4>(p, st);
   }
   return cudaErrorInvalidValue;
 }

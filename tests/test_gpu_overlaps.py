@@ -1,6 +1,7 @@
 """GPU replica-pair and chiral overlaps (hsg_measure_overlaps) against the FP64
-oracle on the same spins, through both kernels: the staged one (D alone) and
-the direct one (D with the chiral overlaps).
+oracle on the same spins, through every path: D from the staged kernel over
+the spins, C from the chirality buffer and the staged kernel over it, and the
+direct kernel (D with C) where the staged systems exceed shared memory.
 
 The GPU reads the stored spins; hsg_get_spins returns exactly the decoded
 values, so the oracle sees the same configurations.  Per-thread sums run in FP32
@@ -109,4 +110,15 @@ def test_overlaps_invalid_arguments():
     assert ctx.info().n_overlap_pairs == 0
     with pytest.raises(hsg.HsgError):
         ctx.measure_overlaps()
+    ctx.close()
+
+
+def test_overlaps_direct_kernel_for_many_slots():
+    """Four replicas x 100 slots: the staged rows exceed the shared-memory
+    budget, so the direct kernel measures D and C; same results."""
+    samples = [inputs.small_sample(4, n_temps=100, h_r=0.1, disorder_seed=12, t_min=0.2, t_max=2.0)]
+    ctx = hsg.Context(samples, 4, 9, precision="fp32")
+    ctx.step(1)
+    compare_with_oracle(ctx, samples, 4, chiral=True)
+    compare_with_oracle(ctx, samples, 4, chiral=False)
     ctx.close()
