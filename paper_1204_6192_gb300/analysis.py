@@ -17,9 +17,10 @@ Definitions:
 * second-moment correlation length      xi = (chi(0)/chi(k_min) - 1)^{1/2} / (2 sin(k_min/2)),
   k_min = 2 pi / L
 * internal energy and specific heat per spin, u = [<E>]/N and c = [<E^2> - <E>^2]/(T^2 N)
-* integrated autocorrelation time of a series (the paper's "time to generate
-  uncorrelated events", Sec. 4): tau_int = 1/2 + sum_{t=1}^{W} rho(t), with the
-  window W the first t >= c tau_int(t) (Sokal's self-consistent window, c = 6)
+* integrated autocorrelation time of a series, which turns a time per update
+  into a time per independent sample (the comparison of schedules Sec. 4 asks
+  for): tau_int = 1/2 + sum_{t=1}^{W} rho(t), with the window W the first
+  t >= c tau_int(t) (Sokal's self-consistent window, c = 6)
 """
 from __future__ import annotations
 
