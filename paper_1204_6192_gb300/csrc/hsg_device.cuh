@@ -59,6 +59,19 @@ enum { TAG_INIT = 0, TAG_HB = 1, TAG_PT = 2 };
 // Packed pair arithmetic (two systems per instruction).
 // ----------------------------------------------------------------------------
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+// Single-instruction reciprocal and square root (at most 1 ulp from the
+// correctly rounded results; the heat bath's inputs are normal numbers).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // Packed binary32 pair arithmetic as PTX with an explicit rounding modifier:
 // PTX never contracts such instructions into fused multiply-adds, so every
 // kernel that inlines these helpers rounds identically.
@@ -420,7 +433,7 @@ __device__ __forceinline__ void hb_move(float& sx, float& sy, float& sz, float h
   const float a = __fmul_rn(beta, hn);
   float dm, dp;
   if (a > 1e-12f) {
-    const float inv_a = __frcp_rn(a);
+    const float inv_a = rcp_approx(a);
     const float om = __fsub_rn(1.0f, u1);
     if (FAST) {
       dm = __fmul_rn(-__logf(__fmaf_rn(om, __fsub_rn(__expf(-2.0f * a), 1.0f), 1.0f)), inv_a);
@@ -443,7 +456,7 @@ __device__ __forceinline__ void hb_move(float& sx, float& sy, float& sz, float h
   dm = fminf(2.0f, fmaxf(0.0f, dm));
   dp = fminf(2.0f, fmaxf(0.0f, dp));
   const float ct = (dm <= 1.0f) ? __fsub_rn(1.0f, dm) : __fsub_rn(dp, 1.0f);
-  const float st = __fsqrt_rn(__fmul_rn(dm, dp));
+  const float st = sqrt_approx(__fmul_rn(dm, dp));
   float sp, cp;
   if (FAST) {
     __sincosf(__fmul_rn(6.28318530717959f, __fsub_rn(u2, 0.5f)), &sp, &cp);
@@ -459,7 +472,7 @@ __device__ __forceinline__ void hb_move(float& sx, float& sy, float& sz, float h
     nz = __fmul_rn(hz, rs);
   }
   const float sg = nz >= 0.0f ? 1.0f : -1.0f;
-  const float A = -__frcp_rn(__fadd_rn(sg, nz));
+  const float A = -rcp_approx(__fadd_rn(sg, nz));
   const float B = __fmul_rn(__fmul_rn(nx, ny), A);
   const float e1x = __fmaf_rn(sg, __fmul_rn(__fmul_rn(nx, nx), A), 1.0f);
   const float e1y = __fmul_rn(sg, B), e1z = -__fmul_rn(sg, nx);
