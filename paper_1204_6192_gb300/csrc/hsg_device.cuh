@@ -96,6 +96,11 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
   asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)));
   return u2f(r);
 }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)), "l"(f2u(c)));
+  return u2f(r);
+}
 
 // ----------------------------------------------------------------------------
 // Storage formats.  A chunk holds VEC = 4 systems of one site in one "plane":
@@ -386,24 +391,11 @@ __device__ __forceinline__ void or_move2(float2& sx, float2& sy, float2& sz, flo
   if (hh.y > 0.0f) { sx.y = nx.y; sy.y = ny.y; sz.y = nz.y; }
 }
 
-// (sin, cos) of 2 pi u for a uniform u in (0, 1).  4u is exact in binary32,
-// so the reduction to the nearest quadrant, f = 4u - q in [-1/2, 1/2], is exact;
-// r = f pi/2 lies in [-pi/4, pi/4], where the Taylor series of sin (to r^9) and
-// cos (to r^10) are truncated below 3e-9; the quadrant rotation is exact.
-__device__ __forceinline__ void sincos_2pi(float u, float& s, float& c) {
-  const float t = __fmul_rn(4.0f, u);
-  const float q = rintf(t);
-  const float r = __fmul_rn(__fsub_rn(t, q), 1.57079632679489662f);
-  const float r2 = __fmul_rn(r, r);
-  float ps = fmaf(r2, 2.75573192e-6f, -1.98412698e-4f);   // 1/9!, -1/7!
-  ps = fmaf(r2, ps, 8.33333333e-3f);                       // 1/5!
-  ps = fmaf(r2, ps, -1.66666667e-1f);                      // -1/3!
-  const float sr = fmaf(__fmul_rn(r, r2), ps, r);
-  float pc = fmaf(r2, -2.75573192e-7f, 2.48015873e-5f);    // -1/10!, 1/8!
-  pc = fmaf(r2, pc, -1.38888889e-3f);                      // -1/6!
-  pc = fmaf(r2, pc, 4.16666667e-2f);                       // 1/4!
-  pc = fmaf(r2, pc, -0.5f);                                // -1/2!
-  const float cr = fmaf(r2, pc, 1.0f);
+// (sin, cos) of 2 pi u for a uniform u in (0, 1), for one system or a pair.
+// 4u is exact in binary32, so the reduction to the nearest quadrant, f = 4u - q in [-1/2, 1/2],
+// is exact; r = f pi/2 lies in [-pi/4, pi/4], where the Taylor series of sin (to
+// r^9) and cos (to r^10) are truncated below 3e-9; the quadrant rotation is exact.
+__device__ __forceinline__ void sincos_2pi_rot(float q, float sr, float cr, float& s, float& c) {
   // rotate by q quarter turns, without branches: odd q swaps sin and cos,
   // q = 2, 3 negate sin, q = 1, 2 negate cos
   const int qi = ((int)q) & 3;
@@ -412,26 +404,55 @@ __device__ __forceinline__ void sincos_2pi(float u, float& s, float& c) {
   s = (qi & 2) ? -a : a;
   c = ((qi + 1) & 2) ? -b : b;
 }
+__device__ __forceinline__ void sincos_2pi(float u, float& s, float& c) {
+  const float t = __fmul_rn(4.0f, u);
+  const float q = rintf(t);
+  const float r = __fmul_rn(__fsub_rn(t, q), 1.57079632679489662f);
+  const float r2 = __fmul_rn(r, r);
+  float ps = fmaf(r2, 2.75573192e-6f, -1.98412698e-4f);
+  ps = fmaf(r2, ps, 8.33333333e-3f);
+  ps = fmaf(r2, ps, -1.66666667e-1f);
+  const float sr = fmaf(__fmul_rn(r, r2), ps, r);
+  float pc = fmaf(r2, -2.75573192e-7f, 2.48015873e-5f);
+  pc = fmaf(r2, pc, -1.38888889e-3f);
+  pc = fmaf(r2, pc, 4.16666667e-2f);
+  pc = fmaf(r2, pc, -0.5f);
+  const float cr = fmaf(r2, pc, 1.0f);
+  sincos_2pi_rot(q, sr, cr, s, c);
+}
+__device__ __forceinline__ void sincos_2pi2(float2 u, float2& s, float2& c) {
+  const float2 t = mul2(f2(4.0f), u);
+  const float2 q = make_float2(rintf(t.x), rintf(t.y));
+  const float2 r = mul2(sub2(t, q), f2(1.57079632679489662f));
+  const float2 r2 = mul2(r, r);
+  float2 ps = fma2(r2, f2(2.75573192e-6f), f2(-1.98412698e-4f));   // 1/9!, -1/7!
+  ps = fma2(r2, ps, f2(8.33333333e-3f));                            // 1/5!
+  ps = fma2(r2, ps, f2(-1.66666667e-1f));                           // -1/3!
+  const float2 sr = fma2(mul2(r, r2), ps, r);
+  float2 pc = fma2(r2, f2(-2.75573192e-7f), f2(2.48015873e-5f));   // -1/10!, 1/8!
+  pc = fma2(r2, pc, f2(-1.38888889e-3f));                           // -1/6!
+  pc = fma2(r2, pc, f2(4.16666667e-2f));                            // 1/4!
+  pc = fma2(r2, pc, f2(-0.5f));                                     // -1/2!
+  const float2 cr = fma2(r2, pc, f2(1.0f));
+  sincos_2pi_rot(q.x, sr.x, cr.x, s.x, c.x);
+  sincos_2pi_rot(q.y, sr.y, cr.y, s.y, c.y);
+}
 
-// Heat bath, Eq. (2), one system: s' ~ exp(beta h.s) from the uniforms u1, u2.
-// With a = beta |h| and t the angle to h, the inverse CDF of exp(a cos t) on
-// [-1, 1] gives both distances to the poles in a well-conditioned form:
+// Heat bath, Eq. (2): s' ~ exp(beta h.s) from the uniforms u1, u2.  With
+// a = beta |h| and t the angle to h, the inverse CDF of exp(a cos t) on [-1, 1]
+// gives both distances to the poles in a well-conditioned form:
 //   dm = 1 - cos t = -log1p((1 - u1) expm1(-2a)) / a
 //   dp = 1 + cos t =  log1p(u1 expm1(2a)) / a        (dm + dp = 2)
 // so sin t = sqrt(dm dp) keeps full relative accuracy near both poles (FP32
 // loses it in 2 - dm when cos t is close to -1).  The azimuth is 2 pi u2 in
 // the frame of Duff et al. (JCGT 6(1), 2017) around h/|h|.
+//
+// hb_poles is the scalar part (one system: branches on a and on the side of
+// the equator); hb_move2 moves two systems with packed pair arithmetic around
+// it.  Every product and sum is an explicit round-to-nearest operation, so no
+// kernel that inlines these functions can round them differently.
 template <bool FAST>
-__device__ __forceinline__ void hb_move(float& sx, float& sy, float& sz, float hx, float hy,
-                                        float hz, float beta, float u1, float u2) {
-  // every product and sum below is an explicit intrinsic, so no kernel that
-  // inlines this function can round it differently
-  const float hn2 = __fmaf_rn(hz, hz, __fmaf_rn(hy, hy, __fmul_rn(hx, hx)));
-  const bool zero = !(hn2 > 0.0f);
-  const float rs = zero ? 0.0f : rsqrtf(hn2);      // 1 / |h|
-  const float hn = __fmul_rn(hn2, rs);             // |h|
-  const float a = __fmul_rn(beta, hn);
-  float dm, dp;
+__device__ __forceinline__ void hb_poles(float a, float u1, float& dm, float& dp) {
   if (a > 1e-12f) {
     const float inv_a = rcp_approx(a);
     const float om = __fsub_rn(1.0f, u1);
@@ -455,6 +476,69 @@ __device__ __forceinline__ void hb_move(float& sx, float& sy, float& sz, float h
   }
   dm = fminf(2.0f, fmaxf(0.0f, dm));
   dp = fminf(2.0f, fmaxf(0.0f, dp));
+}
+
+template <bool FAST>
+__device__ __forceinline__ void hb_move2(float2& sx, float2& sy, float2& sz, float2 hx, float2 hy,
+                                         float2 hz, float2 beta, float2 u1, float2 u2) {
+  const float2 hn2 = fma2(hz, hz, fma2(hy, hy, mul2(hx, hx)));
+  const bool zx = !(hn2.x > 0.0f), zy = !(hn2.y > 0.0f);
+  const float2 rs = make_float2(zx ? 0.0f : rsqrtf(hn2.x), zy ? 0.0f : rsqrtf(hn2.y));   // 1/|h|
+  const float2 a = mul2(beta, mul2(hn2, rs));                                             // beta |h|
+  float2 dm, dp;
+  hb_poles<FAST>(a.x, u1.x, dm.x, dp.x);
+  hb_poles<FAST>(a.y, u1.y, dm.y, dp.y);
+  const float2 ct = make_float2((dm.x <= 1.0f) ? __fsub_rn(1.0f, dm.x) : __fsub_rn(dp.x, 1.0f),
+                                (dm.y <= 1.0f) ? __fsub_rn(1.0f, dm.y) : __fsub_rn(dp.y, 1.0f));
+  const float2 dd = mul2(dm, dp);
+  const float2 st = make_float2(sqrt_approx(dd.x), sqrt_approx(dd.y));
+  float2 sp, cp;
+  if (FAST) {
+    const float2 w = mul2(f2(6.28318530717959f), sub2(u2, f2(0.5f)));
+    __sincosf(w.x, &sp.x, &cp.x);
+    __sincosf(w.y, &sp.y, &cp.y);
+    sp = make_float2(-sp.x, -sp.y);
+    cp = make_float2(-cp.x, -cp.y);
+  } else {
+    sincos_2pi2(u2, sp, cp);
+  }
+  float2 nx = mul2(hx, rs), ny = mul2(hy, rs), nz = mul2(hz, rs);
+  if (zx) { nx.x = 0.0f; ny.x = 0.0f; nz.x = 1.0f; }
+  if (zy) { nx.y = 0.0f; ny.y = 0.0f; nz.y = 1.0f; }
+  const float2 sg = make_float2(nz.x >= 0.0f ? 1.0f : -1.0f, nz.y >= 0.0f ? 1.0f : -1.0f);
+  const float2 sn = add2(sg, nz);
+  const float2 A = make_float2(-rcp_approx(sn.x), -rcp_approx(sn.y));
+  const float2 B = mul2(mul2(nx, ny), A);
+  const float2 e1x = fma2(sg, mul2(mul2(nx, nx), A), f2(1.0f));
+  const float2 e1y = mul2(sg, B);
+  const float2 sgnx = mul2(sg, nx);
+  const float2 e1z = make_float2(-sgnx.x, -sgnx.y);
+  const float2 e2x = B, e2y = fma2(mul2(ny, ny), A, sg), e2z = make_float2(-ny.x, -ny.y);
+  const float2 px = fma2(sp, e2x, mul2(cp, e1x));
+  const float2 py = fma2(sp, e2y, mul2(cp, e1y));
+  const float2 pz = fma2(sp, e2z, mul2(cp, e1z));
+  const float2 ox = fma2(st, px, mul2(ct, nx));
+  const float2 oy = fma2(st, py, mul2(ct, ny));
+  const float2 oz = fma2(st, pz, mul2(ct, nz));
+  const float2 n2 = fma2(oz, oz, fma2(oy, oy, mul2(ox, ox)));
+  const float2 inv = make_float2(rsqrtf(n2.x), rsqrtf(n2.y));
+  sx = mul2(ox, inv);
+  sy = mul2(oy, inv);
+  sz = mul2(oz, inv);
+}
+
+// The same move for one system, in the same operations and order (so the two
+// give identical bits).  The tile kernel uses it: with two systems in flight
+// the packed form needs more registers than its occupancy leaves.
+template <bool FAST>
+__device__ __forceinline__ void hb_move(float& sx, float& sy, float& sz, float hx, float hy,
+                                        float hz, float beta, float u1, float u2) {
+  const float hn2 = __fmaf_rn(hz, hz, __fmaf_rn(hy, hy, __fmul_rn(hx, hx)));
+  const bool zero = !(hn2 > 0.0f);
+  const float rs = zero ? 0.0f : rsqrtf(hn2);
+  const float a = __fmul_rn(beta, __fmul_rn(hn2, rs));
+  float dm, dp;
+  hb_poles<FAST>(a, u1, dm, dp);
   const float ct = (dm <= 1.0f) ? __fsub_rn(1.0f, dm) : __fsub_rn(dp, 1.0f);
   const float st = sqrt_approx(__fmul_rn(dm, dp));
   float sp, cp;

@@ -129,10 +129,9 @@ __device__ __forceinline__ void sweep_block(const SweepParams& p, int bidx, floa
         for (int k = 0; k < VEC / 2; ++k) {
           const uint4 r = philox4x32_10_rk(make_uint4(gm.site, (sys0 >> 1) + k, sweep, TAG_HB),
                                            p.rk);
-          hb_move<FAST>(s.x[k].x, s.y[k].x, s.z[k].x, hf.x[k].x, hf.y[k].x, hf.z[k].x,
-                        bt[2 * k], u01(r.x), u01(r.y));
-          hb_move<FAST>(s.x[k].y, s.y[k].y, s.z[k].y, hf.x[k].y, hf.y[k].y, hf.z[k].y,
-                        bt[2 * k + 1], u01(r.z), u01(r.w));
+          hb_move2<FAST>(s.x[k], s.y[k], s.z[k], hf.x[k], hf.y[k], hf.z[k],
+                         make_float2(bt[2 * k], bt[2 * k + 1]), make_float2(u01(r.x), u01(r.z)),
+                         make_float2(u01(r.y), u01(r.w)));
         }
       } else {
 #pragma unroll

@@ -99,8 +99,14 @@ __device__ __forceinline__ void sh_write(typename Sh<F>::E* A, int cs, int q,
 
 }  // namespace
 
+// Binary32 tiles: at most 80 registers per thread, i.e. 3 blocks of 256 threads
+// (T = 8) or 24 of 32 (T = 4) per SM; unbounded they take 92-99 registers and
+// run 2 blocks per SM.  The 16-bit formats compile to 80 registers unbounded.
+template <int F, int T>
+constexpr int multihit_min_blocks() { return F == FMT_F32 ? (T == 8 ? 3 : 24) : 0; }
+
 template <int F, bool J16, bool FAST, int T>
-__global__ void __launch_bounds__(TileShape<T>::NT) k_multihit(const MultihitParams p) {
+__global__ void __launch_bounds__(TileShape<T>::NT, multihit_min_blocks<F, T>()) k_multihit(const MultihitParams p) {
   using TS = TileShape<T>;
   using E = typename Sh<F>::E;
   constexpr int VEC = 4, PL = FmtInfo<F>::PLANES;

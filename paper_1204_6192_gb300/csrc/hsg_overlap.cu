@@ -247,12 +247,6 @@ namespace {
 
 constexpr int MS_STAGES = 3;   // stages in flight per block
 
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-  unsigned long long r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)), "l"(f2u(c)));
-  return u2f(r);
-}
-
 // products per site: the nine A^mu B^nu of replicas 0 and 1, or the pair dot
 // products of NR replicas
 template <int MODE, int NR>
