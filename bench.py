@@ -386,13 +386,13 @@ class OracleSample:
     sweep; heat-bath and over-relaxation sweeps alternate in the 1:5 ratio of
     the step, with energies and a PT pass after every sixth sweep."""
 
-    def __init__(self, wl):
+    def __init__(self, wl, n_temps=8):
         import oracle
         from paper_1204_6192_gb300 import inputs
         oracle.build()
         self.threads = int(oracle.lib().orc_num_threads())
         smp = wl.samples[0]
-        n_t = min(8, len(smp.temps))
+        n_t = min(n_temps, len(smp.temps))
         sub = inputs.Sample(L=smp.L,
                             J=inputs.round_fp16(smp.J) if wl.j_fp16 else smp.J,
                             H=inputs.round_fp16(smp.H) if wl.j_fp16 else smp.H,
@@ -418,6 +418,24 @@ class OracleSample:
                 f"(HB:OR 1:5, PT every 6), {updates} spin updates in {dt:.1f} s")
 
 
+def cpu_model():
+    """The host CPU as /proc/cpuinfo names it (x86: model name; Arm: implementer
+    and part numbers), with the core count."""
+    import platform
+    name = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read().splitlines()
+        for key in ("model name", "CPU part"):
+            vals = [ln.split(":", 1)[1].strip() for ln in info if ln.startswith(key)]
+            if vals:
+                name = vals[0] if key == "model name" else f"Arm CPU part {vals[0]}"
+                break
+    except OSError:
+        pass
+    return f"{name or platform.processor() or 'unknown'} ({platform.machine()}, {os.cpu_count()} cores)"
+
+
 def cpu_baseline(wl, max_seconds=20.0):
     ob = OracleSample(wl)
     updates = 0
@@ -429,9 +447,25 @@ def cpu_baseline(wl, max_seconds=20.0):
         if time.perf_counter() - t0 > 3 * max_seconds:
             break
     dt = time.perf_counter() - t0
-    return {"value": round(dt * 1e9 / updates, 4), "unit": UNIT,
-            "cores": min(ob.threads, ob.W), "kind": "oracle",
-            "sample": ob.describe(n, updates, dt)}
+    out = {"value": round(dt * 1e9 / updates, 4), "unit": UNIT,
+           "cores": min(ob.threads, ob.W), "kind": "oracle",
+           "sample": ob.describe(n, updates, dt), "cpu": cpu_model()}
+    # the same oracle on one core (the setting of the paper's serial CPU figures),
+    # one step's sweeps (1 HB + 5 OR + PT) of 2 of the systems
+    import oracle
+    one = OracleSample(wl, n_temps=1)
+    oracle.lib().orc_set_num_threads(1)
+    try:
+        updates1 = 0
+        t1 = time.perf_counter()
+        for _ in range(6):
+            updates1 += one.step()
+        dt1 = time.perf_counter() - t1
+    finally:
+        oracle.lib().orc_set_num_threads(ob.threads)
+    out["single_core"] = {"value": round(dt1 * 1e9 / updates1, 4), "unit": UNIT,
+                          "sample": one.describe(6, updates1, dt1)}
+    return out
 
 
 def main():

@@ -77,6 +77,7 @@ def lib():
             "orc_chirality": (None, [dp, c_int, dp]),
             "orc_overlaps": (None, [dp, c_int, c_int, c_int, i32p, dp, dp]),
             "orc_num_threads": (c_int, []),
+            "orc_set_num_threads": (None, [c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)

@@ -547,3 +547,13 @@ int orc_num_threads(void) {
   return 1;
 #endif
 }
+
+/* Threads of the later parallel loops (timing only: every loop is over
+   independent systems or sites, so the results do not depend on it). */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}

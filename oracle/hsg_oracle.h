@@ -87,6 +87,7 @@ void   orc_chirality(const double* s, int L, double* kappa);
 void   orc_overlaps(const double* s, int L, int R_O, int R_T, const int32_t* perm, double* D,
                     double* C);
 int    orc_num_threads(void);
+void   orc_set_num_threads(int n);
 
 #ifdef __cplusplus
 }
