@@ -182,3 +182,25 @@ def test_paper_field_has_fixed_length_and_uniform_direction():
     c = smp.H[:, 2] / n
     assert stats.kstest(c, stats.uniform(loc=-1, scale=2).cdf).pvalue > 1e-3
     assert np.abs(smp.H.mean(axis=0)).max() < 5 * 0.3 / np.sqrt(3 * len(n))
+
+
+def test_results_do_not_depend_on_the_thread_count():
+    """The parallel loops run over independent systems or sites, so one thread
+    and all threads give the same bits (the timed CPU baseline uses both)."""
+    import oracle
+    L = oracle.lib()
+    n0 = int(L.orc_num_threads())
+    out = []
+    try:
+        for n in (1, max(2, n0)):
+            L.orc_set_num_threads(n)
+            smp = inputs.small_sample(8, n_temps=4, h_r=0.1, disorder_seed=11)
+            sim = oracle.OracleSim([smp], 2, 5)
+            sim.sweep_hb(2)
+            sim.sweep_or(3)
+            sim.pt_exchange()
+            out.append((np.array(sim.spins()[0]), np.array(sim.energies()[0])))
+    finally:
+        L.orc_set_num_threads(n0)
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
