@@ -623,7 +623,8 @@ def run_reference(args, world, rank):
             "config": {"workload": args.workload, "L": wl.samples[0].L, "storage": wl.precision,
                        "step": "one oracle sweep of a 16-system sample (HB:OR 1:5, PT every 6)"},
             "cpu_baseline": {"value": round(value, 4), "unit": UNIT,
-                             "cores": min(ob.threads, ob.W), "kind": "oracle", "sample": sample},
+                             "cores": min(ob.threads, ob.W), "kind": "oracle", "sample": sample,
+                             "cpu": cpu_model()},
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
