@@ -153,15 +153,25 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def algorithmic_half_sweep_bytes(ctx, wl):
-    """Bytes one half-sweep launch must move in the two-pass form: per updated
-    spin its own read + write and one read of the opposite-parity spin it sees
-    (3 S per update), plus the 6 bonds and 3 field components of every updated
-    site (shared by the W systems of the sample)."""
-    S = {"fp32": 12, "fp16": 6, "bf16": 6, "angle16": 4, "oct16": 4, "yx4": 8}[wl.precision]
+SPIN_BYTES = {"fp32": 12, "fp16": 6, "bf16": 6, "angle16": 4, "oct16": 4, "yx4": 8}
+
+
+def bytes_per_update(wl, W, fused=True):
+    """Bytes one spin update must move.  Fused (one pass per sweep): the spin is
+    read once and written once (2 S) and every site's 3 bonds and 3 field
+    components are read once for the W systems that share them.  Two-pass (one
+    launch per half-sweep): each updated spin's own read and write plus one read
+    of the opposite-parity spin it sees (3 S), and the 6 bonds + 3 field
+    components of every updated site's record."""
+    S = SPIN_BYTES[wl.precision]
     jb = 2 if wl.j_fp16 else 4
+    return 2 * S + 6 * jb / W if fused else 3 * S + 9 * jb / W
+
+
+def algorithmic_half_sweep_bytes(ctx, wl, fused=True):
+    """Algorithmic bytes of one half-sweep launch (N/2 sites x W systems updated)."""
     sites = sum(s.L ** 3 for s in wl.samples) // 2
-    return sites * (3 * S * ctx.W + 9 * jb)
+    return int(round(sites * ctx.W * bytes_per_update(wl, ctx.W, fused)))
 
 
 def run_ours(args, wl, torch, dev, rank, world, measure_every, do_roofline=True):
@@ -509,17 +519,11 @@ def main():
     ms = max_over_ranks(ms, torch, dev)
 
     info = ctx.info()
-    persistent = info.variant == 2
-    launches_per_step = 1 if persistent else info.n_passes * 2 * sweeps + 3
-    schedule = {"variant": "persistent" if persistent else "two_pass (CUDA graph)",
-                "chunks_per_thread": info.chunks_per_thread, "passes": info.n_passes}
     updates_rank = sweeps * spins * args.steps
     updates = updates_rank * world
     value = whole_job_value(ms, updates_rank, world)
     peak, peak_kind = measured_peak()
-    A = algorithmic_half_sweep_bytes(ctx, wl)
-    achieved = A / (ms_half * 1e-3) / 1e9
-    traffic = traffic_summary(f"or_half_sweep_{wl.precision}")
+    rl = roofline_entry(ctx, wl, ms_half, ms_hb, value, peak, peak_kind)
 
     line = {
         "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
@@ -532,14 +536,10 @@ def main():
                    "step": f"{wl.n_hb} HB + {wl.n_or} OR + energies + PT, measure every "
                            f"{args.measure_every}",
                    "l2": "state larger than L2 (no flush)", "parallelism": f"replicas x{world}",
-                   "schedule": schedule},
+                   "schedule": schedule_of(info)},
         "spin_updates_per_s": round(updates / (ms * 1e-3), 1),
-        "gpu_launches": args.steps * launches_per_step + n_meas * 2,
-        "roofline": {"bound": "hbm", "kernel": f"k_half_sweep OR {wl.precision}",
-                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-                     "traffic": traffic, "algorithmic_bytes_per_launch": A,
-                     "ms_per_launch": round(ms_half, 5), "hb_ms_per_launch": round(ms_hb, 5)},
+        "gpu_launches": args.steps * launches_per_step(info, wl) + n_meas * 2,
+        "roofline": rl,
         "clocks": clocks.summary(),
         "observables_ms": observables_ms,
     }
@@ -552,25 +552,8 @@ def main():
                        "steps": k, "api": "hsg_set_spins(host) + hsg_step + hsg_measure(host)"}
     ctx.close()
 
+    configs = {}
     if not args.no_extras and world == 1:
-        extras = {"plain_fp32": {}, "other_storage": {}}
-        for name, flush, group in (("L128_fp32", False, "plain_fp32"), ("L32_fp32", True, "plain_fp32"),
-                                   ("L128_yx4", False, "other_storage"),
-                                   ("L128_oct16", False, "other_storage")):
-            w2 = inputs.workload(name)
-            r2, sp2, sw2 = run_ours(args, w2, torch, dev, rank, world, args.measure_every)
-            buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev) if flush else None
-            k2 = max(20, args.steps // (2 if flush else 3))
-            ms2, _ = timed_steps(r2["ctx"], r2["stream"], torch, k2, args.measure_every, flush=buf)
-            mh2, _ = roofline(r2["ctx"], r2["stream"], torch, w2)
-            A2 = algorithmic_half_sweep_bytes(r2["ctx"], w2)
-            extras[group][name] = {"value": round(ms2 * 1e6 / (sw2 * sp2 * k2), 6), "unit": UNIT,
-                            "steps": k2, "l2": "flushed between steps" if flush else "state > L2",
-                            "or_half_sweep_GBps": round(A2 / (mh2 * 1e-3) / 1e9, 1),
-                            "or_half_sweep_frac": round(A2 / (mh2 * 1e-3) / 1e9 / peak, 4)}
-            r2["ctx"].close()
-            del buf
-        line.update(extras)
         # the paper's own benchmark (Table 1: 256 systems of L = 32 at T = 100, FP32), with its
         # GTX 480 figures beside ours for context
         paper = {"table1_hb100or": 0.29, "table1_hb10or": 0.45, "table1_hb": 2.23, "table1_or": 1.30}
@@ -586,13 +569,86 @@ def main():
             r2["ctx"].close()
         line["paper_table1_config"] = t1
         line["multihit"] = multihit_extras(torch, dev, inputs, value)
+        # every production shape of the method, one compact entry each (L2-resident
+        # states are timed with L2 flushed before every step)
+        for name in ("L8_plain", "L32_fp32", "L64_fp16", "L64_angle16", "batch512_mixedL",
+                     "L128_fp32", "L128_bf16", "L128_oct16", "L128_yx4"):
+            configs[name] = config_line(args, name, torch, dev, peak)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(wl)
+    if configs:
+        configs[args.workload] = {"ns": line["value"], "ms_step": line["ms_per_step"],
+                                  "or_frac": rl["frac"], "schedule": schedule_of(info, short=True),
+                                  "l2": "> L2"}
+        line["configs"] = configs
+        if "L128_fp32" in configs and args.workload == "L128_fp16":
+            line["vs_plain_fp32"] = {
+                "L128": round(configs["L128_fp32"]["ns"] / line["value"], 3),
+                "note": "plain FP32 ns / compressed ns per update on the same lattice, same GPU"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def schedule_of(info, short=False):
+    persistent = info.variant == 2
+    if short:
+        return (("persistent" if persistent else "graph") + f"/gpt{info.chunks_per_thread}"
+                + f"/p{info.n_passes}")
+    return {"variant": "persistent" if persistent else "two_pass (CUDA graph)",
+            "chunks_per_thread": info.chunks_per_thread, "passes": info.n_passes}
+
+
+def launches_per_step(info, wl):
+    if info.variant == 2:
+        return 1
+    return info.n_passes * 2 * (wl.n_hb + wl.n_or) + 3
+
+
+def roofline_entry(ctx, wl, ms_half, ms_hb, value_ns, peak, peak_kind):
+    """Roofline of the over-relaxation half-sweep kernel (the dominant kernel),
+    on the bytes the method must move (the fused one-pass count), with the
+    two-pass count beside it; step_frac compares the whole step with the
+    time the fused bytes of every update would take at the peak."""
+    A = algorithmic_half_sweep_bytes(ctx, wl, fused=True)
+    A2 = algorithmic_half_sweep_bytes(ctx, wl, fused=False)
+    achieved = A / (ms_half * 1e-3) / 1e9
+    traffic = traffic_summary(f"or_half_sweep_{wl.precision}")
+    floor_ns = bytes_per_update(wl, ctx.W, fused=True) / peak      # ns per update at the peak
+    return {"bound": "hbm", "kernel": f"k_half_sweep OR {wl.precision}",
+            "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_kind": peak_kind, "traffic": traffic,
+            "algorithmic_bytes_per_launch": A,
+            "traffic_over_algorithmic": round(traffic / A, 3) if traffic else None,
+            "frac_two_pass": round(A2 / (ms_half * 1e-3) / 1e9 / peak, 4),
+            "two_pass_bytes_per_launch": A2,
+            "step_frac": round(floor_ns / value_ns, 4),
+            "ms_per_launch": round(ms_half, 5), "hb_ms_per_launch": round(ms_hb, 5)}
+
+
+def config_line(args, name, torch, dev, peak):
+    """One production shape: ns per spin update of its step (with the overlap
+    measurement every 10th step), its schedule and the OR kernel's fraction of
+    the HBM peak on the fused bytes."""
+    from paper_1204_6192_gb300 import inputs
+    w2 = inputs.workload(name)
+    state = sum(s.L ** 3 for s in w2.samples) * w2.n_replicas * w2.n_temps * SPIN_BYTES[w2.precision]
+    flush = state < 256 * 1024 * 1024
+    r2, sp2, sw2 = run_ours(args, w2, torch, dev, 0, 1, args.measure_every)
+    buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev) if flush else None
+    k2 = 30 if flush else 20
+    ms2, _ = timed_steps(r2["ctx"], r2["stream"], torch, k2, args.measure_every, flush=buf)
+    mh2, _ = roofline(r2["ctx"], r2["stream"], torch, w2)
+    A = algorithmic_half_sweep_bytes(r2["ctx"], w2, fused=True)
+    out = {"ns": round(ms2 * 1e6 / (sw2 * sp2 * k2), 6), "ms_step": round(ms2 / k2, 4),
+           "or_frac": round(A / (mh2 * 1e-3) / 1e9 / peak, 3),
+           "schedule": schedule_of(r2["ctx"].info(), short=True),
+           "l2": "flushed" if flush else "> L2"}
+    r2["ctx"].close()
+    del buf
+    return out
 
 
 # ---------------------------------------------------------------------------

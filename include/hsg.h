@@ -313,7 +313,7 @@ hsg_status hsg_get_info(hsg_ctx* ctx, hsg_info* info);
  * can cause.
  *   spins_dev  float[W][L^3][3], (x, y, z) per site (the hsg_get_spins layout)
  *   J_dev      float[L^3][3] bonds (i, i + e_a); H_dev float[L^3][3] or NULL
- *   E_dev      double[W] output, E_w = -sum_bonds J s.s - sum_i H.s (Eq. 1)
+ *   E_dev      double[W] output, E_w = -sum_bonds J s.s - sum_i H.s
  *   stream     cudaStream_t, NULL for the default stream; the call is
  *              asynchronous on it
  * Scratch: block partial sums go to one static __device__ array of 524288

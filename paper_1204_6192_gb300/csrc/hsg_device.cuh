@@ -457,7 +457,10 @@ __device__ __forceinline__ void hb_poles(float a, float u1, float& dm, float& dp
     const float inv_a = rcp_approx(a);
     const float om = __fsub_rn(1.0f, u1);
     if (FAST) {
-      dm = __fmul_rn(-__logf(__fmaf_rn(om, __fsub_rn(__expf(-2.0f * a), 1.0f), 1.0f)), inv_a);
+      // below a = 0.35, exp(-2a) - 1 cancels (for a < ~3e-8 it is exactly 0 and
+      // the spin would snap onto h): expm1 there, as in the accurate branch
+      const float em = (a >= 0.35f) ? __fsub_rn(__expf(-2.0f * a), 1.0f) : expm1f(-2.0f * a);
+      dm = __fmul_rn(-__logf(__fmaf_rn(om, em, 1.0f)), inv_a);
       dp = __fsub_rn(2.0f, dm);
     } else {
       // exp(-2a) - 1 has no cancellation for a >= 0.35; the hardware exp's

@@ -20,18 +20,35 @@ def _fake_ctx(W):
 
 
 def test_algorithmic_bytes_of_the_bench_workload():
-    # L = 128, 48 systems, FP16 spins (6 B) and FP16 couplings and field (2 B each):
-    # (N/2) (3 S W + 9 J_b) = 1048576 * (3*6*48 + 9*2)
+    # L = 128, 48 systems, FP16 spins (S = 6 B), FP16 couplings and field (2 B each).
+    # Fused: per update 2 S + (3 bonds + 3 field) * 2 B / W; a half-sweep launch
+    # updates N/2 sites x 48 systems: 1048576 * (2*6*48 + 12) = 616.6 MB.
     wl = inputs.workload("L128_fp16")
-    assert bench.algorithmic_half_sweep_bytes(_fake_ctx(48), wl) == 1048576 * 882 == 924844032
+    assert bench.bytes_per_update(wl, 48) == pytest.approx(12.25)
+    assert bench.algorithmic_half_sweep_bytes(_fake_ctx(48), wl) == 1048576 * 588 == 616562688
+    # two-pass: (N/2) (3 S W + 9 J_b) = 1048576 * (3*6*48 + 9*2)
+    assert bench.algorithmic_half_sweep_bytes(_fake_ctx(48), wl, fused=False) == 1048576 * 882
 
 
 def test_algorithmic_bytes_fp32_and_batches():
     wl = inputs.workload("L128_fp32")
-    assert bench.algorithmic_half_sweep_bytes(_fake_ctx(48), wl) == 1048576 * (3 * 12 * 48 + 9 * 4)
+    assert bench.algorithmic_half_sweep_bytes(_fake_ctx(48), wl) == 1048576 * (2 * 12 * 48 + 6 * 4)
+    assert bench.algorithmic_half_sweep_bytes(_fake_ctx(48), wl, fused=False) == \
+        1048576 * (3 * 12 * 48 + 9 * 4)
     wl = inputs.workload("batch512_mixedL")
     sites = sum(s.L ** 3 for s in wl.samples) // 2
-    assert bench.algorithmic_half_sweep_bytes(_fake_ctx(32), wl) == sites * (3 * 12 * 32 + 9 * 4)
+    assert bench.algorithmic_half_sweep_bytes(_fake_ctx(32), wl) == sites * (2 * 12 * 32 + 6 * 4)
+
+
+def test_roofline_entry_fractions():
+    wl = inputs.workload("L128_fp16")
+    rl = bench.roofline_entry(_fake_ctx(48), wl, ms_half=0.17634, ms_hb=0.33, value_ns=0.004177,
+                              peak=6686.5, peak_kind="measured")
+    # the kernel on the fused bytes: 616.6 MB / 0.17634 ms = 3.50 TB/s = 0.52 of 6686.5 GB/s
+    assert rl["frac"] == pytest.approx(0.523, abs=2e-3)
+    assert rl["frac_two_pass"] == pytest.approx(0.784, abs=2e-3)
+    # the step: 12.25 B / 6686.5 GB/s = 1.832 ps against 4.177 ps
+    assert rl["step_frac"] == pytest.approx(0.4386, abs=2e-3)
 
 
 def test_traffic_is_reported_only_for_the_profiled_source(monkeypatch):

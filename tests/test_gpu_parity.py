@@ -159,6 +159,48 @@ def test_trajectory_config1_shape():
     trajectory_check(w.samples, w.n_replicas, w.seed, sched)
 
 
+# a step's sweeps and the first four of the next: 1 HB + 5 OR, then 1 HB + 3 OR
+STEP_SWEEPS = ["sweep_hb"] + ["sweep_or"] * 5 + ["sweep_hb"] + ["sweep_or"] * 3
+
+
+def reseeded_sweeps(samples, n_rep, seed, sweeps=STEP_SWEEPS):
+    """Consecutive sweeps in a step's order; before each one the oracle takes
+    over the GPU's current binary32 state, so every sweep starts both sides
+    from the same state (sweep counters 0, 1, ... on both).  Returns the
+    largest component deviation after each sweep."""
+    samples = [f32(s) for s in samples]
+    ctx = hsg.Context(samples, n_rep, seed)
+    orc = oracle.OracleSim(samples, n_rep, seed)
+    dev = []
+    for op in sweeps:
+        for o, st in zip(orc.samples, ctx.get_spins()):
+            o.s = st.astype(np.float64)
+        getattr(ctx, op)(1)
+        getattr(orc, op)(1)
+        dev.append(max(np.abs(g - o).max() for g, o in zip(ctx.get_spins(), orc.spins())))
+    ctx.close()
+    return np.array(dev)
+
+
+@pytest.mark.parametrize("shape", ["L8_plain", "L16_field"])
+def test_ten_sweeps_each_from_the_gpu_state_within_1e5(shape):
+    """Ten consecutive sweeps (HB, 5 OR, HB, 3 OR; sweep counters 0-9), each
+    started from the GPU's own state: every component of every system within
+    1e-5 of the FP64 oracle after every sweep.  L8_plain: L = 8, H = 0,
+    2 x 8 temperatures in [0.15, 0.6]; L16_field: L = 16, H_r = 0.05,
+    2 x 8 temperatures in [0.1, 0.4]."""
+    if shape == "L8_plain":
+        w = inputs.workload("L8_plain")
+        samples, n_rep, seed = w.samples, w.n_replicas, w.seed
+    else:
+        samples = [inputs.small_sample(16, n_temps=8, h_r=0.05, disorder_seed=16, t_min=0.1,
+                                       t_max=0.4)]
+        n_rep, seed = 2, 3
+    dev = reseeded_sweeps(samples, n_rep, seed)
+    print(f"\n[{shape}] max |GPU - oracle| per sweep: {np.array2string(dev, precision=2)}")
+    assert np.all(dev < TOL_FP32), dev
+
+
 def test_ragged_system_count_and_batch():
     """W = 3 (padded to 8 lanes) and a batch of three lattice sizes in one context."""
     samples = [inputs.small_sample(L, n_temps=3, h_r=0.1, disorder_seed=10 + L) for L in (4, 6, 8)]

@@ -1,14 +1,26 @@
 """Statistical parity of equilibrium observables, GPU against the FP64 oracle.
 
-Workload: L = 8, Gaussian J, 2 replicas x 8 temperatures, 1000 steps of
-1 HB + 5 OR + PT, a measurement after every step; the second half of the
-series is averaged.  e(T) = <E>/N per temperature slot (both replicas) and
-<q^2> = <sum_{mu nu} (q^{mu nu})^2> per slot.  Errors from 10 bins.  The GPU and
-oracle chains use the same random numbers, so their difference is smaller
-than the combined error; the bound 3 sigma per slot is conservative.
+Observables per temperature slot: e(T) = <E>/N (both replicas averaged) and
+<q^2> = <sum_{mu nu} (q^{mu nu})^2> of replicas 0 and 1, measured after every
+step of 1 HB + 5 OR + PT (Sec. 4).
 
-For the compressed storage forms the same comparison states the error of
-e(T) and <q^2> against the FP64 oracle (printed; run with -s to see it).
+The GPU and the oracle start from the same state and use the same random
+numbers, so their series are correlated (identical at first, then apart once
+rounding differences have grown).  The test therefore works on the paired
+difference series d_t = O_gpu(t) - O_oracle(t): its mean over the second half
+of the run, with the standard error from NBINS consecutive bins of d, which
+holds whatever correlation the common random numbers leave.  z = mean / error
+follows Student's t with NBINS - 1 degrees of freedom when both chains sample
+the same distribution.  "Within 2 sigma" is read as a statistical test over
+all slots: no more comparisons beyond |z| = 2 than a correct chain gives at
+the 0.5% level (binomial), and none beyond the 1% Bonferroni point.
+
+Shapes: L = 8, H = 0, 2 x 8 temperatures in [0.15, 0.6], 1000 steps; and the
+L = 32 production shape (2 x 32 temperatures in [0.1, 0.4], H_r = 0.05),
+shortened to 600 steps because the FP64 oracle takes ~0.1 s per step there.
+The compressed storage forms (FP16 couplings) are held to the same criterion,
+and their mean differences against the FP64 oracle are printed as the error of
+each form (run with -s).
 """
 import numpy as np
 import pytest
@@ -18,8 +30,12 @@ from paper_1204_6192_gb300 import hsg, inputs
 
 pytestmark = pytest.mark.gpu
 
-STEPS = 1000
-NBINS = 10
+SHAPES = {
+    # name: (L, n_temps, t_min, t_max, h_r, disorder_seed, steps, bins)
+    "L8": (8, 8, 0.15, 0.6, 0.0, 1, 1000, 10),
+    "L32": (32, 32, 0.1, 0.4, 0.05, 2, 600, 10),
+}
+COMPRESSED = ["fp16", "bf16", "angle16", "oct16", "yx4"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -28,17 +44,20 @@ def _build():
     __graft_entry__.build()
 
 
-def workload(h_r=0.0, fp16_couplings=False):
-    t = inputs.geometric_temperatures(0.15, 0.6, 8)
-    smp = inputs.make_sample(8, t, h_r, disorder_seed=1)
+def workload(shape, fp16_couplings):
+    L, nt, t0, t1, h_r, seed, _, _ = SHAPES[shape]
+    if fp16_couplings and h_r == 0.0:
+        h_r = 0.1
+    t = inputs.geometric_temperatures(t0, t1, nt)
+    smp = inputs.make_sample(L, t, h_r, disorder_seed=seed)
     r = inputs.round_fp16 if fp16_couplings else (lambda a: np.asarray(a, np.float32).astype(np.float64))
-    return inputs.Sample(L=8, J=r(smp.J), H=r(smp.H), temps=t)
+    return inputs.Sample(L=L, J=r(smp.J), H=r(smp.H), temps=t)
 
 
-def series_gpu(smp, precision="fp32", j16=False, fast_math=False):
+def series_gpu(smp, steps, precision="fp32", j16=False, fast_math=False):
     ctx = hsg.Context([smp], 2, 1, precision=precision, j_fp16=j16, fast_math=fast_math)
     E, Q = [], []
-    for _ in range(STEPS):
+    for _ in range(steps):
         ctx.step(1)
         m = ctx.measure()
         E.append(m["E"][0])                                   # [R_O, R_T]
@@ -47,10 +66,10 @@ def series_gpu(smp, precision="fp32", j16=False, fast_math=False):
     return np.array(E), np.array(Q)
 
 
-def series_oracle(smp):
+def series_oracle(smp, steps):
     sim = oracle.OracleSim([smp], 2, 1)
     E, Q = [], []
-    for _ in range(STEPS):
+    for _ in range(steps):
         sim.step(1)
         m = sim.measure()[0]
         E.append(m["E"])
@@ -58,67 +77,85 @@ def series_oracle(smp):
     return np.array(E), np.array(Q)
 
 
-def mean_err(x):
+def per_slot(E, Q, N):
+    """e(T) per step and slot (replica average) and q^2 per step and slot."""
+    return E.mean(axis=1) / N, Q
+
+
+def binned(x, nbins):
+    """Mean over the second half and its standard error from nbins bins."""
     x = x[len(x) // 2:]
-    bins = np.array([b.mean(axis=0) for b in np.array_split(x, NBINS)])
-    return x.mean(axis=0), bins.std(axis=0, ddof=1) / np.sqrt(NBINS)
+    bins = np.array([b.mean(axis=0) for b in np.array_split(x, nbins)])
+    return x.mean(axis=0), bins.std(axis=0, ddof=1) / np.sqrt(nbins)
 
 
-def observables(E, Q, N):
-    e_m, e_s = mean_err(E.mean(axis=1) / N)     # replica-averaged energy per spin
-    q_m, q_s = mean_err(Q)
-    return e_m, e_s, q_m, q_s
+def paired_z(gpu, orc, nbins):
+    """Mean paired difference, its error and z, for e(T) and q^2 per slot."""
+    out = {}
+    for k, name in enumerate(("e", "q2")):
+        m, s = binned(gpu[k] - orc[k], nbins)
+        out[name] = (m, s, m / np.maximum(s, 1e-300))
+    return out
 
 
-@pytest.fixture(scope="module")
-def oracle_fp32_couplings():
-    smp = workload()
-    return smp, observables(*series_oracle(smp), N=512)
+def check(res, nbins, label):
+    from scipy import stats
+    z = np.concatenate([res["e"][2], res["q2"][2]])
+    n = z.size
+    dof = nbins - 1
+    p2 = 2.0 * stats.t.sf(2.0, dof)                  # chance of |z| > 2 for a correct chain
+    k_max = int(stats.binom.ppf(0.995, n, p2))
+    z_max = stats.t.isf(0.005 / n, dof)              # 1% two-sided, Bonferroni over n
+    beyond = int(np.sum(np.abs(z) > 2.0))
+    for name in ("e", "q2"):
+        m, s, zz = res[name]
+        print(f"\n[{label}] {name}: GPU - oracle per slot {np.array2string(m, precision=6)}"
+              f"\n[{label}] {name}:   error            {np.array2string(s, precision=6)}"
+              f"\n[{label}] {name}:   z                {np.array2string(zz, precision=2)}")
+    print(f"[{label}] max |d e| {np.abs(res['e'][0]).max():.3g} (error {res['e'][1].max():.3g}), "
+          f"max |d q2| {np.abs(res['q2'][0]).max():.3g} (error {res['q2'][1].max():.3g}), "
+          f"max |z| {np.abs(z).max():.2f}, beyond 2: {beyond} of {n} (allowed {k_max})")
+    assert np.all(np.abs(z) <= z_max), (label, np.abs(z).max(), z_max)
+    assert beyond <= k_max, (label, beyond, k_max)
 
 
-@pytest.fixture(scope="module")
-def oracle_fp16_couplings():
-    smp = workload(h_r=0.1, fp16_couplings=True)
-    return smp, observables(*series_oracle(smp), N=512)
+_cache = {}
 
 
-def compare(a, b, label, limit):
-    e_g, es_g, q_g, qs_g = a
-    e_o, es_o, q_o, qs_o = b
-    ze = (e_g - e_o) / np.sqrt(es_g ** 2 + es_o ** 2 + 1e-30)
-    zq = (q_g - q_o) / np.sqrt(qs_g ** 2 + qs_o ** 2 + 1e-30)
-    print(f"\n[{label}] e(T) GPU - oracle: {np.array2string(e_g - e_o, precision=5)}"
-          f"\n[{label}]   in sigma:        {np.array2string(ze, precision=2)}"
-          f"\n[{label}] <q^2> GPU - oracle: {np.array2string(q_g - q_o, precision=5)}"
-          f"\n[{label}]   in sigma:        {np.array2string(zq, precision=2)}")
-    assert np.all(np.abs(ze) <= limit), ze
-    assert np.all(np.abs(zq) <= limit), zq
-    return ze, zq
+def oracle_reference(shape, fp16_couplings):
+    key = (shape, fp16_couplings)
+    if key not in _cache:
+        smp = workload(shape, fp16_couplings)
+        steps = SHAPES[shape][6]
+        _cache[key] = (smp, per_slot(*series_oracle(smp, steps), N=smp.L ** 3))
+    return _cache[key]
 
 
-def test_equilibrium_observables_fp32(oracle_fp32_couplings):
-    """FP32 against the FP64 oracle: every slot within 3 sigma, and at most 3 of
-    the 16 comparisons (8 slots, e and <q^2>) beyond 2 sigma; for agreeing
-    estimates each one exceeds 2 sigma with probability 0.046, so 4 or more do so
-    with probability 0.006."""
-    smp, ref = oracle_fp32_couplings
-    gpu = observables(*series_gpu(smp), N=512)
-    ze, zq = compare(gpu, ref, "fp32", 3.0)
-    assert np.sum(np.abs(ze) > 2.0) + np.sum(np.abs(zq) > 2.0) <= 3, (ze, zq)
+@pytest.mark.parametrize("shape", ["L8", "L32"])
+def test_equilibrium_observables_fp32(shape):
+    """FP32 spins and couplings against the FP64 oracle, e(T) and <q^2> per slot."""
+    smp, ref = oracle_reference(shape, False)
+    steps, nbins = SHAPES[shape][6], SHAPES[shape][7]
+    gpu = per_slot(*series_gpu(smp, steps), N=smp.L ** 3)
+    check(paired_z(gpu, ref, nbins), nbins, f"{shape} fp32")
 
 
-@pytest.mark.parametrize("precision", ["fp16", "bf16", "angle16", "oct16", "yx4"])
-def test_compressed_storage_error_against_fp64(oracle_fp16_couplings, precision):
-    """Compressed spins with FP16 couplings against the FP64 oracle (no storage
-    rounding): the storage error stays within the statistical error."""
-    smp, ref = oracle_fp16_couplings
-    gpu = observables(*series_gpu(smp, precision=precision, j16=True), N=512)
-    compare(gpu, ref, precision, 4.0)
+@pytest.mark.parametrize("shape", ["L8", "L32"])
+@pytest.mark.parametrize("precision", COMPRESSED)
+def test_compressed_storage_against_fp64(shape, precision):
+    """Compressed spins with FP16 couplings against the FP64 oracle on the same
+    FP16-rounded couplings (no storage rounding in the oracle): the printed mean
+    differences are each form's error, held to the same criterion as FP32."""
+    smp, ref = oracle_reference(shape, True)
+    steps, nbins = SHAPES[shape][6], SHAPES[shape][7]
+    gpu = per_slot(*series_gpu(smp, steps, precision=precision, j16=True), N=smp.L ** 3)
+    check(paired_z(gpu, ref, nbins), nbins, f"{shape} {precision}")
 
 
-def test_fast_math_heat_bath_statistics(oracle_fp32_couplings):
+def test_fast_math_heat_bath_statistics():
     """The hardware-approximation heat bath (the paper's fast_math variant,
-    Table 1) samples the same equilibrium within the statistical error."""
-    smp, ref = oracle_fp32_couplings
-    gpu = observables(*series_gpu(smp, fast_math=True), N=512)
-    compare(gpu, ref, "fast_math", 4.0)
+    Table 1) samples the same equilibrium."""
+    smp, ref = oracle_reference("L8", False)
+    steps, nbins = SHAPES["L8"][6], SHAPES["L8"][7]
+    gpu = per_slot(*series_gpu(smp, steps, fast_math=True), N=smp.L ** 3)
+    check(paired_z(gpu, ref, nbins), nbins, "L8 fast_math")
