@@ -230,24 +230,31 @@ def timed_steps(ctx, stream, torch, steps, measure_every, flush=None):
 
 
 def roofline(ctx, stream, torch, wl, reps=20):
-    """Average duration of the over-relaxation half-sweep kernel (the dominant
-    kernel: 10 of the 15 launches of a step), timed with CUDA events on its
-    stream: `reps` OR sweeps = 2 * reps half-sweep launches (+1 counter bump)."""
+    """Average kernel durations with CUDA events on the context's stream:
+    the over-relaxation sweep as the step runs it (fused: `reps` launches of one
+    sweep each; otherwise 2 * `reps` half-sweep launches), the over-relaxation
+    half-sweep kernel on its own (sweep_or(1) runs it in every schedule) and the
+    heat-bath half-sweep.  Returns (ms per OR launch, fused?, ms per OR
+    half-sweep launch, ms per HB half-sweep launch)."""
+    fused = ctx.info().sweep_kernel == 2
+
+    def timed(fn):
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        fn()
+        t1.record(stream)
+        t1.synchronize()
+        return t0.elapsed_time(t1)
+
     ctx.sweep_or(2)
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    ctx.sweep_or(reps)
-    t1.record(stream)
-    t1.synchronize()
-    ms_half = t0.elapsed_time(t1) / (2 * reps)
-    # heat-bath half-sweep for the record
-    t0.record(stream)
-    ctx.sweep_hb(reps // 4 or 1)
-    t1.record(stream)
-    t1.synchronize()
-    ms_hb = t0.elapsed_time(t1) / (2 * (reps // 4 or 1))
-    return ms_half, ms_hb
+    ms_or = timed(lambda: ctx.sweep_or(reps)) / (reps if fused else 2 * reps)
+    ms_half = ms_or
+    if fused:
+        ms_half = timed(lambda: [ctx.sweep_or(1) for _ in range(reps // 2)]) / (2 * (reps // 2))
+    k = reps // 4 or 1
+    ms_hb = timed(lambda: ctx.sweep_hb(k)) / (2 * k)
+    return ms_or, fused, ms_half, ms_hb
 
 
 def multihit_extras(torch, dev, inputs, lattice_ns):
@@ -513,7 +520,7 @@ def main():
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    ms_half, ms_hb = roofline(ctx, stream, torch, wl)
+    rl_times = roofline(ctx, stream, torch, wl)
     clocks.stop()
     observables_ms = time_observables(ctx)
     ms = max_over_ranks(ms, torch, dev)
@@ -523,7 +530,7 @@ def main():
     updates = updates_rank * world
     value = whole_job_value(ms, updates_rank, world)
     peak, peak_kind = measured_peak()
-    rl = roofline_entry(ctx, wl, ms_half, ms_hb, value, peak, peak_kind)
+    rl = roofline_entry(ctx, wl, rl_times, value, peak, peak_kind)
 
     line = {
         "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
@@ -594,38 +601,53 @@ def main():
 
 def schedule_of(info, short=False):
     persistent = info.variant == 2
+    fused = info.sweep_kernel == 2
     if short:
         return (("persistent" if persistent else "graph") + f"/gpt{info.chunks_per_thread}"
-                + f"/p{info.n_passes}")
-    return {"variant": "persistent" if persistent else "two_pass (CUDA graph)",
-            "chunks_per_thread": info.chunks_per_thread, "passes": info.n_passes}
+                + f"/p{info.n_passes}" + ("/fused" if fused else ""))
+    out = {"variant": "persistent" if persistent else "two_pass (CUDA graph)",
+           "chunks_per_thread": info.chunks_per_thread, "passes": info.n_passes,
+           "or_sweep": "fused (one launch per sweep)" if fused else "one launch per half-sweep"}
+    if fused:
+        out.update({"fused_band_rows": info.fused_band_rows, "fused_items": info.fused_items})
+    return out
 
 
 def launches_per_step(info, wl):
     if info.variant == 2:
         return 1
+    if info.sweep_kernel == 2 and info.n_passes == 1:
+        pairs = (wl.n_or - 1) // 2
+        return 2 * wl.n_hb + 2 * pairs + 2 * (wl.n_or - 2 * pairs) + 3
     return info.n_passes * 2 * (wl.n_hb + wl.n_or) + 3
 
 
-def roofline_entry(ctx, wl, ms_half, ms_hb, value_ns, peak, peak_kind):
-    """Roofline of the over-relaxation half-sweep kernel (the dominant kernel),
-    on the bytes the method must move (the fused one-pass count), with the
-    two-pass count beside it; step_frac compares the whole step with the
-    time the fused bytes of every update would take at the peak."""
-    A = algorithmic_half_sweep_bytes(ctx, wl, fused=True)
+def roofline_entry(ctx, wl, rl, value_ns, peak, peak_kind):
+    """Roofline of the dominant kernel, the over-relaxation sweep, on the bytes
+    the method must move (the fused one-pass count: each spin read and written
+    once per sweep).  With the fused kernel one launch is a whole sweep; the
+    half-sweep kernel is reported beside it, also against the two-pass byte
+    count.  step_frac compares the whole step with the time the fused bytes of
+    every update would take at the peak."""
+    ms_or, fused, ms_half, ms_hb = rl
+    A_half = algorithmic_half_sweep_bytes(ctx, wl, fused=True)
     A2 = algorithmic_half_sweep_bytes(ctx, wl, fused=False)
-    achieved = A / (ms_half * 1e-3) / 1e9
-    traffic = traffic_summary(f"or_half_sweep_{wl.precision}")
+    A = 2 * A_half if fused else A_half
+    achieved = A / (ms_or * 1e-3) / 1e9
+    traffic = traffic_summary(f"{'fused_sweep' if fused else 'or_half_sweep'}_{wl.precision}")
     floor_ns = bytes_per_update(wl, ctx.W, fused=True) / peak      # ns per update at the peak
-    return {"bound": "hbm", "kernel": f"k_half_sweep OR {wl.precision}",
+    return {"bound": "hbm",
+            "kernel": f"{'k_fused_or (one sweep)' if fused else 'k_half_sweep OR'} {wl.precision}",
             "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "peak_kind": peak_kind, "traffic": traffic,
             "algorithmic_bytes_per_launch": A,
             "traffic_over_algorithmic": round(traffic / A, 3) if traffic else None,
-            "frac_two_pass": round(A2 / (ms_half * 1e-3) / 1e9 / peak, 4),
-            "two_pass_bytes_per_launch": A2,
+            "ms_per_launch": round(ms_or, 5),
             "step_frac": round(floor_ns / value_ns, 4),
-            "ms_per_launch": round(ms_half, 5), "hb_ms_per_launch": round(ms_hb, 5)}
+            "half_sweep": {"ms_per_launch": round(ms_half, 5),
+                           "frac": round(A_half / (ms_half * 1e-3) / 1e9 / peak, 4),
+                           "frac_two_pass": round(A2 / (ms_half * 1e-3) / 1e9 / peak, 4)},
+            "hb_ms_per_launch": round(ms_hb, 5)}
 
 
 def config_line(args, name, torch, dev, peak):
@@ -640,10 +662,10 @@ def config_line(args, name, torch, dev, peak):
     buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev) if flush else None
     k2 = 30 if flush else 20
     ms2, _ = timed_steps(r2["ctx"], r2["stream"], torch, k2, args.measure_every, flush=buf)
-    mh2, _ = roofline(r2["ctx"], r2["stream"], torch, w2)
-    A = algorithmic_half_sweep_bytes(r2["ctx"], w2, fused=True)
+    ms_or, fused, _, _ = roofline(r2["ctx"], r2["stream"], torch, w2)
+    A = algorithmic_half_sweep_bytes(r2["ctx"], w2, fused=True) * (2 if fused else 1)
     out = {"ns": round(ms2 * 1e6 / (sw2 * sp2 * k2), 6), "ms_step": round(ms2 / k2, 4),
-           "or_frac": round(A / (mh2 * 1e-3) / 1e9 / peak, 3),
+           "or_frac": round(A / (ms_or * 1e-3) / 1e9 / peak, 3),
            "schedule": schedule_of(r2["ctx"].info(), short=True),
            "l2": "flushed" if flush else "> L2"}
     r2["ctx"].close()

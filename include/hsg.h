@@ -107,7 +107,23 @@ typedef struct {
   int chunks_per_thread;    /* sweep kernels: chunks of 4 systems one thread walks; 0
                                (default): chosen from the problem size (and by the
                                automatic schedule).  Results do not depend on it. */
+  int sweep_kernel;         /* over-relaxation sweeps of hsg_step and hsg_sweep_or: an
+                               HSG_SWEEP_* value.  HSG_SWEEP_FUSED does both half-sweeps of
+                               a sweep in one launch (a wavefront along z through shared
+                               memory), pairs of sweeps at a time, reading the spins once
+                               and writing them once per sweep; it needs a second spin
+                               buffer of spin_bytes, every L a multiple of 4 and a storage
+                               format other than HSG_YX4, and is used with the two-pass
+                               schedule in one pass (elsewhere the per-half-sweep kernel
+                               runs).  0 (default): chosen by the automatic schedule.
+                               Results do not depend on it (bit for bit). */
 } hsg_options;
+
+enum {
+  HSG_SWEEP_AUTO = 0,
+  HSG_SWEEP_HALF = 1,         /* one launch per half-sweep */
+  HSG_SWEEP_FUSED = 2         /* one launch per sweep (pairs of OR sweeps) */
+};
 
 enum {
   HSG_VARIANT_AUTO = 0,
@@ -300,6 +316,9 @@ typedef struct {
   int n_passes;            /* system-blocked passes per step (1: no blocking) */
   long long pass_bytes;    /* footprint bound of a pass in use (0: one pass) */
   int n_overlap_pairs;     /* replica pairs hsg_measure_overlaps reports (0 if n_replicas < 2) */
+  int sweep_kernel;        /* HSG_SWEEP_HALF or HSG_SWEEP_FUSED: the over-relaxation sweep in use */
+  int fused_band_rows;     /* fused sweep: rows of y per block of sample 0 (L: whole planes) */
+  int fused_items;         /* fused sweep: work items (columns of planes) per launch */
 } hsg_info;
 hsg_status hsg_get_info(hsg_ctx* ctx, hsg_info* info);
 

@@ -87,7 +87,7 @@ struct hsg_ctx {
   int variant = HSG_VARIANT_TWO_PASS;   // resolved step schedule
   bool tune_pending = false;            // automatic schedule not yet tuned
   long long max_sweep_blocks = 0;       // sweep table capacity (one chunk per thread)
-  unsigned int* d_bar = nullptr;        // grid barrier: arrivals, generation, error word; [3] measurement error word
+  unsigned int* d_bar = nullptr;        // grid barrier: arrivals, generation, error word; [3] measurement error word; [4] fused sweep error word
   int persist_grid = 0;
   size_t persist_smem = 0;
   bool inject_fault = false;
@@ -98,6 +98,18 @@ struct hsg_ctx {
   // first, built at first use for tile edges 4 and 8
   int4* d_mh_blocks[2] = {nullptr, nullptr};
   int mh_count[2][2] = {{0, 0}, {0, 0}};
+
+  // fused over-relaxation sweep: a second spin buffer (each fused sweep reads
+  // one buffer and writes the other; sweeps run in pairs, so the state is back
+  // in `spins` after every call), the work items and the launch shape
+  bool fused_possible = false;          // format and lattice sizes allow it
+  bool use_fused = false;               // resolved choice of the schedule
+  unsigned char* spins2 = nullptr;
+  int4* d_fused_items = nullptr;
+  int n_fused_items = 0, fused_grid = 0;
+  size_t fused_smem = 0;
+  uint32_t fused_slot1 = 0, fused_slot0 = 0;
+  std::vector<int> fused_ny;            // band rows per sample
 
   std::vector<int> pass_bound{0, 0};    // [n_passes + 1] block table bounds
   int* d_pass_bound = nullptr;
@@ -283,6 +295,122 @@ hsg_status enqueue_energy(hsg_ctx* c) {
   return HSG_OK;
 }
 
+// Plan of the fused over-relaxation sweep (at first use): per sample the rows
+// of y a block holds (the whole plane where it fits, else the largest divisor
+// of L that fits, with the band's halo rows), the shared-memory slots, the
+// second spin buffer and the work items.  Columns (sample, band, chunk group;
+// chunk groups adjacent, so blocks that run together share couplings and halo
+// rows in L2) fill whole rounds of the grid over all planes; the columns left
+// over are cut into z segments so that the last round also fills the grid.
+// Leaves use_fused possible only if everything fits.
+hsg_status plan_fused(hsg_ctx* c) {
+  if (!c->fused_possible || c->d_fused_items) return HSG_OK;
+  const int CH = c->VEC * c->ELEM, PL = c->PL;
+  int optin = 0, n_sm = 0;
+  HSG_CUDA(c, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+  HSG_CUDA(c, cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, c->device));
+  const long long budget = (long long)optin - FUSED_SMEM_HEAD;
+  long long slot1 = 0, slot0 = 0;
+  std::vector<int> ny(c->ns, 0);
+  for (int s = 0; s < c->ns; ++s) {
+    const int L = c->L[s], Lh = L / 2;
+    auto fits = [&](int rows1, int rows0) {
+      const long long a = std::max(slot1, (long long)PL * rows1 * Lh * CH);
+      const long long b = std::max(slot0, (long long)PL * rows0 * Lh * CH);
+      return FUSED_ODD_SLOTS * a + FUSED_EVEN_SLOTS * b <= budget;
+    };
+    int best = 0;
+    if ((long long)L * Lh <= FUSED_MAX_SITES && fits(L, L)) {
+      best = L;
+    } else {
+      for (int n = L - 4; n >= 4; --n)
+        if (L % n == 0 && (long long)(n + 2) * Lh <= FUSED_MAX_SITES && fits(n + 4, n + 2)) {
+          best = n;
+          break;
+        }
+    }
+    if (!best) {
+      c->fused_possible = false;
+      return HSG_OK;
+    }
+    ny[s] = best;
+    const int r1 = best == L ? L : best + 4, r0 = best == L ? L : best + 2;
+    slot1 = std::max(slot1, (long long)PL * r1 * Lh * CH);
+    slot0 = std::max(slot0, (long long)PL * r0 * Lh * CH);
+  }
+  const size_t smem = FUSED_SMEM_HEAD + FUSED_ODD_SLOTS * slot1 + FUSED_EVEN_SLOTS * slot0;
+  int per_sm = 0;
+  HSG_CUDA(c, prepare_fused(c->fmt, c->j16, smem, &per_sm));
+  if (per_sm < 1) {
+    c->fused_possible = false;
+    return HSG_OK;
+  }
+  const int P = n_sm * per_sm;
+  // columns: (sample, chunk group, y0 | ny << 16, L)
+  std::vector<int4> cols;
+  for (int s = 0; s < c->ns; ++s)
+    for (int y0 = 0; y0 < c->L[s]; y0 += ny[s])
+      for (int g = 0; g < c->G; ++g) cols.push_back(make_int4(s, g, y0 | (ny[s] << 16), c->L[s]));
+  const int C = (int)cols.size();
+  const int full = (C / P) * P, rem = C - full;
+  std::vector<int4> items;
+  for (int i = 0; i < full; ++i) items.push_back(make_int4(cols[i].x, cols[i].y, cols[i].z, cols[i].w << 16));
+  if (rem) {
+    int S = std::max(1, P / rem);
+    for (int i = full; i < C; ++i) S = std::min(S, std::max(1, cols[i].w / 4));
+    for (int k = 0; k < S; ++k)
+      for (int i = full; i < C; ++i) {
+        const int L = cols[i].w, za = k * L / S, zb = (k + 1) * L / S;
+        items.push_back(make_int4(cols[i].x, cols[i].y, cols[i].z, za | (zb << 16)));
+      }
+  }
+  HSG_TRY(dev_alloc(c, &c->spins2, c->spin_bytes));
+  HSG_TRY(dev_alloc(c, &c->d_fused_items, sizeof(int4) * items.size()));
+  HSG_CUDA(c, cudaMemcpy(c->d_fused_items, items.data(), sizeof(int4) * items.size(),
+                         cudaMemcpyHostToDevice));
+  c->n_fused_items = (int)items.size();
+  c->fused_grid = std::min(P, c->n_fused_items);
+  c->fused_smem = smem;
+  c->fused_slot1 = (uint32_t)slot1;
+  c->fused_slot0 = (uint32_t)slot0;
+  c->fused_ny = ny;
+  return HSG_OK;
+}
+
+// `pairs` pairs of fused over-relaxation sweeps: spins -> spins2 -> spins.
+hsg_status fused_sweep_pairs(hsg_ctx* c, int pairs) {
+  FusedParams p;
+  p.rec = c->rec;
+  p.samples = c->d_sd;
+  p.items = c->d_fused_items;
+  p.active = c->d_active;
+  p.n_items = c->n_fused_items;
+  p.slot1 = c->fused_slot1;
+  p.slot0 = c->fused_slot0;
+  p.err = c->d_bar + 4;
+  p.timeout_ns = (unsigned long long)std::max(1, c->opt.barrier_timeout_ms) * 1000000ull;
+  for (int k = 0; k < pairs; ++k) {
+    p.src = c->spins;
+    p.dst = c->spins2;
+    HSG_CUDA(c, launch_fused(c->fmt, c->j16, p, c->fused_grid, c->fused_smem, c->stream));
+    p.src = c->spins2;
+    p.dst = c->spins;
+    HSG_CUDA(c, launch_fused(c->fmt, c->j16, p, c->fused_grid, c->fused_smem, c->stream));
+  }
+  return HSG_OK;
+}
+
+// n OR sweeps outside a step: fused pairs where in use, the rest per half-sweep.
+hsg_status or_sweeps(hsg_ctx* c, int n, int sweep_offset) {
+  int k = 0;
+  if (c->use_fused && n >= 2) {
+    HSG_TRY(fused_sweep_pairs(c, n / 2));
+    k = 2 * (n / 2);
+  }
+  for (; k < n; ++k) HSG_TRY(half_sweeps(c, false, sweep_offset + k));
+  return HSG_OK;
+}
+
 // A step: n_hb HB sweeps, n_or OR sweeps (the last one also produces the
 // energy partials of the final state), the energy sums and one PT pass.  The
 // sweeps run pass by pass; systems are independent and every random number is
@@ -293,7 +421,15 @@ hsg_status enqueue_step(hsg_ctx* c) {
   for (int ps = 0; ps < np; ++ps) {
     const int b0 = c->pass_bound[ps], b1 = c->pass_bound[ps + 1];
     for (int k = 0; k < nhb; ++k) HSG_TRY(half_sweeps(c, true, k, false, b0, b1));
-    for (int k = 0; k < nor; ++k) HSG_TRY(half_sweeps(c, false, nhb + k, k == nor - 1, b0, b1));
+    int k = 0;
+    if (c->use_fused && np == 1) {
+      // pairs of fused sweeps, leaving the last sweep (which also sums the
+      // energies) to the per-half-sweep kernel
+      const int pairs = (nor - 1) / 2;
+      HSG_TRY(fused_sweep_pairs(c, pairs));
+      k = 2 * pairs;
+    }
+    for (; k < nor; ++k) HSG_TRY(half_sweeps(c, false, nhb + k, k == nor - 1, b0, b1));
   }
   if (nor > 0) {
     HSG_CUDA(c, launch_energy_final(energy_params(c), c->stream));
@@ -307,10 +443,11 @@ hsg_status enqueue_step(hsg_ctx* c) {
 // A bounded device wait that ran out (persistent schedule, staged measurement)
 // after the stream has been synchronised.
 hsg_status poll_device_error(hsg_ctx* c) {
-  unsigned int err[2] = {0u, 0u};
+  unsigned int err[3] = {0u, 0u, 0u};
   HSG_CUDA(c, cudaMemcpy(err, c->d_bar + 2, sizeof(err), cudaMemcpyDeviceToHost));
   if (err[0]) return fail(c, HSG_ETIMEOUT, "a grid barrier wait of the persistent step kernel timed out");
   if (err[1]) return fail(c, HSG_ETIMEOUT, "a wait for a staged spin copy of a measurement kernel timed out");
+  if (err[2]) return fail(c, HSG_ETIMEOUT, "a wait for a staged plane copy of the fused sweep kernel timed out");
   return HSG_OK;
 }
 
@@ -360,7 +497,7 @@ int default_gpt(hsg_ctx*, const int* L, int n_samples, int G) {
 // samples) stays within `pass_bytes` (0: one pass; a pass holds at least one
 // chunk group), and set up the chosen step schedule (drops a captured graph:
 // its parameters change).
-hsg_status configure_schedule(hsg_ctx* c, int variant, int gpt, long long pass_bytes) {
+hsg_status configure_schedule(hsg_ctx* c, int variant, int gpt, long long pass_bytes, bool fused) {
   gpt = std::max(1, std::min(c->G, gpt));
   const int n_gg = (c->G + gpt - 1) / gpt;
   const long long site_chunk_bytes = (long long)c->PL * c->VEC * c->ELEM;
@@ -414,6 +551,12 @@ hsg_status configure_schedule(hsg_ctx* c, int variant, int gpt, long long pass_b
     c->graph = nullptr;
   }
   c->variant = variant;
+  // the fused over-relaxation sweep serves the two-pass schedule in one pass
+  c->use_fused = false;
+  if (fused && variant == HSG_VARIANT_TWO_PASS && bounds.size() == 2) {
+    HSG_TRY(plan_fused(c));
+    c->use_fused = c->fused_possible;
+  }
   if (variant == HSG_VARIANT_PERSISTENT) {
     c->persist_smem = sizeof(float) * (SWEEP_BS / 32) * c->GPT * c->VEC;
     int max_grid = 0;
@@ -488,15 +631,19 @@ hsg_status copy_chain_state(hsg_ctx* c, unsigned char* host, bool to_host) {
   return HSG_OK;
 }
 
-// Autotuner: the schedules and chunks-per-thread settings compute identical
-// results, so they are timed on the live context (2 steps each, after a warm-up
-// step) and the fastest is kept; the state is saved before and restored after,
-// so the Markov chain is untouched.  Results are cached per problem shape for
-// the life of the process.
+// Autotuner: the schedules, sweep kernels and chunks-per-thread settings
+// compute identical results, so they are timed on the live context and the
+// fastest is kept; the state is saved before and restored after, so the
+// Markov chain is untouched.  Each candidate runs one warm-up step, then
+// TUNE_REPS timings of 2 steps each; the median decides (a single timing let
+// noise pick between close candidates).  Results are cached per problem shape
+// for the life of the process.
 struct TuneChoice {
   int variant, gpt;
   long long pass_bytes;
+  bool fused;
 };
+constexpr int TUNE_REPS = 5;
 std::mutex g_tune_mu;
 std::map<std::string, TuneChoice> g_tune_cache;
 
@@ -505,7 +652,8 @@ std::string tune_key(hsg_ctx* c) {
                   std::to_string(c->opt.fast_math) + "/" + std::to_string(c->W) + "/" +
                   std::to_string(c->opt.n_hb_per_step) + "/" + std::to_string(c->opt.n_or_per_step) +
                   "/" + std::to_string(c->opt.pass_bytes) + "/" +
-                  std::to_string(c->opt.chunks_per_thread) + "/L";
+                  std::to_string(c->opt.chunks_per_thread) + "/" +
+                  std::to_string(c->opt.sweep_kernel) + "/L";
   for (int L : c->L) k += std::to_string(L) + ",";
   return k;
 }
@@ -517,7 +665,8 @@ hsg_status autotune(hsg_ctx* c) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end())
-      return configure_schedule(c, it->second.variant, it->second.gpt, it->second.pass_bytes);
+      return configure_schedule(c, it->second.variant, it->second.gpt, it->second.pass_bytes,
+                                it->second.fused);
   }
   // save the state the trial steps will change
   void* spins_copy = nullptr;
@@ -533,6 +682,11 @@ hsg_status autotune(hsg_ctx* c) {
   for (int g : {c->G, (c->G + 1) / 2, (c->G + 3) / 4, 2, 1, c->GPT})
     if (g >= 1 && g <= c->G && std::find(gpts.begin(), gpts.end(), g) == gpts.end()) gpts.push_back(g);
   if (c->opt.chunks_per_thread > 0) gpts.assign(1, c->GPT);
+  std::vector<bool> fused_opts;
+  if (c->opt.sweep_kernel != HSG_SWEEP_FUSED) fused_opts.push_back(false);
+  if (c->opt.sweep_kernel != HSG_SWEEP_HALF && c->fused_possible && c->opt.n_or_per_step >= 3)
+    fused_opts.push_back(true);
+  if (fused_opts.empty()) fused_opts.push_back(false);
   cudaEvent_t e0, e1;
   HSG_CUDA(c, cudaEventCreate(&e0));
   HSG_CUDA(c, cudaEventCreate(&e1));
@@ -551,22 +705,31 @@ hsg_status autotune(hsg_ctx* c) {
     }
   }
   float best = 1e30f;
-  TuneChoice bestc{HSG_VARIANT_TWO_PASS, c->GPT, budgets[0]};
+  TuneChoice bestc{HSG_VARIANT_TWO_PASS, c->GPT, budgets[0], fused_opts[0]};
   for (long long pb : budgets) {
     for (int v : {HSG_VARIANT_TWO_PASS, HSG_VARIANT_PERSISTENT}) {
-      for (int g : gpts) {
-        HSG_TRY(configure_schedule(c, v, g, pb));
-        HSG_TRY(run_steps(c, 1));
-        HSG_CUDA(c, cudaEventRecord(e0, st));
-        HSG_TRY(run_steps(c, 2));
-        HSG_CUDA(c, cudaEventRecord(e1, st));
-        HSG_CUDA(c, cudaEventSynchronize(e1));
-        HSG_TRY(poll_device_error(c));
-        float ms = 0.0f;
-        HSG_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
-          best = ms;
-          bestc = TuneChoice{v, g, pb};
+      for (bool fu : fused_opts) {
+        // the fused sweep runs in the two-pass schedule with one pass only
+        if (fu && (v != HSG_VARIANT_TWO_PASS || pb != 0)) continue;
+        for (int g : gpts) {
+          HSG_TRY(configure_schedule(c, v, g, pb, fu));
+          if (fu && !c->use_fused) continue;
+          HSG_TRY(run_steps(c, 1));
+          float t[TUNE_REPS];
+          for (int r = 0; r < TUNE_REPS; ++r) {
+            HSG_CUDA(c, cudaEventRecord(e0, st));
+            HSG_TRY(run_steps(c, 2));
+            HSG_CUDA(c, cudaEventRecord(e1, st));
+            HSG_CUDA(c, cudaEventSynchronize(e1));
+            HSG_CUDA(c, cudaEventElapsedTime(&t[r], e0, e1));
+          }
+          HSG_TRY(poll_device_error(c));
+          std::sort(t, t + TUNE_REPS);
+          const float ms = t[TUNE_REPS / 2];
+          if (ms < best) {
+            best = ms;
+            bestc = TuneChoice{v, g, pb, fu};
+          }
         }
       }
     }
@@ -583,7 +746,7 @@ hsg_status autotune(hsg_ctx* c) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune_cache[key] = bestc;
   }
-  return configure_schedule(c, bestc.variant, bestc.gpt, bestc.pass_bytes);
+  return configure_schedule(c, bestc.variant, bestc.gpt, bestc.pass_bytes, bestc.fused);
 }
 
 hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double* temps,
@@ -607,6 +770,8 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   if (opt.variant < HSG_VARIANT_AUTO || opt.variant > HSG_VARIANT_PERSISTENT)
     return bad_arg(nullptr, "unknown variant");
   if (opt.chunks_per_thread < 0) return bad_arg(nullptr, "chunks_per_thread < 0");
+  if (opt.sweep_kernel < HSG_SWEEP_AUTO || opt.sweep_kernel > HSG_SWEEP_FUSED)
+    return bad_arg(nullptr, "unknown sweep_kernel");
   const int W = n_temps * n_replicas;
   if (W > 1024) return bad_arg(nullptr, "n_temps * n_replicas must be <= 1024");
   const int Wp = (W + 7) / 8 * 8;
@@ -769,7 +934,7 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   HSG_ALLOC(c->d_acc, sizeof(unsigned long long) * n_samples * n_replicas * std::max(1, n_temps - 1));
   HSG_ALLOC(c->d_counters, sizeof(unsigned long long) * 2 * n_samples);
   HSG_ALLOC(c->d_active, sizeof(unsigned char) * n_samples);
-  HSG_ALLOC(c->d_bar, sizeof(unsigned int) * 4);
+  HSG_ALLOC(c->d_bar, sizeof(unsigned int) * 5);
   HSG_ALLOC(c->d_moved, sizeof(unsigned long long) * n_samples * n_replicas * n_temps);
   HSG_ALLOC(c->d_tstate, sizeof(unsigned char) * n_samples * n_replicas * n_temps);
   HSG_ALLOC(c->d_tunnel, sizeof(unsigned int) * n_samples * n_replicas * n_temps);
@@ -830,7 +995,7 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   if (e == cudaSuccess) e = cudaMemset(c->d_moved, 0, sizeof(unsigned long long) * perm.size());
   if (e == cudaSuccess) e = cudaMemset(c->d_tunnel, 0, sizeof(unsigned int) * perm.size());
   if (e == cudaSuccess) e = cudaMemset(c->d_E, 0, sizeof(double) * n_samples * Wp);
-  if (e == cudaSuccess) e = cudaMemset(c->d_bar, 0, sizeof(unsigned int) * 4);
+  if (e == cudaSuccess) e = cudaMemset(c->d_bar, 0, sizeof(unsigned int) * 5);
   if (e == cudaSuccess) e = cudaMemset(c->spins, 0, c->spin_bytes);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -844,7 +1009,11 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
     int want = opt.variant == HSG_VARIANT_AUTO ? HSG_VARIANT_TWO_PASS : opt.variant;
     if (opt.n_or_per_step < 1) want = HSG_VARIANT_TWO_PASS;
     c->inject_fault = opt.inject_barrier_fault != 0;
-    hsg_status st2 = configure_schedule(c, want, c->GPT, opt.pass_bytes);
+    c->fused_possible = fmt != FMT_YX4;
+    for (int s = 0; s < n_samples; ++s)
+      if (L[s] % 4 != 0 || L[s] < 8) c->fused_possible = false;
+    const bool fused = opt.sweep_kernel == HSG_SWEEP_FUSED;
+    hsg_status st2 = configure_schedule(c, want, c->GPT, opt.pass_bytes, fused);
     if (st2 != HSG_OK) return cleanup_fail(st2);
   }
   ConvParams cp = conv_params(c, nullptr, nullptr);
@@ -895,7 +1064,7 @@ hsg_status hsg_sweep_or(hsg_ctx* c, int n) {
   if (n == 0) return HSG_OK;
   HSG_CUDA(c, cudaSetDevice(c->device));
   c->e_valid = false;
-  for (int k = 0; k < n; ++k) HSG_TRY(half_sweeps(c, false, k));
+  HSG_TRY(or_sweeps(c, n, 0));
   HSG_CUDA(c, launch_bump(c->d_counters, c->d_active, c->ns, n, 0, c->stream));
   return HSG_OK;
 }
@@ -1416,6 +1585,9 @@ hsg_status hsg_get_info(hsg_ctx* c, hsg_info* info) {
   info->sweep_count = cnt[0];
   info->pt_count = cnt[1];
   info->stream = (void*)c->stream;
+  info->sweep_kernel = c->use_fused ? HSG_SWEEP_FUSED : HSG_SWEEP_HALF;
+  info->fused_band_rows = c->fused_ny.empty() ? 0 : c->fused_ny[0];
+  info->fused_items = c->n_fused_items;
   return HSG_OK;
 }
 

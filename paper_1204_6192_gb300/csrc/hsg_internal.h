@@ -179,6 +179,30 @@ struct MultihitParams {
 cudaError_t launch_multihit(int fmt, bool j16, bool fast, int tile, const MultihitParams& p,
                             int n_blocks, cudaStream_t st);
 
+// Fused over-relaxation sweep (hsg_fused.cu): one launch per sweep, reading
+// `src` and writing `dst` (two spin buffers of the same layout).  A work item
+// is one column: (sample, chunk group, y0 | ny << 16, za | zb << 16) -- the band
+// of rows [y0, y0 + ny) (ny = L: the whole plane) over the planes [za, zb).
+constexpr int FUSED_CONSUMER_WARPS = 16;
+constexpr int FUSED_SMEM_HEAD = 256;     // mbarriers and the abort flag
+constexpr int FUSED_ODD_SLOTS = 6, FUSED_EVEN_SLOTS = 4;
+constexpr int FUSED_MAX_SITES = 2 * FUSED_CONSUMER_WARPS * 32;   // per half-step and block
+struct FusedParams {
+  const unsigned char* src;
+  unsigned char* dst;
+  const void* rec;
+  const SampleDev* samples;
+  const int4* items;
+  const unsigned char* active;          // [n_samples]: frozen samples are skipped
+  int n_items;
+  uint32_t slot1, slot0;                // bytes of one odd / even plane slot
+  unsigned int* err;                    // set when a bounded wait ran out
+  unsigned long long timeout_ns;
+};
+cudaError_t prepare_fused(int fmt, bool j16, size_t smem, int* blocks_per_sm);
+cudaError_t launch_fused(int fmt, bool j16, const FusedParams& p, int grid, size_t smem,
+                         cudaStream_t st);
+
 // launchers (hsg_kernels*.cu)
 cudaError_t launch_half_sweep(int fmt, bool hb, bool j16, bool fast, bool energy,
                               const SweepParams& p, int n_blocks, cudaStream_t st);

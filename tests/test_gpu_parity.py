@@ -119,11 +119,13 @@ def fp32_storage_reference(samples, n_rep, seed, schedule):
 
 
 # FP32 arithmetic adds a few ulp per update on top of the half-ulp storage
-# rounding (median: 10x).  The tail quantiles of a chaotic divergence are set
-# by a handful of sites with small local fields and move by tens of percent
-# between equally valid roundings, so they get 20x; the maximum, one outlier, 30x.
-# A wrong index, sign or random number gives O(1) deviations and fails all four.
-CHAOS_FACTOR = {0.5: 10.0, 0.9: 20.0, 0.99: 20.0, 1.0: 30.0}
+# rounding.  Measured over ten free-running sweeps of five shapes (L = 4, 8, 16;
+# H_r 0 to 2; T from 0.1 to 5), the GPU's deviation from the FP64 oracle is
+# 2.7-3.8x the FP32-storage spread at the median, 3.0-4.6x at the 90th and
+# 3.1-6.0x at the 99th percentile, and 2.0-15.6x at the maximum (one site):
+# 10x bounds the quantiles, 30x the maximum.  A wrong index, sign or random
+# number gives O(1) deviations and fails all four.
+CHAOS_FACTOR = {0.5: 10.0, 0.9: 10.0, 0.99: 10.0, 1.0: 30.0}
 
 
 def assert_within_fp32_spread(d, ref):
@@ -163,32 +165,56 @@ def test_trajectory_config1_shape():
 STEP_SWEEPS = ["sweep_hb"] + ["sweep_or"] * 5 + ["sweep_hb"] + ["sweep_or"] * 3
 
 
-def reseeded_sweeps(samples, n_rep, seed, sweeps=STEP_SWEEPS):
-    """Consecutive sweeps in a step's order; before each one the oracle takes
-    over the GPU's current binary32 state, so every sweep starts both sides
-    from the same state (sweep counters 0, 1, ... on both).  Returns the
-    largest component deviation after each sweep."""
+def parity_mask(L):
+    x, y, z = np.meshgrid(np.arange(L), np.arange(L), np.arange(L), indexing="ij")
+    return ((x + y + z) % 2).transpose(2, 1, 0).ravel()      # site = x + L (y + L z)
+
+
+def half_sweep_deviations(samples, n_rep, seed, sweeps=STEP_SWEEPS):
+    """Consecutive sweeps in a step's order, each half-sweep compared from
+    identical inputs.  Before a sweep the oracle takes the GPU's binary32
+    state S0 and does the even half-sweep; the GPU does the whole sweep (S1).
+    The GPU's even sites in S1 are its even half-sweep's output (the odd half
+    does not touch them), so the oracle's odd half-sweep then starts from the
+    even sites of S1 and the odd sites of S0 -- the GPU's own intermediate state.
+    Returns the largest component deviation of each half-sweep."""
     samples = [f32(s) for s in samples]
     ctx = hsg.Context(samples, n_rep, seed)
     orc = oracle.OracleSim(samples, n_rep, seed)
+    odd = [parity_mask(s.L).astype(bool) for s in samples]
     dev = []
     for op in sweeps:
-        for o, st in zip(orc.samples, ctx.get_spins()):
-            o.s = st.astype(np.float64)
+        s0 = ctx.get_spins()
         getattr(ctx, op)(1)
-        getattr(orc, op)(1)
-        dev.append(max(np.abs(g - o).max() for g, o in zip(ctx.get_spins(), orc.spins())))
+        s1 = ctx.get_spins()
+        d = [0.0, 0.0]
+        for o, a, b, m in zip(orc.samples, s0, s1, odd):
+            for parity in (0, 1):
+                if parity == 0:
+                    o.s = a.astype(np.float64)
+                else:
+                    mid = a.astype(np.float64)
+                    mid[:, ~m] = b[:, ~m]
+                    o.s = mid
+                if op == "sweep_hb":
+                    o.hb_half(parity, o.sweep)
+                else:
+                    o.or_half(parity)
+                sel = m if parity else ~m
+                d[parity] = max(d[parity], float(np.abs(o.s[:, sel] - b[:, sel]).max()))
+            o.sweep += 1
+        dev.append(d)
     ctx.close()
     return np.array(dev)
 
 
 @pytest.mark.parametrize("shape", ["L8_plain", "L16_field"])
-def test_ten_sweeps_each_from_the_gpu_state_within_1e5(shape):
-    """Ten consecutive sweeps (HB, 5 OR, HB, 3 OR; sweep counters 0-9), each
-    started from the GPU's own state: every component of every system within
-    1e-5 of the FP64 oracle after every sweep.  L8_plain: L = 8, H = 0,
-    2 x 8 temperatures in [0.15, 0.6]; L16_field: L = 16, H_r = 0.05,
-    2 x 8 temperatures in [0.1, 0.4]."""
+def test_ten_sweeps_each_half_from_the_gpu_state_within_1e5(shape):
+    """Ten consecutive sweeps (HB, 5 OR, HB, 3 OR; sweep counters 0-9); every
+    half-sweep is compared with the FP64 oracle from identical inputs, the
+    GPU's own state: every component of every system within 1e-5.  L8_plain:
+    L = 8, H = 0, 2 x 8 temperatures in [0.15, 0.6]; L16_field: L = 16,
+    H_r = 0.05, 2 x 8 temperatures in [0.1, 0.4]."""
     if shape == "L8_plain":
         w = inputs.workload("L8_plain")
         samples, n_rep, seed = w.samples, w.n_replicas, w.seed
@@ -196,9 +222,30 @@ def test_ten_sweeps_each_from_the_gpu_state_within_1e5(shape):
         samples = [inputs.small_sample(16, n_temps=8, h_r=0.05, disorder_seed=16, t_min=0.1,
                                        t_max=0.4)]
         n_rep, seed = 2, 3
-    dev = reseeded_sweeps(samples, n_rep, seed)
-    print(f"\n[{shape}] max |GPU - oracle| per sweep: {np.array2string(dev, precision=2)}")
+    dev = half_sweep_deviations(samples, n_rep, seed)
+    print(f"\n[{shape}] max |GPU - oracle| per half-sweep (even, odd):\n"
+          f"{np.array2string(dev, precision=2)}")
     assert np.all(dev < TOL_FP32), dev
+
+
+def test_field_dominated_trajectory_ten_sweeps_within_1e5():
+    """Where the random field dominates the couplings (H_r = 10 against |J| ~ 1)
+    a spin's move depends on its neighbours through J/|h| << 1, so rounding
+    differences shrink from sweep to sweep instead of growing: the free-running
+    FP32 trajectory stays within 1e-5 per component of the FP64 oracle through
+    ten sweeps of a step's order (HB, 5 OR, HB, 3 OR), at L = 8, 2 x 4
+    temperatures in [0.15, 0.6]."""
+    smp = f32(inputs.small_sample(8, n_temps=4, h_r=10.0, disorder_seed=8, t_min=0.15, t_max=0.6))
+    ctx = hsg.Context([smp], 2, 7)
+    orc = oracle.OracleSim([smp], 2, 7)
+    dev = []
+    for op in STEP_SWEEPS:
+        getattr(ctx, op)(1)
+        getattr(orc, op)(1)
+        dev.append(max(np.abs(g - o).max() for g, o in zip(ctx.get_spins(), orc.spins())))
+    ctx.close()
+    print(f"\n[field-dominated] max |GPU - oracle| per sweep: {np.array2string(np.array(dev), precision=2)}")
+    assert max(dev) < TOL_FP32, dev
 
 
 def test_ragged_system_count_and_batch():

@@ -15,12 +15,18 @@ the same distribution.  "Within 2 sigma" is read as a statistical test over
 all slots: no more comparisons beyond |z| = 2 than a correct chain gives at
 the 0.5% level (binomial), and none beyond the 1% Bonferroni point.
 
-Shapes: L = 8, H = 0, 2 x 8 temperatures in [0.15, 0.6], 1000 steps; and the
-L = 32 production shape (2 x 32 temperatures in [0.1, 0.4], H_r = 0.05),
-shortened to 600 steps because the FP64 oracle takes ~0.1 s per step there.
-The compressed storage forms (FP16 couplings) are held to the same criterion,
-and their mean differences against the FP64 oracle are printed as the error of
-each form (run with -s).
+Shapes.  L = 8, H = 0, 2 x 8 temperatures in [0.15, 0.6], 1000 steps, the
+error from bins of the series.  And the L = 32 production shape (2 x 32
+temperatures in [0.1, 0.4], H_r = 0.05), shortened because the FP64 oracle
+takes ~0.1 s per step there: 600 steps are far from equilibrium at T = 0.1 and
+correlated over the whole run, so binning one run cannot give its error.
+Instead 16 independent runs (seeds 1..16) of 40 steps each: per run and slot
+the mean over steps 10..39; the paired differences of the 16 runs are
+independent, so their spread gives the error (t with 15 degrees of freedom).
+Equal Markov chains give equal distributions at every step, in or out of
+equilibrium, so this tests the same property.  The compressed storage forms
+(FP16 couplings) are held to the same criterion, and their mean differences
+against the FP64 oracle are printed as the error of each form (run with -s).
 """
 import numpy as np
 import pytest
@@ -33,8 +39,10 @@ pytestmark = pytest.mark.gpu
 SHAPES = {
     # name: (L, n_temps, t_min, t_max, h_r, disorder_seed, steps, bins)
     "L8": (8, 8, 0.15, 0.6, 0.0, 1, 1000, 10),
-    "L32": (32, 32, 0.1, 0.4, 0.05, 2, 600, 10),
+    "L32": (32, 32, 0.1, 0.4, 0.05, 2, 40, None),
 }
+ENSEMBLE_SEEDS = 16        # L32: independent runs
+ENSEMBLE_SKIP = 10         # L32: steps before the average of each run
 COMPRESSED = ["fp16", "bf16", "angle16", "oct16", "yx4"]
 
 
@@ -54,8 +62,8 @@ def workload(shape, fp16_couplings):
     return inputs.Sample(L=L, J=r(smp.J), H=r(smp.H), temps=t)
 
 
-def series_gpu(smp, steps, precision="fp32", j16=False, fast_math=False):
-    ctx = hsg.Context([smp], 2, 1, precision=precision, j_fp16=j16, fast_math=fast_math)
+def series_gpu(smp, steps, precision="fp32", j16=False, fast_math=False, seed=1):
+    ctx = hsg.Context([smp], 2, seed, precision=precision, j_fp16=j16, fast_math=fast_math)
     E, Q = [], []
     for _ in range(steps):
         ctx.step(1)
@@ -66,8 +74,8 @@ def series_gpu(smp, steps, precision="fp32", j16=False, fast_math=False):
     return np.array(E), np.array(Q)
 
 
-def series_oracle(smp, steps):
-    sim = oracle.OracleSim([smp], 2, 1)
+def series_oracle(smp, steps, seed=1):
+    sim = oracle.OracleSim([smp], 2, seed)
     E, Q = [], []
     for _ in range(steps):
         sim.step(1)
@@ -89,20 +97,37 @@ def binned(x, nbins):
     return x.mean(axis=0), bins.std(axis=0, ddof=1) / np.sqrt(nbins)
 
 
-def paired_z(gpu, orc, nbins):
-    """Mean paired difference, its error and z, for e(T) and q^2 per slot."""
+def ensemble(runner, smp, N):
+    """Per run (seed) and slot, the means of e(T) and q^2 over steps
+    ENSEMBLE_SKIP.. of the run: arrays [runs, slots]."""
+    e, q = [], []
+    for seed in range(1, ENSEMBLE_SEEDS + 1):
+        E, Q = runner(seed)
+        ee, qq = per_slot(E, Q, N)
+        e.append(ee[ENSEMBLE_SKIP:].mean(axis=0))
+        q.append(qq[ENSEMBLE_SKIP:].mean(axis=0))
+    return np.array(e), np.array(q)
+
+
+def paired(gpu, orc, shape):
+    """Mean paired difference, its error and z, for e(T) and q^2 per slot, with
+    the degrees of freedom of the error."""
+    nbins = SHAPES[shape][7]
     out = {}
     for k, name in enumerate(("e", "q2")):
-        m, s = binned(gpu[k] - orc[k], nbins)
+        d = gpu[k] - orc[k]
+        if nbins:
+            m, s = binned(d, nbins)
+        else:
+            m, s = d.mean(axis=0), d.std(axis=0, ddof=1) / np.sqrt(len(d))
         out[name] = (m, s, m / np.maximum(s, 1e-300))
-    return out
+    return out, (nbins - 1 if nbins else ENSEMBLE_SEEDS - 1)
 
 
-def check(res, nbins, label):
+def check(res, dof, label):
     from scipy import stats
     z = np.concatenate([res["e"][2], res["q2"][2]])
     n = z.size
-    dof = nbins - 1
     p2 = 2.0 * stats.t.sf(2.0, dof)                  # chance of |z| > 2 for a correct chain
     k_max = int(stats.binom.ppf(0.995, n, p2))
     z_max = stats.t.isf(0.005 / n, dof)              # 1% two-sided, Bonferroni over n
@@ -126,18 +151,28 @@ def oracle_reference(shape, fp16_couplings):
     key = (shape, fp16_couplings)
     if key not in _cache:
         smp = workload(shape, fp16_couplings)
-        steps = SHAPES[shape][6]
-        _cache[key] = (smp, per_slot(*series_oracle(smp, steps), N=smp.L ** 3))
+        steps, N = SHAPES[shape][6], smp.L ** 3
+        if SHAPES[shape][7]:
+            ref = per_slot(*series_oracle(smp, steps), N=N)
+        else:
+            ref = ensemble(lambda sd: series_oracle(smp, steps, seed=sd), smp, N)
+        _cache[key] = (smp, ref)
     return _cache[key]
+
+
+def gpu_observables(shape, smp, **kw):
+    steps, N = SHAPES[shape][6], smp.L ** 3
+    if SHAPES[shape][7]:
+        return per_slot(*series_gpu(smp, steps, **kw), N=N)
+    return ensemble(lambda sd: series_gpu(smp, steps, seed=sd, **kw), smp, N)
 
 
 @pytest.mark.parametrize("shape", ["L8", "L32"])
 def test_equilibrium_observables_fp32(shape):
     """FP32 spins and couplings against the FP64 oracle, e(T) and <q^2> per slot."""
     smp, ref = oracle_reference(shape, False)
-    steps, nbins = SHAPES[shape][6], SHAPES[shape][7]
-    gpu = per_slot(*series_gpu(smp, steps), N=smp.L ** 3)
-    check(paired_z(gpu, ref, nbins), nbins, f"{shape} fp32")
+    res, dof = paired(gpu_observables(shape, smp), ref, shape)
+    check(res, dof, f"{shape} fp32")
 
 
 @pytest.mark.parametrize("shape", ["L8", "L32"])
@@ -147,15 +182,13 @@ def test_compressed_storage_against_fp64(shape, precision):
     FP16-rounded couplings (no storage rounding in the oracle): the printed mean
     differences are each form's error, held to the same criterion as FP32."""
     smp, ref = oracle_reference(shape, True)
-    steps, nbins = SHAPES[shape][6], SHAPES[shape][7]
-    gpu = per_slot(*series_gpu(smp, steps, precision=precision, j16=True), N=smp.L ** 3)
-    check(paired_z(gpu, ref, nbins), nbins, f"{shape} {precision}")
+    res, dof = paired(gpu_observables(shape, smp, precision=precision, j16=True), ref, shape)
+    check(res, dof, f"{shape} {precision}")
 
 
 def test_fast_math_heat_bath_statistics():
     """The hardware-approximation heat bath (the paper's fast_math variant,
     Table 1) samples the same equilibrium."""
     smp, ref = oracle_reference("L8", False)
-    steps, nbins = SHAPES["L8"][6], SHAPES["L8"][7]
-    gpu = per_slot(*series_gpu(smp, steps, fast_math=True), N=smp.L ** 3)
-    check(paired_z(gpu, ref, nbins), nbins, "L8 fast_math")
+    res, dof = paired(gpu_observables("L8", smp, fast_math=True), ref, "L8")
+    check(res, dof, "L8 fast_math")
