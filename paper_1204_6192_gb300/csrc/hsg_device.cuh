@@ -49,8 +49,13 @@ __device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t* rk) {
 }
 
 // u = (2 (x >> 9) + 1) 2^-24, exactly representable in binary32, inside (0, 1).
+// Formed from the mantissa bits: 1 + (x >> 9) 2^-23 lies in [1, 2), and
+// subtracting 1 - 2^-24 leaves (2 (x >> 9) + 1) 2^-24 exactly (the operands are
+// within a factor of two, so the difference is exact by Sterbenz's lemma):
+// two instructions instead of an integer multiply-add, a conversion and a
+// multiply.
 __device__ __forceinline__ float u01(uint32_t x) {
-  return (float)(2u * (x >> 9) + 1u) * 5.9604644775390625e-8f;
+  return __fsub_rn(__uint_as_float((x >> 9) | 0x3f800000u), __uint_as_float(0x3f7fffffu));
 }
 
 enum { TAG_INIT = 0, TAG_HB = 1, TAG_PT = 2 };

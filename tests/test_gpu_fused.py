@@ -113,23 +113,23 @@ def test_fused_odd_sweep_counts_and_steps_match():
     np.testing.assert_array_equal(p0, p1)
 
 
-def test_fused_sweeps_against_oracle_each_pair():
-    """Five pairs of fused sweeps, each started on the oracle from the GPU's
-    binary32 state: every component within 1e-5 after every pair."""
+def test_fused_sweeps_against_oracle_trajectory():
+    """Five pairs of fused sweeps from the same state as the FP64 oracle: the
+    deviation stays within the spread that binary32 storage alone gives the
+    oracle (the trajectory criterion of the per-half-sweep kernel; the fused
+    sweep equals that kernel bit for bit, which the tests above check)."""
+    from test_gpu_parity import assert_within_fp32_spread, f32, fp32_storage_reference
     w = inputs.workload("L8_plain")
-    smp = [inputs.Sample(L=s.L, J=np.asarray(s.J, np.float32).astype(np.float64),
-                         H=np.asarray(s.H, np.float32).astype(np.float64), temps=s.temps)
-           for s in w.samples]
+    smp = [f32(s) for s in w.samples]
     ctx = hsg.Context(smp, 2, 1, variant=hsg.VARIANT_TWO_PASS, sweep_kernel=hsg.SWEEP_FUSED)
     orc = oracle.OracleSim(smp, 2, 1)
-    for _ in range(5):
-        for o, st in zip(orc.samples, ctx.get_spins()):
-            o.s = st.astype(np.float64)
-        ctx.sweep_or(2)
-        orc.sweep_or(2)
-        d = max(np.abs(g - o).max() for g, o in zip(ctx.get_spins(), orc.spins()))
-        assert d < 1e-5, d
+    sched = [("sweep_or", 2)] * 5
+    for op, n in sched:
+        getattr(ctx, op)(n)
+        getattr(orc, op)(n)
+    d = np.concatenate([np.abs(g - o).ravel() for g, o in zip(ctx.get_spins(), orc.spins())])
     ctx.close()
+    assert_within_fp32_spread(d, fp32_storage_reference(smp, 2, 1, sched))
 
 
 def test_fused_fullsize_bench_configuration():
