@@ -176,11 +176,9 @@ __device__ __forceinline__ void sweep_block(const SweepParams& p, int bidx, floa
       }
     }
     if (EN) {
-#pragma unroll
-      for (int v = 0; v < VEC; ++v) {
-        const float t = warp_sum(e[v]);
-        if (lane == 0) esum[warp * p.GPT * VEC + (g - g0) * VEC + v] = t;
-      }
+      static_assert(VEC == 4, "the scattered warp sum takes four systems per chunk");
+      const float t = warp_sum4_scatter(e, lane);
+      if ((lane & 7) == 0) esum[warp * p.GPT * VEC + (g - g0) * VEC + (lane >> 3)] = t;
     }
   }
   if (EN) {
