@@ -295,14 +295,18 @@ hsg_status enqueue_energy(hsg_ctx* c) {
   return HSG_OK;
 }
 
-// Plan of the fused over-relaxation sweep (at first use): per sample the rows
-// of y a block holds (the whole plane where it fits, else the largest divisor
-// of L that fits, with the band's halo rows), the shared-memory slots, the
-// second spin buffer and the work items.  Columns (sample, band, chunk group;
-// chunk groups adjacent, so blocks that run together share couplings and halo
-// rows in L2) fill whole rounds of the grid over all planes; the columns left
-// over are cut into z segments so that the last round also fills the grid.
-// Leaves use_fused possible only if everything fits.
+// Plan of the fused over-relaxation sweep (at first use).  Per sample, the rows
+// of y a block holds: the whole plane (rows wrap in the slot) or bands of ny
+// rows (the last band may be shorter) with one halo row of even sites and two
+// of odd sites on each side.  A step updates R0 = ny + 2 rows of even sites and
+// ny rows of odd sites with FUSED_THREADS threads, so the band height is the one
+// that fits shared memory and wastes the fewest thread slots on halo rows and
+// idle threads (at L = 128: 7 rows, 1024 sites, exactly 2 per thread).  The
+// work items are columns (sample, band, chunk group; chunk groups adjacent, so
+// blocks that run together share couplings and halo rows in L2) over all
+// planes, in whole rounds of the grid; the columns left over are cut into z
+// segments so that the last round also fills the grid.  Leaves use_fused off
+// unless everything fits.
 hsg_status plan_fused(hsg_ctx* c) {
   if (!c->fused_possible || c->d_fused_items) return HSG_OK;
   const int CH = c->VEC * c->ELEM, PL = c->PL;
@@ -319,15 +323,25 @@ hsg_status plan_fused(hsg_ctx* c) {
       const long long b = std::max(slot0, (long long)PL * rows0 * Lh * CH);
       return FUSED_ODD_SLOTS * a + FUSED_EVEN_SLOTS * b <= budget;
     };
+    // useful site updates per thread slot of a step
+    auto score = [&](int n, bool full) {
+      const long long sites = full ? 2ll * L * Lh : (long long)(2 * n + 2) * Lh;
+      const long long passes = (sites + FUSED_THREADS - 1) / FUSED_THREADS;
+      if (passes > FUSED_SITES_PER_THREAD) return -1.0;
+      return (double)(2ll * n * Lh) / (double)(passes * FUSED_THREADS);
+    };
     int best = 0;
-    if ((long long)L * Lh <= FUSED_MAX_SITES && fits(L, L)) {
-      best = L;
-    } else {
-      for (int n = L - 4; n >= 4; --n)
-        if (L % n == 0 && (long long)(n + 2) * Lh <= FUSED_MAX_SITES && fits(n + 4, n + 2)) {
-          best = n;
-          break;
-        }
+    double best_score = 0.0;
+    if (fits(L, L)) {
+      best_score = score(L, true);
+      if (best_score > 0.0) best = L;
+    }
+    for (int n = 2; n <= L - 4; ++n) {
+      const double sc = score(n, false);
+      if (sc > best_score + 1e-9 && fits(n + 4, n + 2)) {
+        best = n;
+        best_score = sc;
+      }
     }
     if (!best) {
       c->fused_possible = false;
@@ -346,11 +360,13 @@ hsg_status plan_fused(hsg_ctx* c) {
     return HSG_OK;
   }
   const int P = n_sm * per_sm;
-  // columns: (sample, chunk group, y0 | ny << 16, L)
+  // columns: (sample, chunk group, y0 | rows << 16, L); the last band of a sample may be shorter
   std::vector<int4> cols;
   for (int s = 0; s < c->ns; ++s)
-    for (int y0 = 0; y0 < c->L[s]; y0 += ny[s])
-      for (int g = 0; g < c->G; ++g) cols.push_back(make_int4(s, g, y0 | (ny[s] << 16), c->L[s]));
+    for (int y0 = 0; y0 < c->L[s]; y0 += ny[s]) {
+      const int rows = std::min(ny[s], c->L[s] - y0);
+      for (int g = 0; g < c->G; ++g) cols.push_back(make_int4(s, g, y0 | (rows << 16), c->L[s]));
+    }
   const int C = (int)cols.size();
   const int full = (C / P) * P, rem = C - full;
   std::vector<int4> items;

@@ -3,24 +3,26 @@
 //
 // A block walks a column of the lattice -- one chunk group (4 systems) of one
 // sample, a band of ny rows of y (all x), a range of planes [za, zb) -- as a
-// wavefront along z.  At plane t it updates the even sites of plane t (from the
-// odd sites of planes t-1, t, t+1, all still old), then the odd sites of plane
-// t-1 (from the even sites of planes t-2, t-1, t, all already new).  That is
-// the order of the two half-sweeps: every even site sees only old odd spins and
-// every odd site only new even spins, so the result equals the even half-sweep
-// followed by the odd one, bit for bit (the same arithmetic in the same order
-// as the per-half-sweep kernel).
+// wavefront along z.  In the step at plane t it updates the even sites of plane
+// t (from the odd sites of planes t-1, t, t+1, all still old) and the odd sites
+// of plane t-2 (from the even sites of planes t-3, t-2, t-1, all updated in
+// earlier steps).  The two sets do not depend on each other, so one block
+// barrier per step suffices, and every thread gets the same number of sites.
+// That is the order of the two half-sweeps: every even site sees only old odd
+// spins and every odd site only new even spins, so the result equals the even
+// half-sweep followed by the odd one, bit for bit (the same arithmetic in the
+// same order as the per-half-sweep kernel).
 //
 // The sweep reads one spin buffer and writes the other, so blocks never wait
 // for one another: the even sites a band's odd rows need from its neighbours
 // (rows y0-1 and y0+ny) and those a segment needs from the planes beyond it
 // (za-1 and zb) are recomputed from the old spins.  Odd and even spins reach
 // shared memory by bulk copies (cp.async.bulk) into two rings of plane slots
-// (odd: 6, even: 4), each with a full mbarrier.  Thread 0 issues the copies:
+// (odd: 6, even: 5), each with a full mbarrier.  Thread 0 issues the copies:
 // the first ones at the start, then, after every step, into the slots that
-// step released (the consumers are past a block barrier there), running ahead
+// step released (the threads are past the block barrier there), running ahead
 // into the block's next work item.  The six bonds and the field of a site
-// (shared by all chunk groups, so mostly L2 hits) are loaded one plane ahead.
+// (shared by all chunk groups, so mostly L2 hits) are loaded one step ahead.
 // Every wait is bounded: one that runs out sets the error word and the block
 // winds down after its copies have landed.
 #include <type_traits>
@@ -33,11 +35,11 @@ namespace hsg {
 
 namespace {
 
-constexpr int FD1 = 6;          // odd-site plane slots
-constexpr int FD0 = 4;          // even-site plane slots
+constexpr int FD1 = FUSED_ODD_SLOTS;    // odd-site plane slots
+constexpr int FD0 = FUSED_EVEN_SLOTS;   // even-site plane slots
 constexpr int FCW = FUSED_CONSUMER_WARPS;
 constexpr int FNCT = FCW * 32;  // consumer threads
-constexpr int FMAXI = 2;        // sites per consumer thread and half-step (host-checked)
+constexpr int FMAXI = FUSED_SITES_PER_THREAD;   // sites per thread and step (host-checked)
 
 __device__ __forceinline__ void consumer_bar() {
   asm volatile("bar.sync 1, %0;" ::"n"(FNCT) : "memory");
@@ -122,29 +124,6 @@ __device__ __forceinline__ void load_rec(const void* rec, long long idx, Rec<J16
     r.w[0] = __ldg(q);
     r.w[1] = __ldg(q + 1);
     r.w[2] = __ldg(q + 2);
-  }
-}
-
-// Couplings and field of this thread's sites of step j (even sites of plane
-// t = za - 1 + j, odd sites of plane t - 1).
-template <bool J16>
-__device__ __forceinline__ void load_step_recs(const void* rec, const FItem& f, long long rbase,
-                                               long long half, int j, const int* r0a, const int* xa,
-                                               const int* rba, const int* xba, Rec<J16>* r0,
-                                               Rec<J16>* r1) {
-  const int L = f.L, Lh = f.Lh;
-  const int t = f.za - 1 + j;
-  const int zq = wrap(t, L), zq1 = wrap(t - 1, L);
-#pragma unroll
-  for (int k = 0; k < FMAXI; ++k) {
-    if (r0a[k] >= 0) {
-      const int y = wrap(f.y0 - f.hp0 + r0a[k], L);
-      load_rec<J16>(rec, rbase + (long long)Lh * (y + (long long)L * zq) + xa[k], r0[k]);
-    }
-    if (rba[k] >= 0 && j >= 2) {
-      const int y = f.y0 + rba[k];
-      load_rec<J16>(rec, rbase + half + (long long)Lh * (y + (long long)L * zq1) + xba[k], r1[k]);
-    }
   }
 }
 
@@ -281,6 +260,20 @@ __device__ __forceinline__ void advance(const FusedParams& p, CopyCursor& c, int
   }
 }
 
+// One of a thread's sites in the current item (fixed for the whole item; the
+// plane changes from step to step).
+struct FSite {
+  int kind;            // -1: none, 0: even site (slot row r0), 1: odd site (band row r)
+  uint32_t own;        // byte offset of its chunk in its own slot (plane 0)
+  uint32_t row;        // byte offset of its row in the neighbour slots
+  uint32_t yp, ym;     // byte offsets of the rows y + 1, y - 1 in the neighbour slots
+  int xh;              // half-x of the site
+  int pb;              // x parity of the site at plane t: (pb + t) & 1
+  long long ss;        // storage site in the plane-0 layout, without the plane term
+  long long rec;       // record index, without the plane term
+  bool out;            // even sites: the row is the block's own (written out)
+};
+
 template <int F, bool J16>
 __global__ void __launch_bounds__(FNCT, 1) k_fused_or(const FusedParams p) {
   constexpr int CH = FmtInfo<F>::CHUNK, PL = FmtInfo<F>::PLANES;
@@ -310,7 +303,7 @@ __global__ void __launch_bounds__(FNCT, 1) k_fused_or(const FusedParams p) {
     if (!p.active[f.s]) continue;
     const SampleDev& sd = p.samples[f.s];
     const int L = f.L, Lh = f.Lh;
-    const int nsteps = f.zb - f.za + 2;
+    const int nsteps = f.zb - f.za + 3;
     const uint32_t RB = (uint32_t)Lh * CH;
     const uint32_t pb1 = (uint32_t)f.R1 * RB, pb0 = (uint32_t)f.R0 * RB;
     const int nP0 = f.R0 * Lh, nP1 = f.ny * Lh;
@@ -318,124 +311,116 @@ __global__ void __launch_bounds__(FNCT, 1) k_fused_or(const FusedParams p) {
     const long long ps = sd.plane_stride;
     unsigned char* dstg = p.dst + sd.spin_off + f.g * gstride;
     const long long half = sd.N >> 1;
-    const long long rbase = sd.rec_off;
-    // this thread's sites: slot row and half-x of its even sites, band row and half-x of its odd sites
-    int r0a[FMAXI], xa[FMAXI], rba[FMAXI], xba[FMAXI];
+    const long long plane_sites = (long long)Lh * L;
+    // this thread's sites: the even sites of the slot rows first, then the odd
+    // sites of the band rows
+    FSite st[FMAXI];
 #pragma unroll
     for (int k = 0; k < FMAXI; ++k) {
-      const int i = ct + k * FNCT;
-      const int q0 = (int)((__umulhi((uint32_t)i, sd.fdLh_m) + (uint32_t)i) >> sd.fdLh_s);
-      r0a[k] = i < nP0 ? q0 : -1;
-      xa[k] = i - q0 * Lh;
-      rba[k] = i < nP1 ? q0 : -1;
-      xba[k] = i - q0 * Lh;
+      int i = ct + k * FNCT;
+      FSite& q = st[k];
+      q.kind = i < nP0 ? 0 : (i < nP0 + nP1 ? 1 : -1);
+      if (q.kind == 1) i -= nP0;
+      const int rr = (int)((__umulhi((uint32_t)i, sd.fdLh_m) + (uint32_t)i) >> sd.fdLh_s);
+      q.xh = i - rr * Lh;
+      // rn: the site's row in the slots it reads (odd slots for even sites and vice versa)
+      const int rown = q.kind == 0 ? rr + (f.hp1 - f.hp0) : rr + f.hp0;
+      const int rowo = q.kind == 0 ? rr : rr + f.hp1;        // its row in its own slot
+      int ryp = rown + 1, rym = rown - 1;
+      if (f.full) {
+        if (ryp == L) ryp = 0;
+        if (rym < 0) rym = L - 1;
+      }
+      q.own = (uint32_t)rowo * RB + (uint32_t)q.xh * CH;
+      q.row = (uint32_t)rown * RB;
+      q.yp = (uint32_t)ryp * RB + (uint32_t)q.xh * CH;
+      q.ym = (uint32_t)rym * RB + (uint32_t)q.xh * CH;
+      const int y = q.kind == 0 ? wrap(f.y0 - f.hp0 + rr, L) : f.y0 + rr;
+      // x = 2 xh + ((y + z + parity) & 1); the odd sites sit on plane t - 2
+      q.pb = q.kind == 0 ? y : y - 1;
+      q.out = q.kind == 0 && rr >= f.hp0 && rr < f.hp0 + f.ny;
+      q.ss = (q.kind == 1 ? half : 0) + (long long)Lh * y + q.xh;
+      q.rec = sd.rec_off + q.ss;
     }
-    Rec<J16> rc0[FMAXI], rc1[FMAXI], rn0[FMAXI], rn1[FMAXI];
-    load_step_recs<J16>(p.rec, f, rbase, half, 0, r0a, xa, rba, xba, rn0, rn1);
+    Rec<J16> rc[FMAXI], rn[FMAXI];
+    // couplings and field of the sites of step j: even sites on plane t, odd on t - 2
+#define HSG_FUSED_RECS(j_, dst_)                                                   \
+    {                                                                              \
+      const int t_ = f.za - 1 + (j_);                                              \
+      const long long z0_ = plane_sites * wrap(t_, L), z1_ = plane_sites * wrap(t_ - 2, L); \
+      _Pragma("unroll") for (int k = 0; k < FMAXI; ++k) {                          \
+        if (st[k].kind == 0 && t_ <= f.zb) load_rec<J16>(p.rec, st[k].rec + z0_, dst_[k]); \
+        if (st[k].kind == 1 && t_ - 2 >= f.za) load_rec<J16>(p.rec, st[k].rec + z1_, dst_[k]); \
+      }                                                                            \
+    }
+    HSG_FUSED_RECS(0, rn)
     for (int j = 0; j < nsteps; ++j) {
       const int t = f.za - 1 + j;
+      const bool do0 = t <= f.zb, do1 = t - 2 >= f.za;
 #pragma unroll
-      for (int k = 0; k < FMAXI; ++k) {
-        rc0[k] = rn0[k];
-        rc1[k] = rn1[k];
-      }
-      if (j + 1 < nsteps) load_step_recs<J16>(p.rec, f, rbase, half, j + 1, r0a, xa, rba, xba, rn0, rn1);
+      for (int k = 0; k < FMAXI; ++k) rc[k] = rn[k];
+      if (j + 1 < nsteps) HSG_FUSED_RECS(j + 1, rn)
       bool ok = true;
-      if (j == 0) {
-        for (uint32_t m = 0; m < 3; ++m)
-          ok = ok && mbar_wait(full1 + (k1 + m) % FD1, ((k1 + m) / FD1) & 1u, p.timeout_ns);
-      } else {
-        const uint32_t k = k1 + j + 2;
-        ok = mbar_wait(full1 + k % FD1, (k / FD1) & 1u, p.timeout_ns);
-      }
-      {
-        const uint32_t k = k0 + j;
-        ok = ok && mbar_wait(full0 + k % FD0, (k / FD0) & 1u, p.timeout_ns);
+      if (do0) {
+        if (j == 0) {
+          for (uint32_t m = 0; m < 2; ++m)
+            ok = ok && mbar_wait(full1 + (k1 + m) % FD1, ((k1 + m) / FD1) & 1u, p.timeout_ns);
+        }
+        const uint32_t ka = k1 + j + 2, kb = k0 + j;
+        ok = ok && mbar_wait(full1 + ka % FD1, (ka / FD1) & 1u, p.timeout_ns);
+        ok = ok && mbar_wait(full0 + kb % FD0, (kb / FD0) & 1u, p.timeout_ns);
       }
       if (!ok) {
         atomicOr(p.err, 1u);
         *s_abort = 1;
       }
       if (!*s_abort) {
-        // even sites of plane t from the old odd sites of planes t-1, t, t+1
-        const unsigned char* s1m = ring1 + (size_t)((k1 + j) % FD1) * p.slot1;
-        const unsigned char* s1c = ring1 + (size_t)((k1 + j + 1) % FD1) * p.slot1;
-        const unsigned char* s1p = ring1 + (size_t)((k1 + j + 2) % FD1) * p.slot1;
-        unsigned char* s0c = ring0 + (size_t)((k0 + j) % FD0) * p.slot0;
+        // slots of this step: odd planes t-1, t, t+1 and even plane t (even
+        // sites); even planes t-3, t-2, t-1 and odd plane t-2 (odd sites)
+        const unsigned char* o_m = ring1 + (size_t)((k1 + j) % FD1) * p.slot1;
+        const unsigned char* o_c = ring1 + (size_t)((k1 + j + 1) % FD1) * p.slot1;
+        const unsigned char* o_p = ring1 + (size_t)((k1 + j + 2) % FD1) * p.slot1;
+        unsigned char* e_t = ring0 + (size_t)((k0 + j) % FD0) * p.slot0;
+        const unsigned char* e_m = ring0 + (size_t)((k0 + j + FD0 - 3) % FD0) * p.slot0;
+        const unsigned char* e_c = ring0 + (size_t)((k0 + j + FD0 - 2) % FD0) * p.slot0;
+        const unsigned char* e_p = ring0 + (size_t)((k0 + j + FD0 - 1) % FD0) * p.slot0;
+        const unsigned char* o_own = ring1 + (size_t)((k1 + j + FD1 - 1) % FD1) * p.slot1;
         const bool write0 = t >= f.za && t < f.zb;
-        const int zq = wrap(t, L);
+        const long long z0 = plane_sites * wrap(t, L), z1 = plane_sites * wrap(t - 2, L);
 #pragma unroll
         for (int k = 0; k < FMAXI; ++k) {
-          if (r0a[k] < 0) continue;
-          const int r0 = r0a[k], xh = xa[k];
-          const int o = (f.y0 - f.hp0 + r0 + t) & 1;
-          const int r1 = r0 + (f.hp1 - f.hp0);
-          int xp = xh + o, xm = xh + o - 1;
+          const FSite& q = st[k];
+          const bool even = q.kind == 0;
+          if (even ? !do0 : (q.kind != 1 || !do1)) continue;
+          const int o = (q.pb + t) & 1;
+          int xp = q.xh + o, xm = q.xh + o - 1;
           if (xp == Lh) xp = 0;
           if (xm < 0) xm = Lh - 1;
-          int ryp = r1 + 1, rym = r1 - 1;
-          if (f.full) {
-            if (ryp == L) ryp = 0;
-            if (rym < 0) rym = L - 1;
-          }
+          const unsigned char* nc_ = even ? o_c : e_c;   // same plane
+          const unsigned char* np_ = even ? o_p : e_p;   // + z
+          const unsigned char* nm_ = even ? o_m : e_m;   // - z
+          const uint32_t pbn = even ? pb1 : pb0, pbo = even ? pb0 : pb1;
+          const uint32_t rc_ = q.row + (uint32_t)q.xh * CH;
           Chunk nc[6][PL];
-          lds_chunks<F>(s1c + r1 * RB + xp * CH, pb1, nc[0]);
-          lds_chunks<F>(s1c + r1 * RB + xm * CH, pb1, nc[1]);
-          lds_chunks<F>(s1c + ryp * RB + xh * CH, pb1, nc[2]);
-          lds_chunks<F>(s1c + rym * RB + xh * CH, pb1, nc[3]);
-          lds_chunks<F>(s1p + r1 * RB + xh * CH, pb1, nc[4]);
-          lds_chunks<F>(s1m + r1 * RB + xh * CH, pb1, nc[5]);
-          unsigned char* own = s0c + r0 * RB + xh * CH;
+          lds_chunks<F>(nc_ + q.row + xp * CH, pbn, nc[0]);
+          lds_chunks<F>(nc_ + q.row + xm * CH, pbn, nc[1]);
+          lds_chunks<F>(nc_ + q.yp, pbn, nc[2]);
+          lds_chunks<F>(nc_ + q.ym, pbn, nc[3]);
+          lds_chunks<F>(np_ + rc_, pbn, nc[4]);
+          lds_chunks<F>(nm_ + rc_, pbn, nc[5]);
+          unsigned char* own = (even ? e_t : const_cast<unsigned char*>(o_own)) + q.own;
           Chunk c[PL];
-          lds_chunks<F>(own, pb0, c);
-          or_chunk<F, J16>(nc, c, rc0[k]);
-          sts_chunks<F>(own, pb0, c);
-          if (write0 && r0 >= f.hp0 && r0 < f.hp0 + f.ny) {
-            const int y = f.y0 + r0 - f.hp0;
-            const long long ss = (long long)Lh * (y + (long long)L * zq) + xh;
+          lds_chunks<F>(own, pbo, c);
+          or_chunk<F, J16>(nc, c, rc[k]);
+          if (even) sts_chunks<F>(own, pb0, c);
+          if (even ? (write0 && q.out) : true) {
+            const long long ss = q.ss + (even ? z0 : z1);
 #pragma unroll
             for (int pl = 0; pl < PL; ++pl) *reinterpret_cast<Chunk*>(dstg + pl * ps + ss * CH) = c[pl];
           }
         }
         // the even slot is refilled by bulk copies (async proxy) once released
-        fence_proxy_async_smem();
-      }
-      consumer_bar();
-      if (!*s_abort && j >= 2) {
-        // odd sites of plane t-1 from the new even sites of planes t-2, t-1, t
-        const unsigned char* s0m = ring0 + (size_t)((k0 + j - 2) % FD0) * p.slot0;
-        const unsigned char* s0c = ring0 + (size_t)((k0 + j - 1) % FD0) * p.slot0;
-        const unsigned char* s0p = ring0 + (size_t)((k0 + j) % FD0) * p.slot0;
-        const unsigned char* s1c = ring1 + (size_t)((k1 + j) % FD1) * p.slot1;
-        const int zq = wrap(t - 1, L);
-#pragma unroll
-        for (int k = 0; k < FMAXI; ++k) {
-          if (rba[k] < 0) continue;
-          const int r = rba[k], xh = xba[k];
-          const int o = (f.y0 + r + t) & 1;
-          const int r0 = r + f.hp0, r1 = r + f.hp1;
-          int xp = xh + o, xm = xh + o - 1;
-          if (xp == Lh) xp = 0;
-          if (xm < 0) xm = Lh - 1;
-          int ryp = r0 + 1, rym = r0 - 1;
-          if (f.full) {
-            if (ryp == L) ryp = 0;
-            if (rym < 0) rym = L - 1;
-          }
-          Chunk nc[6][PL];
-          lds_chunks<F>(s0c + r0 * RB + xp * CH, pb0, nc[0]);
-          lds_chunks<F>(s0c + r0 * RB + xm * CH, pb0, nc[1]);
-          lds_chunks<F>(s0c + ryp * RB + xh * CH, pb0, nc[2]);
-          lds_chunks<F>(s0c + rym * RB + xh * CH, pb0, nc[3]);
-          lds_chunks<F>(s0p + r0 * RB + xh * CH, pb0, nc[4]);
-          lds_chunks<F>(s0m + r0 * RB + xh * CH, pb0, nc[5]);
-          Chunk c[PL];
-          lds_chunks<F>(s1c + r1 * RB + xh * CH, pb1, c);
-          or_chunk<F, J16>(nc, c, rc1[k]);
-          const long long ss = half + (long long)Lh * (f.y0 + r + (long long)L * zq) + xh;
-#pragma unroll
-          for (int pl = 0; pl < PL; ++pl) *reinterpret_cast<Chunk*>(dstg + pl * ps + ss * CH) = c[pl];
-        }
+        if (do0) fence_proxy_async_smem();
       }
       consumer_bar();
       if (*s_abort) {
@@ -443,16 +428,18 @@ __global__ void __launch_bounds__(FNCT, 1) k_fused_or(const FusedParams p) {
         break;
       }
       if (ct == 0) {
-        // slots released by this step: odd plane t-1 and even plane t-2 (all of
-        // the item's remaining ones after its last step); refill them
-        const uint32_t rel1 = k1 + j + (j < nsteps - 1 ? 1u : 3u);
-        const uint32_t rel0 = j < nsteps - 1 ? (j >= 2 ? k0 + j - 1 : k0) : k0 + j + 1;
+        // released by this step: odd plane t-2 and even plane t-3 (every slot
+        // of the item after its last step); refill them
+        const bool last = j == nsteps - 1;
+        const uint32_t rel1 = k1 + (last ? (uint32_t)nsteps + 1u : (uint32_t)j);
+        const uint32_t rel0 = k0 + (last ? (uint32_t)nsteps - 1u : (uint32_t)max(0, j - 2));
         advance<F>(p, c1, 1, rel1 + FD1, ring1, p.slot1, full1, FD1);
         advance<F>(p, c0, 0, rel0 + FD0, ring0, p.slot0, full0, FD0);
       }
     }
-    k1 += nsteps + 2;
-    k0 += nsteps;
+#undef HSG_FUSED_RECS
+    k1 += nsteps + 1;
+    k0 += nsteps - 1;
   }
   if (ct == 0 && aborted) {
     // wind down: let the copies still in flight land before the block exits
