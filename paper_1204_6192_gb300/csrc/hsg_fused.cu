@@ -18,10 +18,10 @@
 // (rows y0-1 and y0+ny) and those a segment needs from the planes beyond it
 // (za-1 and zb) are recomputed from the old spins.  Odd and even spins reach
 // shared memory by bulk copies (cp.async.bulk) into two rings of plane slots
-// (odd: 6, even: 5), each with a full mbarrier.  Thread 0 issues the copies:
-// the first ones at the start, then, after every step, into the slots that
-// step released (the threads are past the block barrier there), running ahead
-// into the block's next work item.  The six bonds and the field of a site
+// (odd: 6, even: 5), each with a full mbarrier.  One thread per ring (warps 0
+// and 1) issues its copies: the first ones at the start, then, after every
+// step, into the slots that step released (the threads are past the block
+// barrier there), running ahead into the block's next work item.  The six bonds and the field of a site
 // (shared by all chunk groups, so mostly L2 hits) are loaded one step ahead.
 // Every wait is bounded: one that runs out sets the error word and the block
 // winds down after its copies have landed.
@@ -76,32 +76,6 @@ __device__ __forceinline__ FItem item_geom(const FusedParams& p, int it) {
 }
 
 __device__ __forceinline__ int wrap(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
-
-// ---------------------------------------------------------------------------
-// producer: bulk copies of rows [ya, ya + R) (mod L) of one parity of plane q
-// ---------------------------------------------------------------------------
-template <int F>
-__device__ __forceinline__ void copy_plane(const FusedParams& p, const FItem& f, const SampleDev& sd,
-                                           int parity, int q, int ya, int R, unsigned char* slot,
-                                           uint64_t* bar) {
-  constexpr int CH = FmtInfo<F>::CHUNK, PL = FmtInfo<F>::PLANES;
-  const uint32_t RB = (uint32_t)f.Lh * CH;
-  const uint32_t bytes = (uint32_t)PL * R * RB;
-  mbar_expect_tx(bar, bytes);
-  const int L = f.L;
-  q = ((q % L) + L) % L;
-  ya = ((ya % L) + L) % L;
-  const int n1 = min(R, L - ya);
-  const long long gstride = (long long)sd.N * CH;
-  const long long base_ss = (long long)parity * (sd.N >> 1) + (long long)f.Lh * L * q;
-#pragma unroll
-  for (int c = 0; c < PL; ++c) {
-    const unsigned char* g0 = p.src + sd.spin_off + c * sd.plane_stride + f.g * gstride;
-    unsigned char* d = slot + (uint32_t)c * R * RB;
-    bulk_copy_g2s(d, g0 + (base_ss + (long long)f.Lh * ya) * CH, (uint32_t)n1 * RB, bar);
-    if (n1 < R) bulk_copy_g2s(d + (uint32_t)n1 * RB, g0 + base_ss * CH, (uint32_t)(R - n1) * RB, bar);
-  }
-}
 
 // ---------------------------------------------------------------------------
 // consumer: one site update from chunks in shared memory
@@ -230,33 +204,71 @@ __device__ __forceinline__ void or_chunk(const typename FmtInfo<F>::Chunk (*nc)[
 
 }  // namespace
 
-// Thread 0's queue of bulk copies: the odd-plane loads of every item of the
-// block (planes za-2 .. zb+1) and its even-plane loads (za-1 .. zb), each issued
-// as soon as a slot of its ring has been released, running into the next item.
+// The queue of bulk copies of one ring: the odd-plane loads of every item of
+// the block (planes za-2 .. zb+1; warp 0 issues them) or its even-plane loads
+// (za-1 .. zb; warp 1), each issued as soon as a slot of its ring has been
+// released, running into the next item.  The cursor keeps the current item's
+// copy geometry, so a copy costs a few integer operations.
 struct CopyCursor {
-  int it;         // current item (n_items: done)
-  int m;          // next load within the item
-  uint32_t k;     // loads issued
+  int it;                    // current item (>= n_items: done)
+  int m, n;                  // next load within the item, loads in the item (0: not decoded)
+  uint32_t k;                // loads issued
+  int q, L;                  // plane of the next load (wrapped), lattice size
+  const unsigned char* src;  // component 0 of row ya of plane 0 of the ring's parity
+  long long plane_stride;    // bytes between components
+  long long plane_bytes;     // bytes between planes (Lh L CHUNK)
+  long long wrap_back;       // bytes from row ya back to row 0 (second segment)
+  uint32_t seg1, seg2;       // bytes of the two row segments (seg2 = 0: one segment)
+  uint32_t slot_stride;      // bytes between components in the slot (R rows)
 };
 
 template <int F>
 __device__ __forceinline__ void advance(const FusedParams& p, CopyCursor& c, int parity, uint32_t limit,
                                         unsigned char* ring, uint32_t slot_bytes, uint64_t* full,
                                         uint32_t D) {
+  constexpr int CH = FmtInfo<F>::CHUNK, PL = FmtInfo<F>::PLANES;
   while (c.k < limit && c.it < p.n_items) {
-    const FItem f = item_geom(p, c.it);
-    const int n = f.zb - f.za + (parity ? 4 : 2);
-    if (!p.active[f.s] || c.m >= n) {
-      c.it += gridDim.x;
+    if (c.n == 0) {
+      // decode the item once
+      const FItem f = item_geom(p, c.it);
+      if (!p.active[f.s]) {
+        c.it += gridDim.x;
+        continue;
+      }
+      const SampleDev& sd = p.samples[f.s];
+      const int L = f.L, R = parity ? f.R1 : f.R0;
+      const int ya = wrap(f.y0 - (parity ? f.hp1 : f.hp0), L);
+      const uint32_t RB = (uint32_t)f.Lh * CH;
+      const int n1 = min(R, L - ya);
+      c.n = f.zb - f.za + (parity ? 4 : 2);
       c.m = 0;
-      continue;
+      c.L = L;
+      c.q = ((parity ? f.za - 2 : f.za - 1) + L) % L;
+      c.plane_stride = sd.plane_stride;
+      c.plane_bytes = (long long)f.Lh * L * CH;
+      c.src = p.src + sd.spin_off + (long long)f.g * sd.N * CH +
+              ((long long)parity * (sd.N >> 1) + (long long)f.Lh * ya) * CH;
+      c.wrap_back = (long long)f.Lh * ya * CH;
+      c.seg1 = (uint32_t)n1 * RB;
+      c.seg2 = (uint32_t)(R - n1) * RB;
+      c.slot_stride = (uint32_t)R * RB;
     }
-    const SampleDev& sd = p.samples[f.s];
-    const int q = parity ? f.za - 2 + c.m : f.za - 1 + c.m;
-    copy_plane<F>(p, f, sd, parity, q, f.y0 - (parity ? f.hp1 : f.hp0), parity ? f.R1 : f.R0,
-                  ring + (size_t)(c.k % D) * slot_bytes, full + c.k % D);
-    ++c.m;
+    unsigned char* slot = ring + (size_t)(c.k % D) * slot_bytes;
+    uint64_t* bar = full + c.k % D;
+    mbar_expect_tx(bar, (uint32_t)PL * (c.seg1 + c.seg2));
+    const unsigned char* g = c.src + c.q * c.plane_bytes;
+#pragma unroll
+    for (int pl = 0; pl < PL; ++pl) {
+      unsigned char* d = slot + pl * c.slot_stride;
+      bulk_copy_g2s(d, g + pl * c.plane_stride, c.seg1, bar);
+      if (c.seg2) bulk_copy_g2s(d + c.seg1, g + pl * c.plane_stride - c.wrap_back, c.seg2, bar);
+    }
     ++c.k;
+    if (++c.q == c.L) c.q = 0;
+    if (++c.m == c.n) {
+      c.it += gridDim.x;
+      c.n = 0;
+    }
   }
 }
 
@@ -285,16 +297,19 @@ __global__ void __launch_bounds__(FNCT, 1) k_fused_or(const FusedParams p) {
   unsigned char* ring1 = smem + FUSED_SMEM_HEAD;
   unsigned char* ring0 = ring1 + (size_t)FD1 * p.slot1;
   const int ct = threadIdx.x;
-  CopyCursor c1{(int)blockIdx.x, 0, 0u}, c0{(int)blockIdx.x, 0, 0u};   // thread 0 only
+  // copy cursors: odd planes issued by thread 0, even planes by thread 32
+  const bool issue1 = ct == 0, issue0 = ct == 32;
+  CopyCursor cc{};
+  cc.it = (int)blockIdx.x;
   if (ct == 0) {
     for (int k = 0; k < FD1; ++k) mbar_init(full1 + k, 1);
     for (int k = 0; k < FD0; ++k) mbar_init(full0 + k, 1);
     *s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    advance<F>(p, c1, 1, FD1, ring1, p.slot1, full1, FD1);
-    advance<F>(p, c0, 0, FD0, ring0, p.slot0, full0, FD0);
   }
   __syncthreads();
+  if (issue1) advance<F>(p, cc, 1, FD1, ring1, p.slot1, full1, FD1);
+  if (issue0) advance<F>(p, cc, 0, FD0, ring0, p.slot0, full0, FD0);
 
   uint32_t k1 = 0, k0 = 0;   // loads consumed (and released) before the current item
   bool aborted = false;
@@ -427,26 +442,27 @@ __global__ void __launch_bounds__(FNCT, 1) k_fused_or(const FusedParams p) {
         aborted = true;
         break;
       }
-      if (ct == 0) {
-        // released by this step: odd plane t-2 and even plane t-3 (every slot
-        // of the item after its last step); refill them
-        const bool last = j == nsteps - 1;
-        const uint32_t rel1 = k1 + (last ? (uint32_t)nsteps + 1u : (uint32_t)j);
-        const uint32_t rel0 = k0 + (last ? (uint32_t)nsteps - 1u : (uint32_t)max(0, j - 2));
-        advance<F>(p, c1, 1, rel1 + FD1, ring1, p.slot1, full1, FD1);
-        advance<F>(p, c0, 0, rel0 + FD0, ring0, p.slot0, full0, FD0);
+      // released by this step: odd plane t-2 and even plane t-3 (every slot of
+      // the item after its last step); refill them
+      if (issue1) {
+        const uint32_t rel1 = k1 + (j == nsteps - 1 ? (uint32_t)nsteps + 1u : (uint32_t)j);
+        advance<F>(p, cc, 1, rel1 + FD1, ring1, p.slot1, full1, FD1);
+      }
+      if (issue0) {
+        const uint32_t rel0 = k0 + (j == nsteps - 1 ? (uint32_t)nsteps - 1u : (uint32_t)max(0, j - 2));
+        advance<F>(p, cc, 0, rel0 + FD0, ring0, p.slot0, full0, FD0);
       }
     }
 #undef HSG_FUSED_RECS
     k1 += nsteps + 1;
     k0 += nsteps - 1;
   }
-  if (ct == 0 && aborted) {
+  if (aborted && (issue1 || issue0)) {
     // wind down: let the copies still in flight land before the block exits
-    for (uint32_t k = c1.k > (uint32_t)FD1 ? c1.k - FD1 : 0u; k < c1.k; ++k)
-      mbar_wait(full1 + k % FD1, (k / FD1) & 1u, p.timeout_ns);
-    for (uint32_t k = c0.k > (uint32_t)FD0 ? c0.k - FD0 : 0u; k < c0.k; ++k)
-      mbar_wait(full0 + k % FD0, (k / FD0) & 1u, p.timeout_ns);
+    const uint32_t D = issue1 ? FD1 : FD0;
+    uint64_t* full = issue1 ? full1 : full0;
+    for (uint32_t k = cc.k > D ? cc.k - D : 0u; k < cc.k; ++k)
+      mbar_wait(full + k % D, (k / D) & 1u, p.timeout_ns);
   }
 }
 
