@@ -40,6 +40,7 @@ constexpr int FD0 = FUSED_EVEN_SLOTS;   // even-site plane slots
 constexpr int FCW = FUSED_CONSUMER_WARPS;
 constexpr int FNCT = FCW * 32;  // consumer threads
 constexpr int FMAXI = FUSED_SITES_PER_THREAD;   // sites per thread and step (host-checked)
+constexpr int FUSED_CURSOR_OFFSET = 128;         // the two copy cursors in the shared-memory head
 
 __device__ __forceinline__ void consumer_bar() {
   asm volatile("bar.sync 1, %0;" ::"n"(FNCT) : "memory");
@@ -286,6 +287,9 @@ struct FSite {
   bool out;            // even sites: the row is the block's own (written out)
 };
 
+static_assert((FD1 + FD0) * 8 + 4 <= FUSED_CURSOR_OFFSET, "mbarriers overlap the copy cursors");
+static_assert(FUSED_CURSOR_OFFSET + 2 * sizeof(CopyCursor) <= FUSED_SMEM_HEAD, "copy cursors overlap the rings");
+
 template <int F, bool J16>
 __global__ void __launch_bounds__(FNCT, 1) k_fused_or(const FusedParams p) {
   constexpr int CH = FmtInfo<F>::CHUNK, PL = FmtInfo<F>::PLANES;
@@ -297,10 +301,15 @@ __global__ void __launch_bounds__(FNCT, 1) k_fused_or(const FusedParams p) {
   unsigned char* ring1 = smem + FUSED_SMEM_HEAD;
   unsigned char* ring0 = ring1 + (size_t)FD1 * p.slot1;
   const int ct = threadIdx.x;
-  // copy cursors: odd planes issued by thread 0, even planes by thread 32
+  // copy cursors (in shared memory: only their two threads use them): odd
+  // planes issued by thread 0, even planes by thread 32
   const bool issue1 = ct == 0, issue0 = ct == 32;
-  CopyCursor cc{};
-  cc.it = (int)blockIdx.x;
+  CopyCursor& cc = reinterpret_cast<CopyCursor*>(smem + FUSED_CURSOR_OFFSET)[issue1 ? 0 : 1];
+  if (issue1 || issue0) {
+    cc.it = (int)blockIdx.x;
+    cc.n = 0;
+    cc.k = 0u;
+  }
   if (ct == 0) {
     for (int k = 0; k < FD1; ++k) mbar_init(full1 + k, 1);
     for (int k = 0; k < FD0; ++k) mbar_init(full0 + k, 1);

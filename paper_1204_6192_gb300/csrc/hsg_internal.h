@@ -185,7 +185,7 @@ cudaError_t launch_multihit(int fmt, bool j16, bool fast, int tile, const Multih
 // of rows [y0, y0 + ny) (ny = L: the whole plane) over the planes [za, zb).
 constexpr int FUSED_CONSUMER_WARPS = 32;
 constexpr int FUSED_THREADS = FUSED_CONSUMER_WARPS * 32;
-constexpr int FUSED_SMEM_HEAD = 256;     // mbarriers and the abort flag
+constexpr int FUSED_SMEM_HEAD = 384;     // mbarriers, the abort flag and the two copy cursors
 constexpr int FUSED_ODD_SLOTS = 6, FUSED_EVEN_SLOTS = 5;
 constexpr int FUSED_SITES_PER_THREAD = 1;                        // per step (even + odd sites)
 constexpr int FUSED_MAX_SITES = FUSED_SITES_PER_THREAD * FUSED_THREADS;
