@@ -86,6 +86,7 @@ struct Rec {
   // FP16 records: the 12 halves as three 8-byte words; FP32: three float4
   typename std::conditional<J16, uint2, float4>::type w[3];
 };
+static_assert(sizeof(Rec<true>) == 24 && sizeof(Rec<false>) == 48, "one record per storage site");
 
 template <bool J16>
 __device__ __forceinline__ void load_rec(const void* rec, long long idx, Rec<J16>& r) {
@@ -276,15 +277,13 @@ __device__ __forceinline__ void advance(const FusedParams& p, CopyCursor& c, int
 // One of a thread's sites in the current item (fixed for the whole item; the
 // plane changes from step to step).
 struct FSite {
-  int kind;            // -1: none, 0: even site (slot row r0), 1: odd site (band row r)
-  uint32_t own;        // byte offset of its chunk in its own slot (plane 0)
-  uint32_t row;        // byte offset of its row in the neighbour slots
-  uint32_t yp, ym;     // byte offsets of the rows y + 1, y - 1 in the neighbour slots
-  int xh;              // half-x of the site
-  int pb;              // x parity of the site at plane t: (pb + t) & 1
-  long long ss;        // storage site in the plane-0 layout, without the plane term
-  long long rec;       // record index, without the plane term
-  bool out;            // even sites: the row is the block's own (written out)
+  int kind;                 // -1: none, 0: even site, 1: odd site
+  uint32_t own;             // byte offset of its chunk in its own slot (component 0)
+  uint32_t xo[2], xm[2];    // byte offsets of its +x and -x neighbours (site x parity 0, 1)
+  uint32_t yp, ym, zc;      // ... of its +y, -y neighbours and of itself in the z-neighbour slots
+  int pb;                   // x parity of the site at plane t: (pb + t) & 1
+  long long ss;             // storage site without the plane term
+  bool out;                 // even sites: the row is the block's own (written out)
 };
 
 static_assert((FD1 + FD0) * 8 + 4 <= FUSED_CURSOR_OFFSET, "mbarriers overlap the copy cursors");
@@ -294,6 +293,7 @@ template <int F, bool J16>
 __global__ void __launch_bounds__(FNCT, 1) k_fused_or(const FusedParams p) {
   constexpr int CH = FmtInfo<F>::CHUNK, PL = FmtInfo<F>::PLANES;
   using Chunk = typename FmtInfo<F>::Chunk;
+  using RecT = Rec<J16>;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* full1 = reinterpret_cast<uint64_t*>(smem);
   uint64_t* full0 = full1 + FD1;
@@ -331,10 +331,9 @@ __global__ void __launch_bounds__(FNCT, 1) k_fused_or(const FusedParams p) {
     const uint32_t RB = (uint32_t)Lh * CH;
     const uint32_t pb1 = (uint32_t)f.R1 * RB, pb0 = (uint32_t)f.R0 * RB;
     const int nP0 = f.R0 * Lh, nP1 = f.ny * Lh;
-    const long long gstride = (long long)sd.N * CH;
     const long long ps = sd.plane_stride;
-    unsigned char* dstg = p.dst + sd.spin_off + f.g * gstride;
-    const long long half = sd.N >> 1;
+    unsigned char* dstg = p.dst + sd.spin_off + (long long)f.g * sd.N * CH;
+    const long long rbase = sd.rec_off;
     const long long plane_sites = (long long)Lh * L;
     // this thread's sites: the even sites of the slot rows first, then the odd
     // sites of the band rows
@@ -346,101 +345,110 @@ __global__ void __launch_bounds__(FNCT, 1) k_fused_or(const FusedParams p) {
       q.kind = i < nP0 ? 0 : (i < nP0 + nP1 ? 1 : -1);
       if (q.kind == 1) i -= nP0;
       const int rr = (int)((__umulhi((uint32_t)i, sd.fdLh_m) + (uint32_t)i) >> sd.fdLh_s);
-      q.xh = i - rr * Lh;
-      // rn: the site's row in the slots it reads (odd slots for even sites and vice versa)
+      const int xh = i - rr * Lh;
+      // rown: the site's row in the slots it reads (odd slots for even sites and
+      // vice versa); rowo: its row in its own slot
       const int rown = q.kind == 0 ? rr + (f.hp1 - f.hp0) : rr + f.hp0;
-      const int rowo = q.kind == 0 ? rr : rr + f.hp1;        // its row in its own slot
+      const int rowo = q.kind == 0 ? rr : rr + f.hp1;
       int ryp = rown + 1, rym = rown - 1;
       if (f.full) {
         if (ryp == L) ryp = 0;
         if (rym < 0) rym = L - 1;
       }
-      q.own = (uint32_t)rowo * RB + (uint32_t)q.xh * CH;
-      q.row = (uint32_t)rown * RB;
-      q.yp = (uint32_t)ryp * RB + (uint32_t)q.xh * CH;
-      q.ym = (uint32_t)rym * RB + (uint32_t)q.xh * CH;
+      q.own = (uint32_t)rowo * RB + (uint32_t)xh * CH;
+      q.zc = (uint32_t)rown * RB + (uint32_t)xh * CH;
+      q.yp = (uint32_t)ryp * RB + (uint32_t)xh * CH;
+      q.ym = (uint32_t)rym * RB + (uint32_t)xh * CH;
+#pragma unroll
+      for (int o = 0; o < 2; ++o) {
+        // x = 2 xh + o: the +x neighbour has half-x xh + o, the -x neighbour xh + o - 1
+        const int xp = xh + o == Lh ? 0 : xh + o;
+        const int xm = xh + o - 1 < 0 ? Lh - 1 : xh + o - 1;
+        q.xo[o] = (uint32_t)rown * RB + (uint32_t)xp * CH;
+        q.xm[o] = (uint32_t)rown * RB + (uint32_t)xm * CH;
+      }
       const int y = q.kind == 0 ? wrap(f.y0 - f.hp0 + rr, L) : f.y0 + rr;
       // x = 2 xh + ((y + z + parity) & 1); the odd sites sit on plane t - 2
       q.pb = q.kind == 0 ? y : y - 1;
       q.out = q.kind == 0 && rr >= f.hp0 && rr < f.hp0 + f.ny;
-      q.ss = (q.kind == 1 ? half : 0) + (long long)Lh * y + q.xh;
-      q.rec = sd.rec_off + q.ss;
+      q.ss = (q.kind == 1 ? (sd.N >> 1) : 0) + (long long)Lh * y + xh;
     }
-    Rec<J16> rc[FMAXI], rn[FMAXI];
-    // couplings and field of the sites of step j: even sites on plane t, odd on t - 2
-#define HSG_FUSED_RECS(j_, dst_)                                                   \
-    {                                                                              \
-      const int t_ = f.za - 1 + (j_);                                              \
-      const long long z0_ = plane_sites * wrap(t_, L), z1_ = plane_sites * wrap(t_ - 2, L); \
-      _Pragma("unroll") for (int k = 0; k < FMAXI; ++k) {                          \
-        if (st[k].kind == 0 && t_ <= f.zb) load_rec<J16>(p.rec, st[k].rec + z0_, dst_[k]); \
-        if (st[k].kind == 1 && t_ - 2 >= f.za) load_rec<J16>(p.rec, st[k].rec + z1_, dst_[k]); \
-      }                                                                            \
-    }
-    HSG_FUSED_RECS(0, rn)
+    // planes of the step (wrapped): t for the even sites, t - 2 for the odd ones
+    int z0 = wrap(f.za - 1, L), z1 = wrap(f.za - 3 + L, L);
+    // ring slots, rotated one plane per step: odd planes t-2 (own of the odd
+    // sites), t-1, t, t+1; even planes t-3, t-2, t-1 and t (own of the even sites)
+    uint32_t i1 = (k1 + 2) % FD1, ph1 = ((k1 + 2) / FD1) & 1u;   // slot, phase of odd plane t+1
+    uint32_t i0 = k0 % FD0, ph0 = (k0 / FD0) & 1u;               // slot, phase of even plane t
+    const unsigned char* o_own = ring1;
+    const unsigned char* o_m = ring1 + (size_t)(k1 % FD1) * p.slot1;
+    const unsigned char* o_c = ring1 + (size_t)((k1 + 1) % FD1) * p.slot1;
+    const unsigned char* o_p = ring1 + (size_t)i1 * p.slot1;
+    const unsigned char* e_m = ring0;
+    const unsigned char* e_c = ring0;
+    const unsigned char* e_p = ring0;
+    unsigned char* e_t = ring0 + (size_t)i0 * p.slot0;
+    RecT rc[FMAXI], rn[FMAXI];
+    // couplings and field of the sites of a step (even sites on plane za, odd on za-2 ... )
+#pragma unroll
+    for (int k = 0; k < FMAXI; ++k)
+      if (st[k].kind == 0) load_rec<J16>(p.rec, rbase + st[k].ss + plane_sites * z0, rn[k]);
     for (int j = 0; j < nsteps; ++j) {
       const int t = f.za - 1 + j;
       const bool do0 = t <= f.zb, do1 = t - 2 >= f.za;
 #pragma unroll
       for (int k = 0; k < FMAXI; ++k) rc[k] = rn[k];
-      if (j + 1 < nsteps) HSG_FUSED_RECS(j + 1, rn)
+      const int zn0 = z0 + 1 == L ? 0 : z0 + 1, zn1 = z1 + 1 == L ? 0 : z1 + 1;
+      if (j + 1 < nsteps) {
+        // next step's records: even sites on plane t + 1, odd sites on plane t - 1
+        const long long a0 = plane_sites * zn0, a1 = plane_sites * zn1;
+#pragma unroll
+        for (int k = 0; k < FMAXI; ++k) {
+          if (st[k].kind == 0 && t + 1 <= f.zb) load_rec<J16>(p.rec, rbase + st[k].ss + a0, rn[k]);
+          if (st[k].kind == 1 && t - 1 >= f.za) load_rec<J16>(p.rec, rbase + st[k].ss + a1, rn[k]);
+        }
+      }
       bool ok = true;
       if (do0) {
         if (j == 0) {
           for (uint32_t m = 0; m < 2; ++m)
             ok = ok && mbar_wait(full1 + (k1 + m) % FD1, ((k1 + m) / FD1) & 1u, p.timeout_ns);
         }
-        const uint32_t ka = k1 + j + 2, kb = k0 + j;
-        ok = ok && mbar_wait(full1 + ka % FD1, (ka / FD1) & 1u, p.timeout_ns);
-        ok = ok && mbar_wait(full0 + kb % FD0, (kb / FD0) & 1u, p.timeout_ns);
+        ok = ok && mbar_wait(full1 + i1, ph1, p.timeout_ns);
+        ok = ok && mbar_wait(full0 + i0, ph0, p.timeout_ns);
       }
       if (!ok) {
         atomicOr(p.err, 1u);
         *s_abort = 1;
       }
       if (!*s_abort) {
-        // slots of this step: odd planes t-1, t, t+1 and even plane t (even
-        // sites); even planes t-3, t-2, t-1 and odd plane t-2 (odd sites)
-        const unsigned char* o_m = ring1 + (size_t)((k1 + j) % FD1) * p.slot1;
-        const unsigned char* o_c = ring1 + (size_t)((k1 + j + 1) % FD1) * p.slot1;
-        const unsigned char* o_p = ring1 + (size_t)((k1 + j + 2) % FD1) * p.slot1;
-        unsigned char* e_t = ring0 + (size_t)((k0 + j) % FD0) * p.slot0;
-        const unsigned char* e_m = ring0 + (size_t)((k0 + j + FD0 - 3) % FD0) * p.slot0;
-        const unsigned char* e_c = ring0 + (size_t)((k0 + j + FD0 - 2) % FD0) * p.slot0;
-        const unsigned char* e_p = ring0 + (size_t)((k0 + j + FD0 - 1) % FD0) * p.slot0;
-        const unsigned char* o_own = ring1 + (size_t)((k1 + j + FD1 - 1) % FD1) * p.slot1;
+        const long long d0 = plane_sites * z0, d1 = plane_sites * z1;
         const bool write0 = t >= f.za && t < f.zb;
-        const long long z0 = plane_sites * wrap(t, L), z1 = plane_sites * wrap(t - 2, L);
 #pragma unroll
         for (int k = 0; k < FMAXI; ++k) {
           const FSite& q = st[k];
           const bool even = q.kind == 0;
           if (even ? !do0 : (q.kind != 1 || !do1)) continue;
           const int o = (q.pb + t) & 1;
-          int xp = q.xh + o, xm = q.xh + o - 1;
-          if (xp == Lh) xp = 0;
-          if (xm < 0) xm = Lh - 1;
           const unsigned char* nc_ = even ? o_c : e_c;   // same plane
           const unsigned char* np_ = even ? o_p : e_p;   // + z
           const unsigned char* nm_ = even ? o_m : e_m;   // - z
           const uint32_t pbn = even ? pb1 : pb0, pbo = even ? pb0 : pb1;
-          const uint32_t rc_ = q.row + (uint32_t)q.xh * CH;
           Chunk nc[6][PL];
-          lds_chunks<F>(nc_ + q.row + xp * CH, pbn, nc[0]);
-          lds_chunks<F>(nc_ + q.row + xm * CH, pbn, nc[1]);
+          lds_chunks<F>(nc_ + (o ? q.xo[1] : q.xo[0]), pbn, nc[0]);
+          lds_chunks<F>(nc_ + (o ? q.xm[1] : q.xm[0]), pbn, nc[1]);
           lds_chunks<F>(nc_ + q.yp, pbn, nc[2]);
           lds_chunks<F>(nc_ + q.ym, pbn, nc[3]);
-          lds_chunks<F>(np_ + rc_, pbn, nc[4]);
-          lds_chunks<F>(nm_ + rc_, pbn, nc[5]);
+          lds_chunks<F>(np_ + q.zc, pbn, nc[4]);
+          lds_chunks<F>(nm_ + q.zc, pbn, nc[5]);
           unsigned char* own = (even ? e_t : const_cast<unsigned char*>(o_own)) + q.own;
           Chunk c[PL];
           lds_chunks<F>(own, pbo, c);
           or_chunk<F, J16>(nc, c, rc[k]);
           if (even) sts_chunks<F>(own, pb0, c);
           if (even ? (write0 && q.out) : true) {
-            const long long ss = q.ss + (even ? z0 : z1);
+            unsigned char* g = dstg + (q.ss + (even ? d0 : d1)) * CH;
 #pragma unroll
-            for (int pl = 0; pl < PL; ++pl) *reinterpret_cast<Chunk*>(dstg + pl * ps + ss * CH) = c[pl];
+            for (int pl = 0; pl < PL; ++pl) *reinterpret_cast<Chunk*>(g + pl * ps) = c[pl];
           }
         }
         // the even slot is refilled by bulk copies (async proxy) once released
@@ -461,8 +469,26 @@ __global__ void __launch_bounds__(FNCT, 1) k_fused_or(const FusedParams p) {
         const uint32_t rel0 = k0 + (j == nsteps - 1 ? (uint32_t)nsteps - 1u : (uint32_t)max(0, j - 2));
         advance<F>(p, cc, 0, rel0 + FD0, ring0, p.slot0, full0, FD0);
       }
+      // next step: planes and slots move by one
+      z0 = zn0;
+      z1 = zn1;
+      o_own = o_m;
+      o_m = o_c;
+      o_c = o_p;
+      if (++i1 == FD1) {
+        i1 = 0;
+        ph1 ^= 1u;
+      }
+      o_p = ring1 + (size_t)i1 * p.slot1;
+      e_m = e_c;
+      e_c = e_p;
+      e_p = e_t;
+      if (++i0 == FD0) {
+        i0 = 0;
+        ph0 ^= 1u;
+      }
+      e_t = ring0 + (size_t)i0 * p.slot0;
     }
-#undef HSG_FUSED_RECS
     k1 += nsteps + 1;
     k0 += nsteps - 1;
   }
