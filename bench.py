@@ -614,12 +614,16 @@ def schedule_of(info, short=False):
 
 
 def launches_per_step(info, wl):
+    """Kernel launches of one step: the sweeps (two per sweep and pass, one per
+    fused sweep), the energy sums' first level and the PT pass with the sums'
+    last level (one launch for up to 4096 systems in all, else two)."""
     if info.variant == 2:
         return 1
+    tail = 2 if info.n_samples * info.Wp <= 4096 else 3
     if info.sweep_kernel == 2 and info.n_passes == 1:
         pairs = (wl.n_or - 1) // 2
-        return 2 * wl.n_hb + 2 * pairs + 2 * (wl.n_or - 2 * pairs) + 3
-    return info.n_passes * 2 * (wl.n_hb + wl.n_or) + 3
+        return 2 * wl.n_hb + 2 * pairs + 2 * (wl.n_or - 2 * pairs) + tail
+    return info.n_passes * 2 * (wl.n_hb + wl.n_or) + tail
 
 
 def roofline_entry(ctx, wl, rl, value_ns, peak, peak_kind):

@@ -448,11 +448,11 @@ hsg_status enqueue_step(hsg_ctx* c) {
     for (; k < nor; ++k) HSG_TRY(half_sweeps(c, false, nhb + k, k == nor - 1, b0, b1));
   }
   if (nor > 0) {
-    HSG_CUDA(c, launch_energy_final(energy_params(c), c->stream));
+    HSG_CUDA(c, launch_energy_final_pt(energy_params(c), pt_params(c, nhb + nor, 1), c->stream));
   } else {
     HSG_TRY(enqueue_energy(c));
+    HSG_CUDA(c, launch_pt(pt_params(c, nhb + nor, 1), c->stream));
   }
-  HSG_CUDA(c, launch_pt(pt_params(c, nhb + nor, 1), c->stream));
   return HSG_OK;
 }
 

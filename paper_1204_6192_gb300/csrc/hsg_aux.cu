@@ -186,6 +186,41 @@ cudaError_t launch_pt(const PTParams& p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// The last level of the FP64 energy sums (Eq. 1) and the PT pass (Eq. 4) in one
+// block, for steps with few systems: each warp sums the level-1 partials of its
+// systems (the same code and order as k_energy_final2), then, after a block
+// barrier, one thread per chain walks its pairs as k_pt does.  One launch
+// instead of two.
+__global__ void __launch_bounds__(1024) k_energy2_pt(const EnergyParams e, const PTParams p) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int gw = warp; gw < e.n_samples * e.Wp; gw += nw)
+    energy_final2_warp<false>(e, gw / e.Wp, gw % e.Wp, lane);
+  __syncthreads();
+  const int n_chains = p.n_samples * p.R_O;
+  for (int c = threadIdx.x; c < n_chains; c += blockDim.x) pt_chain<false>(p, c);
+  __syncthreads();
+  for (int s = threadIdx.x; s < p.n_samples; s += blockDim.x) {
+    if (!p.active[s]) continue;
+    p.counters[2 * s] += (unsigned long long)p.sweeps_per_call;
+    p.counters[2 * s + 1] += (unsigned long long)p.bump_pt;
+  }
+}
+
+bool energy_pt_folded(int n_samples, int Wp) { return (long long)n_samples * Wp <= ENERGY_PT_FOLD_SYSTEMS; }
+
+cudaError_t launch_energy_final_pt(const EnergyParams& e, const PTParams& p, cudaStream_t st) {
+  if (!energy_pt_folded(e.n_samples, e.Wp)) {
+    cudaError_t err = launch_energy_final(e, st);
+    if (err != cudaSuccess) return err;
+    return launch_pt(p, st);
+  }
+  k_energy_final1<<<dim3(e.splits, (e.Wp + 31) / 32, e.n_samples), 256, 0, st>>>(e);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  k_energy2_pt<<<1, 1024, 0, st>>>(e, p);
+  return cudaGetLastError();
+}
+
 __global__ void k_bump(unsigned long long* counters, const unsigned char* active, int n_samples,
                        int sweeps, int pts) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_samples; s += gridDim.x * blockDim.x) {

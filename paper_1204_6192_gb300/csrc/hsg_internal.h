@@ -211,6 +211,11 @@ cudaError_t launch_half_sweep(int fmt, bool hb, bool j16, bool fast, bool energy
 cudaError_t launch_energy(int fmt, bool j16, const EnergyParams& p, cudaStream_t st);
 cudaError_t launch_energy_final(const EnergyParams& p, cudaStream_t st);
 cudaError_t launch_pt(const PTParams& p, cudaStream_t st);
+// The energy sums' last level and the PT pass of a step: one launch after the
+// level-1 sums when samples x systems <= ENERGY_PT_FOLD_SYSTEMS, else two.
+constexpr long long ENERGY_PT_FOLD_SYSTEMS = 4096;
+bool energy_pt_folded(int n_samples, int Wp);
+cudaError_t launch_energy_final_pt(const EnergyParams& e, const PTParams& p, cudaStream_t st);
 // counters of the active samples += (sweeps, pts)
 cudaError_t launch_bump(unsigned long long* counters, const unsigned char* active, int n_samples,
                         int sweeps, int pts, cudaStream_t st);

@@ -59,11 +59,13 @@ def test_roofline_entry_fractions():
 
 
 def test_launches_per_step():
-    info = types.SimpleNamespace(variant=1, sweep_kernel=1, n_passes=1)
-    wl = inputs.workload("L128_fp16")        # 1 HB + 5 OR
-    assert bench.launches_per_step(info, wl) == 15
+    info = types.SimpleNamespace(variant=1, sweep_kernel=1, n_passes=1, n_samples=1, Wp=48)
+    wl = inputs.workload("L128_fp16")        # 1 HB + 5 OR, 48 systems: energies and PT folded
+    assert bench.launches_per_step(info, wl) == 12 + 2
     info.sweep_kernel = 2                    # two fused pairs, one half-sweep sweep with energies
-    assert bench.launches_per_step(info, wl) == 2 + 4 + 2 + 3
+    assert bench.launches_per_step(info, wl) == 2 + 4 + 2 + 2
+    info = types.SimpleNamespace(variant=1, sweep_kernel=1, n_passes=17, n_samples=512, Wp=32)
+    assert bench.launches_per_step(info, inputs.workload("batch512_mixedL", steps=1)) == 17 * 12 + 3
 
 
 def test_traffic_is_reported_only_for_the_profiled_source(monkeypatch):
