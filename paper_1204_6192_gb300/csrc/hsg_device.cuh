@@ -474,8 +474,13 @@ __device__ __forceinline__ void hb_poles(float a, float u1, float& dm, float& dp
       dm = __fmul_rn(-log1pf(__fmul_rn(om, em)), inv_a);
       dp = __fsub_rn(2.0f, dm);                     // accurate while cos t >= 0
       if (dm > 1.0f && a < 40.0f) {
+        // southern hemisphere: dp from its own form, and dm = 2 - dp (in [1, 2],
+        // so accurate); the direct dm cancels there when u1 is small, since
+        // 1 + (1 - u1) expm1(-2a) is then close to u1 (a = 7.7, u1 = 1.6e-5:
+        // ~1e-3 relative in dm, which reached the spin through sin t)
         const float ep = (a >= 0.35f) ? __fsub_rn(__expf(2.0f * a), 1.0f) : expm1f(2.0f * a);
         dp = __fmul_rn(log1pf(__fmul_rn(u1, ep)), inv_a);
+        dm = __fsub_rn(2.0f, dp);
       }
     }
   } else {
