@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--schedule", default="auto", choices=["auto", "two_pass", "persistent"],
                     help="step schedule: tuned at the first step (default) or fixed")
+    ap.add_argument("--sweep-kernel", default="auto", choices=["auto", "half", "fused"],
+                    help="over-relaxation sweep kernel: tuned (default), one launch per half-sweep, "
+                         "or the fused one-pass sweep")
     return ap.parse_args()
 
 
@@ -179,9 +182,11 @@ def run_ours(args, wl, torch, dev, rank, world, measure_every, do_roofline=True)
     stream = torch.cuda.Stream(device=dev)
     variant = {"auto": hsg.VARIANT_AUTO, "two_pass": hsg.VARIANT_TWO_PASS,
                "persistent": hsg.VARIANT_PERSISTENT}[getattr(args, "schedule", "auto")]
+    kernel = {"auto": hsg.SWEEP_AUTO, "half": hsg.SWEEP_HALF,
+              "fused": hsg.SWEEP_FUSED}[getattr(args, "sweep_kernel", "auto")]
     ctx = hsg.Context(wl.samples, wl.n_replicas, wl.seed + rank, precision=wl.precision,
                       j_fp16=wl.j_fp16, n_hb=wl.n_hb, n_or=wl.n_or, device=dev.index,
-                      stream=stream.cuda_stream, variant=variant)
+                      stream=stream.cuda_stream, variant=variant, sweep_kernel=kernel)
     info = ctx.info()
     spins = info.total_spins
     sweeps = wl.n_hb + wl.n_or
