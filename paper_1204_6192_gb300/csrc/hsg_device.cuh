@@ -461,17 +461,23 @@ __device__ __forceinline__ void hb_poles(float a, float u1, float& dm, float& dp
   if (a > 1e-12f) {
     const float inv_a = rcp_approx(a);
     const float om = __fsub_rn(1.0f, u1);
+    // 1 - cos t = -log(y) / a with y = 1 + (1 - u1) expm1(-2a) = u1 + (1 - u1) e^{-2a}.
+    // For a >= 0.35 y is formed as that sum of two positive terms (one fused
+    // multiply-add, no cancellation): the form 1 + (1 - u1) (e^{-2a} - 1) loses
+    // the e^{-2a} term once e^{-2a} is below half an ulp of 1 (a > ~8.7), which
+    // moved cos t by up to ~e^{-a} / a for draws near the equator (u1 ~ e^{-a}).
+    // Below a = 0.35, y is close to 1 and log1p of (1 - u1) expm1(-2a) keeps
+    // its accuracy (for a < ~3e-8, e^{-2a} - 1 would be exactly 0 and the spin
+    // would snap onto h).
     if (FAST) {
-      // below a = 0.35, exp(-2a) - 1 cancels (for a < ~3e-8 it is exactly 0 and
-      // the spin would snap onto h): expm1 there, as in the accurate branch
-      const float em = (a >= 0.35f) ? __fsub_rn(__expf(-2.0f * a), 1.0f) : expm1f(-2.0f * a);
-      dm = __fmul_rn(-__logf(__fmaf_rn(om, em, 1.0f)), inv_a);
+      dm = (a >= 0.35f) ? __fmul_rn(-__logf(__fmaf_rn(om, __expf(-2.0f * a), u1)), inv_a)
+                        : __fmul_rn(-__logf(__fmaf_rn(om, expm1f(-2.0f * a), 1.0f)), inv_a);
       dp = __fsub_rn(2.0f, dm);
     } else {
-      // exp(-2a) - 1 has no cancellation for a >= 0.35; the hardware exp's
-      // relative error (<~ 2a * 6e-8) enters 1 - cos t as <~ 1.2e-7 absolute
-      const float em = (a >= 0.35f) ? __fsub_rn(__expf(-2.0f * a), 1.0f) : expm1f(-2.0f * a);
-      dm = __fmul_rn(-log1pf(__fmul_rn(om, em)), inv_a);
+      // the hardware exp's relative error (<~ 2a * 6e-8) enters 1 - cos t as
+      // <~ 1.2e-7 absolute
+      dm = (a >= 0.35f) ? __fmul_rn(-logf(__fmaf_rn(om, __expf(-2.0f * a), u1)), inv_a)
+                        : __fmul_rn(-log1pf(__fmul_rn(om, expm1f(-2.0f * a))), inv_a);
       dp = __fsub_rn(2.0f, dm);                     // accurate while cos t >= 0
       if (dm > 1.0f && a < 40.0f) {
         // southern hemisphere: dp from its own form, and dm = 2 - dp (in [1, 2],

@@ -302,6 +302,32 @@ def test_field_dominated_trajectory_ten_sweeps_within_1e5():
     assert max(dev) < TOL_FP32, dev
 
 
+def test_heat_bath_in_a_strong_field_near_the_equator():
+    """Heat-bath draws at a = beta |h| = 8 ... 11 (no couplings, a unit field of
+    random direction, T = 1/11 ... 1/8), where exp(-2a) is below half an ulp of
+    1: draws near the equator (u1 ~ exp(-a)) need the (1 - u1) exp(-2a) term of
+    the inverse CDF, which a binary32 1 + (1 - u1)(exp(-2a) - 1) loses (up to
+    1.4e-5 in cos t at a = 9).  Without couplings every site is independent, so
+    three sweeps of 16^3 sites x 8 systems (~10^5 draws, dozens near the equator
+    at each a) compare move by move: every component within 2e-6."""
+    L = 16
+    rng = np.random.default_rng(23)
+    H = inputs.sphere_field(L, 1.0, rng)
+    smp = f32(inputs.Sample(L=L, J=np.zeros((L ** 3, 3)), H=H, temps=1.0 / np.array([11.0, 10.0, 9.0, 8.0])))
+    ctx = hsg.Context([smp], 2, 31)
+    orc = oracle.OracleSim([smp], 2, 31)
+    dev = []
+    for _ in range(3):
+        for o, st in zip(orc.samples, ctx.get_spins()):
+            o.s = st.astype(np.float64)
+        ctx.sweep_hb(1)
+        orc.sweep_hb(1)
+        dev.append(max(np.abs(g - o).max() for g, o in zip(ctx.get_spins(), orc.spins())))
+    ctx.close()
+    print(f"\n[strong field] max |GPU - oracle| per heat-bath sweep: {np.array2string(np.array(dev), precision=2)}")
+    assert max(dev) < 2e-6, dev
+
+
 def test_ragged_system_count_and_batch():
     """W = 3 (padded to 8 lanes) and a batch of three lattice sizes in one context."""
     samples = [inputs.small_sample(L, n_temps=3, h_r=0.1, disorder_seed=10 + L) for L in (4, 6, 8)]
