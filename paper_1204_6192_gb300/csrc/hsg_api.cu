@@ -42,6 +42,10 @@ struct hsg_ctx {
   // device state
   unsigned char* spins = nullptr;
   size_t spin_bytes = 0;
+  // packed formats: the opposite parity decoded to binary32 before each half-sweep
+  bool dec_once = false;
+  unsigned char* dec = nullptr;
+  size_t dec_bytes = 0;
   void* rec = nullptr;
   size_t rec_bytes = 0;
   SampleDev* d_sd = nullptr;
@@ -205,6 +209,7 @@ SweepParams sweep_params(hsg_ctx* c, int parity, int sweep_offset) {
   p.epart = c->d_epart;
   p.n_blocks = c->n_sweep_blocks;
   p.blk_base = 0;
+  p.dec = c->dec;
   uint32_t k0 = c->seed_lo, k1 = c->seed_hi;
   for (int r = 0; r < 10; ++r) {
     p.rk[2 * r] = k0;
@@ -283,8 +288,10 @@ hsg_status half_sweeps(hsg_ctx* c, bool hb, int sweep_offset, bool energy = fals
   for (int parity = 0; parity < 2; ++parity) {
     SweepParams p = sweep_params(c, parity, sweep_offset);
     p.blk_base = b0;
-    HSG_CUDA(c, launch_half_sweep(c->fmt, hb, c->j16, c->opt.fast_math != 0, energy, p, b1 - b0,
-                                  c->stream));
+    // packed formats: decode the other parity once for the six neighbour loads
+    if (c->dec_once) HSG_CUDA(c, launch_decode_parity(c->fmt, p, 1 - parity, b1 - b0, c->stream));
+    HSG_CUDA(c, launch_half_sweep(c->fmt, hb, c->j16, c->opt.fast_math != 0, energy, c->dec_once, p,
+                                  b1 - b0, c->stream));
   }
   return HSG_OK;
 }
@@ -874,6 +881,11 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
       for (int s0 = 0; s0 < d.N; s0 += 256) conv_blocks.push_back(make_int4(s, g, s0, 0));
     size_t sb = (size_t)c->PL * d.plane_stride;
     spin_off += (sb + 255) / 256 * 256;
+    if (fmt_decodes_once(fmt)) {
+      d.dec_off = (long long)c->dec_bytes;
+      d.dec_plane_stride = (long long)(d.N / 2) * Wp * 4;
+      c->dec_bytes += ((size_t)3 * d.dec_plane_stride + 255) / 256 * 256;
+    }
     rec_off += (size_t)d.N;
     c->sd.push_back(d);
     c->xyz_off.push_back(xyz);
@@ -935,6 +947,10 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   st = dev_alloc(c, &(ptr), (bytes));           \
   if (st != HSG_OK) return cleanup_fail(st);
   HSG_ALLOC(c->spins, c->spin_bytes);
+  c->dec_once = fmt_decodes_once(fmt);
+  if (c->dec_once) {
+    HSG_ALLOC(c->dec, c->dec_bytes);
+  }
   HSG_ALLOC(c->rec, c->rec_bytes);
   HSG_ALLOC(c->d_sd, sizeof(SampleDev) * n_samples);
   HSG_ALLOC(c->d_sweep_blocks, sizeof(int4) * max_sweep_blocks);

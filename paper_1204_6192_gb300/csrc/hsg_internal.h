@@ -43,6 +43,9 @@ struct SampleDev {
   long long rec_off;        // record index of storage site 0
   int sys_base;             // global id of system 0 = sample * Wp
   int blk0, blk1;           // the sample's blocks in the sweep block table
+  // packed formats: the opposite parity decoded to binary32 before each
+  // half-sweep, chunk layout [c][g][N/2][4] (byte offset and plane stride)
+  long long dec_off, dec_plane_stride;
 };
 
 struct SweepParams {
@@ -61,6 +64,7 @@ struct SweepParams {
   int n_blocks;
   int blk_base;             // block table entry of launch block 0 (a pass's first block)
   uint32_t rk[20];          // Philox round keys of the seed
+  const unsigned char* dec; // packed formats: the opposite parity as binary32 (see SampleDev)
 };
 
 struct EnergyParams {
@@ -205,9 +209,17 @@ cudaError_t prepare_fused(int fmt, bool j16, size_t smem, int* blocks_per_sm);
 cudaError_t launch_fused(int fmt, bool j16, const FusedParams& p, int grid, size_t smem,
                          cudaStream_t st);
 
-// launchers (hsg_kernels*.cu)
-cudaError_t launch_half_sweep(int fmt, bool hb, bool j16, bool fast, bool energy,
+// The packed spin formats (one or two 32-bit words per system) decode each
+// neighbour spin once into a binary32 buffer before a half-sweep instead of
+// at every one of its six uses.
+inline bool fmt_decodes_once(int fmt) { return fmt == FMT_ANG16 || fmt == FMT_OCT16 || fmt == FMT_YX4; }
+
+// launchers (hsg_kernels*.cu).  dec: the half-sweep reads its neighbours from
+// p.dec, which launch_decode_parity filled with parity 1 - p.parity.
+cudaError_t launch_half_sweep(int fmt, bool hb, bool j16, bool fast, bool energy, bool dec,
                               const SweepParams& p, int n_blocks, cudaStream_t st);
+cudaError_t launch_decode_parity(int fmt, const SweepParams& p, int parity, int n_blocks,
+                                 cudaStream_t st);
 cudaError_t launch_energy(int fmt, bool j16, const EnergyParams& p, cudaStream_t st);
 cudaError_t launch_energy_final(const EnergyParams& p, cudaStream_t st);
 cudaError_t launch_pt(const PTParams& p, cudaStream_t st);

@@ -11,8 +11,9 @@ namespace hsg {
 // One block's share of a half-sweep: virtual block `bidx` of the sweep block
 // table.  CG: every load of data written during the launch bypasses L1 (for
 // the persistent kernel, whose blocks see each other's writes across grid
-// barriers).  esum: shared memory [SWEEP_BS / 32][GPT * VEC] (EN only).
-template <int F, bool HB, bool J16, bool FAST, bool EN, bool CG>
+// barriers).  DEC: the neighbours come decoded from p.dec (packed formats).
+// esum: shared memory [SWEEP_BS / 32][GPT * VEC] (EN only).
+template <int F, bool HB, bool J16, bool FAST, bool EN, bool CG, bool DEC = false>
 __device__ __forceinline__ void sweep_block(const SweepParams& p, int bidx, float* esum) {
   constexpr int VEC = FmtInfo<F>::VEC, PL = FmtInfo<F>::PLANES;
   using Chunk = typename FmtInfo<F>::Chunk;
@@ -55,14 +56,25 @@ __device__ __forceinline__ void sweep_block(const SweepParams& p, int bidx, floa
                       (unsigned long long)p.sweep_offset)
          : 0u;
 
+  // DEC: the decoded opposite parity, chunk (g, h') at dec + (g N/2 + h') 16 bytes
+  const unsigned char* decb = DEC ? p.dec + sd.dec_off : nullptr;
+  const uint32_t ob = (uint32_t)(1 - p.parity) * half_n;
+
   for (int g = g0; g < g1; ++g) {
     float e[VEC];
 #pragma unroll
     for (int v = 0; v < VEC; ++v) e[v] = 0.0f;
     if (active) {
-      Chunk nc[6][PL];
+      Chunk nc[DEC ? 1 : 6][PL];
+      uint4 ncd[DEC ? 6 : 1][3];
       unsigned char* own_p;
-      if constexpr (EN) {
+      if constexpr (DEC) {
+        const unsigned char* dg = decb + (long long)g * half_n * 16;
+#pragma unroll
+        for (int n = 0; n < 6; ++n)
+          load_chunks<FMT_F32, CG ? LD_CG : LD_RO>(dg + (size_t)(gm.nb[n] - ob) * 16, sd.dec_plane_stride, ncd[n]);
+        own_p = p.spins + sd.spin_off + (long long)g * gstride + (size_t)gm.own * FmtInfo<F>::CHUNK;
+      } else if constexpr (EN) {
         const long long dg = (long long)(g - g0) * gstride;
 #pragma unroll
         for (int n = 0; n < 6; ++n) load_chunks<F, CG ? LD_CG : LD_RO>(base + nb_off[n] + dg, ps, nc[n]);
@@ -101,7 +113,8 @@ __device__ __forceinline__ void sweep_block(const SweepParams& p, int bidx, floa
       } else {
         {
           Spins<VEC> nb;
-          decode<F>(nc[0], nb);
+          if constexpr (DEC) decode<FMT_F32>(ncd[0], nb);
+          else decode<F>(nc[0], nb);
           const float2 jj = f2(j6[0]);
 #pragma unroll
           for (int k = 0; k < VEC / 2; ++k) {
@@ -113,7 +126,8 @@ __device__ __forceinline__ void sweep_block(const SweepParams& p, int bidx, floa
 #pragma unroll
         for (int n = 1; n < 6; ++n) {
           Spins<VEC> nb;
-          decode<F>(nc[n], nb);
+          if constexpr (DEC) decode<FMT_F32>(ncd[n], nb);
+          else decode<F>(nc[n], nb);
           const float2 jj = f2(j6[n]);
 #pragma unroll
           for (int k = 0; k < VEC / 2; ++k) {

@@ -657,11 +657,14 @@ def test_invalid_arguments_rejected():
     ctx.close()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "angle16", "oct16", "yx4"])
 def test_persistent_schedule_bit_identical(precision):
     """The persistent step kernel (one cooperative launch, grid barriers) runs
     the same arithmetic as the per-phase graph: identical spins, energies and
-    permutations, here for a batch of three lattice sizes."""
+    permutations, here for a batch of three lattice sizes.  For the packed
+    formats the graph decodes each neighbour parity once into binary32 before
+    a half-sweep while the persistent kernel decodes at every use, so this also
+    checks that the two give the same values."""
     samples = [inputs.small_sample(L, n_temps=4, h_r=0.2, disorder_seed=L) for L in (4, 8, 12)]
     out = {}
     for variant in (hsg.VARIANT_TWO_PASS, hsg.VARIANT_PERSISTENT):
@@ -681,9 +684,10 @@ def test_persistent_schedule_bit_identical(precision):
     assert a[3] == b[3] == 30 and a[4] == b[4] == 5
 
 
-@pytest.mark.parametrize("variant", [hsg.VARIANT_TWO_PASS, hsg.VARIANT_PERSISTENT])
+@pytest.mark.parametrize("variant,precision", [(hsg.VARIANT_TWO_PASS, "fp16"), (hsg.VARIANT_PERSISTENT, "fp16"),
+                                               (hsg.VARIANT_TWO_PASS, "oct16")])
 @pytest.mark.parametrize("pass_bytes", [1, 40000])
-def test_system_blocked_passes_bit_identical(variant, pass_bytes):
+def test_system_blocked_passes_bit_identical(variant, precision, pass_bytes):
     """Sweeping the systems pass by pass (each pass a range of 4-system chunks
     swept through the whole step before the next) computes the same step as one
     pass: systems are independent and the random numbers are keyed by site,
@@ -692,7 +696,7 @@ def test_system_blocked_passes_bit_identical(variant, pass_bytes):
     samples = [inputs.small_sample(L, n_temps=8, h_r=0.2, disorder_seed=L) for L in (4, 8, 12)]
     out = []
     for pb in (0, pass_bytes):
-        ctx = hsg.Context(samples, 2, 6, precision="fp16", j_fp16=True, variant=variant,
+        ctx = hsg.Context(samples, 2, 6, precision=precision, j_fp16=True, variant=variant,
                           pass_bytes=pb)
         info = ctx.info()
         assert info.pass_bytes == pb
