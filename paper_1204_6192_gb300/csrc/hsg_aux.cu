@@ -71,9 +71,9 @@ __global__ void __launch_bounds__(RED_BS) k_energy(const EnergyParams p) {
         decode<F>(nc[n], t);
 #pragma unroll
         for (int q = 0; q < VEC / 2; ++q) {
-          hf.x[q] = add2(hf.x[q], mul2(f2(j6[n]), t.x[q]));
-          hf.y[q] = add2(hf.y[q], mul2(f2(j6[n]), t.y[q]));
-          hf.z[q] = add2(hf.z[q], mul2(f2(j6[n]), t.z[q]));
+          hf.x[q] = fma2(f2(j6[n]), t.x[q], hf.x[q]);
+          hf.y[q] = fma2(f2(j6[n]), t.y[q], hf.y[q]);
+          hf.z[q] = fma2(f2(j6[n]), t.z[q], hf.z[q]);
         }
       }
       Spins<VEC> so, se;
@@ -84,9 +84,8 @@ __global__ void __launch_bounds__(RED_BS) k_energy(const EnergyParams p) {
         const float2 hx2 = add2(hf.x[q], f2(h3[0]));
         const float2 hy2 = add2(hf.y[q], f2(h3[1]));
         const float2 hz2 = add2(hf.z[q], f2(h3[2]));
-        const float2 o = add2(add2(mul2(so.x[q], hx2), mul2(so.y[q], hy2)), mul2(so.z[q], hz2));
-        const float2 e = add2(add2(mul2(se.x[q], f2(he[0])), mul2(se.y[q], f2(he[1]))),
-                              mul2(se.z[q], f2(he[2])));
+        const float2 o = dot3_2(so.x[q], so.y[q], so.z[q], hx2, hy2, hz2);
+        const float2 e = dot3_2(se.x[q], se.y[q], se.z[q], f2(he[0]), f2(he[1]), f2(he[2]));
         eo[2 * q] = -o.x;
         eo[2 * q + 1] = -o.y;
         ee[2 * q] = -e.x;

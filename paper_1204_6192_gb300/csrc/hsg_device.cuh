@@ -77,9 +77,17 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   return r;
 }
 
-// Packed binary32 pair arithmetic as PTX with an explicit rounding modifier:
-// PTX never contracts such instructions into fused multiply-adds, so every
-// kernel that inlines these helpers rounds identically.
+// Packed binary32 pair arithmetic as PTX with an explicit rounding modifier.
+// The rounding modifier does not keep the code generator from contracting a
+// packed multiply whose result feeds a packed add or subtract into one fused
+// multiply-add, and which pairs it contracts differs from kernel to kernel:
+// an over-relaxation sweep fed with neighbours decoded by an earlier launch
+// rounded its fields a few ulp away from the same sweep decoding them itself,
+// and the per-half-sweep kernel's results equal a binary32 emulation in which
+// every such pair is fused.  So no packed product in this code feeds a packed
+// sum: each such pair is written as the fused multiply-add (fma2, dot3_2), and
+// a sum that must stay unfused is formed with scalar round-to-nearest adds,
+// which are never contracted.  Every kernel then rounds identically.
 __device__ __forceinline__ unsigned long long f2u(float2 a) {
   return *reinterpret_cast<unsigned long long*>(&a);
 }
@@ -105,6 +113,12 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
   unsigned long long r;
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2u(a)), "l"(f2u(b)), "l"(f2u(c)));
   return u2f(r);
+}
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+// The dot product a.b of two pairs of 3-vectors as fma(az, bz, fma(ax, bx, ay by)).
+__device__ __forceinline__ float2 dot3_2(float2 ax, float2 ay, float2 az, float2 bx, float2 by,
+                                         float2 bz) {
+  return fma2(az, bz, fma2(ax, bx, mul2(ay, by)));
 }
 
 // ----------------------------------------------------------------------------
@@ -373,7 +387,7 @@ __device__ __forceinline__ void decode_one(const unsigned char* plane0, long lon
 
 // s <- s / |s| for a pair
 __device__ __forceinline__ void normalize2(float2& x, float2& y, float2& z) {
-  const float2 n2 = add2(add2(mul2(x, x), mul2(y, y)), mul2(z, z));
+  const float2 n2 = dot3_2(x, y, z, x, y, z);
   const float2 inv = make_float2(rsqrtf(n2.x), rsqrtf(n2.y));
   x = mul2(x, inv);
   y = mul2(y, inv);
@@ -384,13 +398,13 @@ __device__ __forceinline__ void normalize2(float2& x, float2& y, float2& z) {
 // unchanged where h = 0; then renormalised.
 __device__ __forceinline__ void or_move2(float2& sx, float2& sy, float2& sz, float2 hx, float2 hy,
                                          float2 hz) {
-  const float2 hh = add2(add2(mul2(hx, hx), mul2(hy, hy)), mul2(hz, hz));
-  const float2 sh = add2(add2(mul2(sx, hx), mul2(sy, hy)), mul2(sz, hz));
+  const float2 hh = dot3_2(hx, hy, hz, hx, hy, hz);
+  const float2 sh = dot3_2(sx, sy, sz, hx, hy, hz);
   const float2 two_sh = add2(sh, sh);
   float2 f = make_float2(__fdividef(two_sh.x, hh.x), __fdividef(two_sh.y, hh.y));
-  float2 nx = sub2(mul2(f, hx), sx);
-  float2 ny = sub2(mul2(f, hy), sy);
-  float2 nz = sub2(mul2(f, hz), sz);
+  float2 nx = fma2(f, hx, neg2(sx));
+  float2 ny = fma2(f, hy, neg2(sy));
+  float2 nz = fma2(f, hz, neg2(sz));
   normalize2(nx, ny, nz);
   if (hh.x > 0.0f) { sx.x = nx.x; sy.x = ny.x; sz.x = nz.x; }
   if (hh.y > 0.0f) { sx.y = nx.y; sy.y = ny.y; sz.y = nz.y; }
@@ -525,7 +539,7 @@ __device__ __forceinline__ void hb_move2(float2& sx, float2& sy, float2& sz, flo
   if (zx) { nx.x = 0.0f; ny.x = 0.0f; nz.x = 1.0f; }
   if (zy) { nx.y = 0.0f; ny.y = 0.0f; nz.y = 1.0f; }
   const float2 sg = make_float2(nz.x >= 0.0f ? 1.0f : -1.0f, nz.y >= 0.0f ? 1.0f : -1.0f);
-  const float2 sn = add2(sg, nz);
+  const float2 sn = make_float2(__fadd_rn(sg.x, nz.x), __fadd_rn(sg.y, nz.y));   // unfused, as in hb_move
   const float2 A = make_float2(-rcp_approx(sn.x), -rcp_approx(sn.y));
   const float2 B = mul2(mul2(nx, ny), A);
   const float2 e1x = fma2(sg, mul2(mul2(nx, nx), A), f2(1.0f));

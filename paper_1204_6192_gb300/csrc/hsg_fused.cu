@@ -182,9 +182,9 @@ __device__ __forceinline__ void or_chunk(const typename FmtInfo<F>::Chunk (*nc)[
       const float2 jj = f2(j6[n]);
 #pragma unroll
       for (int k = 0; k < VEC / 2; ++k) {
-        hf.x[k] = add2(hf.x[k], mul2(jj, nb.x[k]));
-        hf.y[k] = add2(hf.y[k], mul2(jj, nb.y[k]));
-        hf.z[k] = add2(hf.z[k], mul2(jj, nb.z[k]));
+        hf.x[k] = fma2(jj, nb.x[k], hf.x[k]);
+        hf.y[k] = fma2(jj, nb.y[k], hf.y[k]);
+        hf.z[k] = fma2(jj, nb.z[k], hf.z[k]);
       }
     }
   }

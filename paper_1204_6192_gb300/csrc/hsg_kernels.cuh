@@ -131,9 +131,9 @@ __device__ __forceinline__ void sweep_block(const SweepParams& p, int bidx, floa
           const float2 jj = f2(j6[n]);
 #pragma unroll
           for (int k = 0; k < VEC / 2; ++k) {
-            hf.x[k] = add2(hf.x[k], mul2(jj, nb.x[k]));
-            hf.y[k] = add2(hf.y[k], mul2(jj, nb.y[k]));
-            hf.z[k] = add2(hf.z[k], mul2(jj, nb.z[k]));
+            hf.x[k] = fma2(jj, nb.x[k], hf.x[k]);
+            hf.y[k] = fma2(jj, nb.y[k], hf.y[k]);
+            hf.z[k] = fma2(jj, nb.z[k], hf.z[k]);
           }
         }
       }
@@ -179,10 +179,9 @@ __device__ __forceinline__ void sweep_block(const SweepParams& p, int bidx, floa
         for (int k = 0; k < VEC / 2; ++k) {
           float2 d;
           if (p.parity == 1) {
-            d = add2(add2(mul2(st.x[k], hf.x[k]), mul2(st.y[k], hf.y[k])), mul2(st.z[k], hf.z[k]));
+            d = dot3_2(st.x[k], st.y[k], st.z[k], hf.x[k], hf.y[k], hf.z[k]);
           } else {
-            d = add2(add2(mul2(st.x[k], f2(h3[0])), mul2(st.y[k], f2(h3[1]))),
-                     mul2(st.z[k], f2(h3[2])));
+            d = dot3_2(st.x[k], st.y[k], st.z[k], f2(h3[0]), f2(h3[1]), f2(h3[2]));
           }
           e[2 * k] = -d.x;
           e[2 * k + 1] = -d.y;

@@ -228,9 +228,9 @@ __global__ void __launch_bounds__(TileShape<T>::NT, multihit_min_blocks<F, T>())
             const float2 jj = f2(j6[par][n]);
 #pragma unroll
             for (int q = 0; q < VEC / 2; ++q) {
-              hf.x[q] = add2(hf.x[q], mul2(jj, nbv.x[q]));
-              hf.y[q] = add2(hf.y[q], mul2(jj, nbv.y[q]));
-              hf.z[q] = add2(hf.z[q], mul2(jj, nbv.z[q]));
+              hf.x[q] = fma2(jj, nbv.x[q], hf.x[q]);
+              hf.y[q] = fma2(jj, nbv.y[q], hf.y[q]);
+              hf.z[q] = fma2(jj, nbv.z[q], hf.z[q]);
             }
           }
         }
