@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--schedule", default="auto", choices=["auto", "two_pass", "persistent"],
                     help="step schedule: tuned at the first step (default) or fixed")
-    ap.add_argument("--sweep-kernel", default="auto", choices=["auto", "half", "fused"],
+    ap.add_argument("--sweep-kernel", default="auto", choices=["auto", "half", "fused", "wave"],
                     help="over-relaxation sweep kernel: tuned (default), one launch per half-sweep, "
                          "or the fused one-pass sweep")
     return ap.parse_args()
@@ -182,8 +182,8 @@ def run_ours(args, wl, torch, dev, rank, world, measure_every, do_roofline=True)
     stream = torch.cuda.Stream(device=dev)
     variant = {"auto": hsg.VARIANT_AUTO, "two_pass": hsg.VARIANT_TWO_PASS,
                "persistent": hsg.VARIANT_PERSISTENT}[getattr(args, "schedule", "auto")]
-    kernel = {"auto": hsg.SWEEP_AUTO, "half": hsg.SWEEP_HALF,
-              "fused": hsg.SWEEP_FUSED}[getattr(args, "sweep_kernel", "auto")]
+    kernel = {"auto": hsg.SWEEP_AUTO, "half": hsg.SWEEP_HALF, "fused": hsg.SWEEP_FUSED,
+              "wave": hsg.SWEEP_WAVE}[getattr(args, "sweep_kernel", "auto")]
     ctx = hsg.Context(wl.samples, wl.n_replicas, wl.seed + rank, precision=wl.precision,
                       j_fp16=wl.j_fp16, n_hb=wl.n_hb, n_or=wl.n_or, device=dev.index,
                       stream=stream.cuda_stream, variant=variant, sweep_kernel=kernel)
@@ -234,14 +234,24 @@ def timed_steps(ctx, stream, torch, steps, measure_every, flush=None):
     return total, n_meas
 
 
-def roofline(ctx, stream, torch, wl, reps=20):
+SWEEP_NAMES = {1: "half", 2: "fused", 3: "wave"}
+
+
+def one_launch_per_sweep(info):
+    """The fused and the wave sweep do both half-sweeps in one launch."""
+    return info.sweep_kernel in (2, 3)
+
+
+def roofline(ctx, stream, torch, wl, reps=20, half=True):
     """Average kernel durations with CUDA events on the context's stream:
-    the over-relaxation sweep as the step runs it (fused: `reps` launches of one
-    sweep each; otherwise 2 * `reps` half-sweep launches), the over-relaxation
-    half-sweep kernel on its own (sweep_or(1) runs it in every schedule) and the
-    heat-bath half-sweep.  Returns (ms per OR launch, fused?, ms per OR
-    half-sweep launch, ms per HB half-sweep launch)."""
-    fused = ctx.info().sweep_kernel == 2
+    the over-relaxation sweep as the step runs it (fused or wave: `reps`
+    launches of one sweep each; otherwise 2 * `reps` half-sweep launches), the
+    over-relaxation half-sweep kernel on its own (sweep_or(1) runs it beside the
+    fused sweep; with the wave sweep a context with the half-sweep kernel is
+    timed) and the heat-bath half-sweep.  Returns (ms per OR launch, sweep kind,
+    ms per OR half-sweep launch, ms per HB half-sweep launch)."""
+    info = ctx.info()
+    kind = SWEEP_NAMES[info.sweep_kernel]
 
     def timed(fn):
         t0 = torch.cuda.Event(enable_timing=True)
@@ -253,13 +263,28 @@ def roofline(ctx, stream, torch, wl, reps=20):
         return t0.elapsed_time(t1)
 
     ctx.sweep_or(2)
-    ms_or = timed(lambda: ctx.sweep_or(reps)) / (reps if fused else 2 * reps)
+    ms_or = timed(lambda: ctx.sweep_or(reps)) / (reps if one_launch_per_sweep(info) else 2 * reps)
     ms_half = ms_or
-    if fused:
+    if kind == "fused":
         ms_half = timed(lambda: [ctx.sweep_or(1) for _ in range(reps // 2)]) / (2 * (reps // 2))
+    elif kind == "wave" and half:
+        from paper_1204_6192_gb300 import hsg
+        h = hsg.Context(wl.samples, wl.n_replicas, wl.seed, precision=wl.precision,
+                        j_fp16=wl.j_fp16, device=torch.cuda.current_device(), stream=stream.cuda_stream,
+                        variant=hsg.VARIANT_TWO_PASS, sweep_kernel=hsg.SWEEP_HALF,
+                        chunks_per_thread=info.chunks_per_thread)
+        h.sweep_or(2)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        h.sweep_or(reps)
+        t1.record(stream)
+        t1.synchronize()
+        ms_half = t0.elapsed_time(t1) / (2 * reps)
+        h.close()
     k = reps // 4 or 1
     ms_hb = timed(lambda: ctx.sweep_hb(k)) / (2 * k)
-    return ms_or, fused, ms_half, ms_hb
+    return ms_or, kind, ms_half, ms_hb
 
 
 def multihit_extras(torch, dev, inputs, lattice_ns):
@@ -606,15 +631,20 @@ def main():
 
 def schedule_of(info, short=False):
     persistent = info.variant == 2
-    fused = info.sweep_kernel == 2
+    kind = SWEEP_NAMES.get(info.sweep_kernel, "half")
     if short:
         return (("persistent" if persistent else "graph") + f"/gpt{info.chunks_per_thread}"
-                + f"/p{info.n_passes}" + ("/fused" if fused else ""))
+                + f"/p{info.n_passes}" + ("" if kind == "half" else f"/{kind}"))
+    or_sweep = {"half": "one launch per half-sweep",
+                "fused": "fused (one launch per sweep, through shared memory)",
+                "wave": "wave (one launch per sweep, odd blocks trailing even blocks in L2)"}[kind]
     out = {"variant": "persistent" if persistent else "two_pass (CUDA graph)",
            "chunks_per_thread": info.chunks_per_thread, "passes": info.n_passes,
-           "or_sweep": "fused (one launch per sweep)" if fused else "one launch per half-sweep"}
-    if fused:
+           "or_sweep": or_sweep}
+    if kind == "fused":
         out.update({"fused_band_rows": info.fused_band_rows, "fused_items": info.fused_items})
+    if kind == "wave":
+        out.update({"wave_lag_blocks": info.wave_lag})
     return out
 
 
@@ -628,6 +658,8 @@ def launches_per_step(info, wl):
     if info.sweep_kernel == 2 and info.n_passes == 1:
         pairs = (wl.n_or - 1) // 2
         return 2 * wl.n_hb + 2 * pairs + 2 * (wl.n_or - 2 * pairs) + tail
+    if info.sweep_kernel == 3:
+        return info.n_passes * (2 * wl.n_hb + wl.n_or) + tail
     return info.n_passes * 2 * (wl.n_hb + wl.n_or) + tail
 
 
@@ -638,15 +670,18 @@ def roofline_entry(ctx, wl, rl, value_ns, peak, peak_kind):
     half-sweep kernel is reported beside it, also against the two-pass byte
     count.  step_frac compares the whole step with the time the fused bytes of
     every update would take at the peak."""
-    ms_or, fused, ms_half, ms_hb = rl
+    ms_or, kind, ms_half, ms_hb = rl
     A_half = algorithmic_half_sweep_bytes(ctx, wl, fused=True)
     A2 = algorithmic_half_sweep_bytes(ctx, wl, fused=False)
-    A = 2 * A_half if fused else A_half
+    A = A_half if kind == "half" else 2 * A_half
     achieved = A / (ms_or * 1e-3) / 1e9
-    traffic = traffic_summary(f"{'fused_sweep' if fused else 'or_half_sweep'}_{wl.precision}")
+    key = {"half": "or_half_sweep", "fused": "fused_sweep", "wave": "wave_sweep"}[kind]
+    traffic = traffic_summary(f"{key}_{wl.precision}")
     floor_ns = bytes_per_update(wl, ctx.W, fused=True) / peak      # ns per update at the peak
+    name = {"half": "k_half_sweep OR", "fused": "k_fused_or (one sweep)",
+            "wave": "k_wave_sweep OR (one sweep)"}[kind]
     return {"bound": "hbm",
-            "kernel": f"{'k_fused_or (one sweep)' if fused else 'k_half_sweep OR'} {wl.precision}",
+            "kernel": f"{name} {wl.precision}",
             "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "peak_kind": peak_kind, "traffic": traffic,
             "algorithmic_bytes_per_launch": A,
@@ -671,8 +706,8 @@ def config_line(args, name, torch, dev, peak):
     buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev) if flush else None
     k2 = 30 if flush else 20
     ms2, _ = timed_steps(r2["ctx"], r2["stream"], torch, k2, args.measure_every, flush=buf)
-    ms_or, fused, _, _ = roofline(r2["ctx"], r2["stream"], torch, w2)
-    A = algorithmic_half_sweep_bytes(r2["ctx"], w2, fused=True) * (2 if fused else 1)
+    ms_or, kind, _, _ = roofline(r2["ctx"], r2["stream"], torch, w2, half=False)
+    A = algorithmic_half_sweep_bytes(r2["ctx"], w2, fused=True) * (1 if kind == "half" else 2)
     out = {"ns": round(ms2 * 1e6 / (sw2 * sp2 * k2), 6), "ms_step": round(ms2 / k2, 4),
            "or_frac": round(A / (ms_or * 1e-3) / 1e9 / peak, 3),
            "schedule": schedule_of(r2["ctx"].info(), short=True),

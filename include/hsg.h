@@ -91,8 +91,9 @@ typedef struct {
   void* stream;       /* cudaStream_t to use; NULL: the library creates a non-blocking stream */
   int variant;        /* step schedule: 0 = automatic, else an HSG_VARIANT_* value */
   int barrier_timeout_ms;   /* bound of every device wait: the grid barriers of the
-                               persistent schedule and the waits of the measurement kernels
-                               for their staged spin copies (default 2000); a wait that runs
+                               persistent schedule, the waits of the measurement kernels
+                               for their staged spin copies and of the fused and wave sweeps
+                               for their plane copies and even blocks (default 2000); a wait that runs
                                out ends the launch and the next synchronising call returns
                                HSG_ETIMEOUT */
   int inject_barrier_fault; /* testing only: nonzero makes one block skip the first grid
@@ -115,14 +116,30 @@ typedef struct {
                                buffer of spin_bytes, every L a multiple of 4 and a storage
                                format other than HSG_YX4, and is used with the two-pass
                                schedule in one pass (elsewhere the per-half-sweep kernel
-                               runs).  0 (default): chosen by the automatic schedule.
-                               Results do not depend on it (bit for bit). */
+                               runs).  HSG_SWEEP_WAVE also does both half-sweeps of a
+                               sweep in one launch: the blocks of the per-half-sweep kernel,
+                               the odd-parity blocks of each plane following the even-parity
+                               blocks of the planes around it, so that they read the spins
+                               from the L2 cache; it needs a storage format among HSG_FP32,
+                               HSG_FP16 and HSG_BF16 and the two-pass schedule (any pass
+                               footprint); where every L is a power of 2 and at least 32,
+                               its blocks stage their neighbour rows through shared
+                               memory with bulk copies.  HSG_SWEEP_STAGED keeps one launch
+                               per half-sweep but with that staged block body (same
+                               conditions).  0 (default): chosen by the automatic
+                               schedule.  Results do not depend on it (bit for bit). */
+  int wave_lag;             /* HSG_SWEEP_WAVE: even-parity blocks scheduled between the last
+                               even block an odd block reads and that odd block (more: fewer
+                               waits, more spins held in L2).  0 (default): chosen from the
+                               number of resident blocks and by the automatic schedule. */
 } hsg_options;
 
 enum {
   HSG_SWEEP_AUTO = 0,
   HSG_SWEEP_HALF = 1,         /* one launch per half-sweep */
-  HSG_SWEEP_FUSED = 2         /* one launch per sweep (pairs of OR sweeps) */
+  HSG_SWEEP_FUSED = 2,        /* one launch per sweep through shared memory (pairs of OR sweeps) */
+  HSG_SWEEP_WAVE = 3,         /* one launch per sweep, odd blocks trailing even blocks in L2 */
+  HSG_SWEEP_STAGED = 4        /* one launch per half-sweep, neighbour rows staged in shared memory */
 };
 
 enum {
@@ -316,9 +333,12 @@ typedef struct {
   int n_passes;            /* system-blocked passes per step (1: no blocking) */
   long long pass_bytes;    /* footprint bound of a pass in use (0: one pass) */
   int n_overlap_pairs;     /* replica pairs hsg_measure_overlaps reports (0 if n_replicas < 2) */
-  int sweep_kernel;        /* HSG_SWEEP_HALF or HSG_SWEEP_FUSED: the over-relaxation sweep in use */
+  int sweep_kernel;        /* HSG_SWEEP_HALF, HSG_SWEEP_FUSED or HSG_SWEEP_WAVE: the
+                              over-relaxation sweep in use */
   int fused_band_rows;     /* fused sweep: rows of y per block of sample 0 (L: whole planes) */
   int fused_items;         /* fused sweep: work items (columns of planes) per launch */
+  int wave_lag;            /* wave sweep: the lag in use (even blocks) */
+  int staged;              /* nonzero: the over-relaxation sweep stages its neighbour rows */
 } hsg_info;
 hsg_status hsg_get_info(hsg_ctx* ctx, hsg_info* info);
 

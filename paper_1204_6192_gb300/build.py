@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhsg.so")
 SOURCES = ["hsg_api.cu", "hsg_sweep.cu", "hsg_aux.cu", "hsg_persist.cu", "hsg_noalloc.cu",
-           "hsg_overlap.cu", "hsg_multihit.cu", "hsg_fused.cu"]
+           "hsg_overlap.cu", "hsg_multihit.cu", "hsg_fused.cu", "hsg_wave.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -91,7 +91,7 @@ struct hsg_ctx {
   int variant = HSG_VARIANT_TWO_PASS;   // resolved step schedule
   bool tune_pending = false;            // automatic schedule not yet tuned
   long long max_sweep_blocks = 0;       // sweep table capacity (one chunk per thread)
-  unsigned int* d_bar = nullptr;        // grid barrier: arrivals, generation, error word; [3] measurement error word; [4] fused sweep error word
+  unsigned int* d_bar = nullptr;        // grid barrier: arrivals, generation, error word; [3] measurement error word; [4] fused sweep error word; [5] wave sweep error word
   int persist_grid = 0;
   size_t persist_smem = 0;
   bool inject_fault = false;
@@ -114,6 +114,21 @@ struct hsg_ctx {
   size_t fused_smem = 0;
   uint32_t fused_slot1 = 0, fused_slot0 = 0;
   std::vector<int> fused_ny;            // band rows per sample
+
+  // wave over-relaxation sweep: both half-sweeps in one launch of the sweep
+  // block table's blocks, odd blocks trailing the even blocks of their planes
+  bool wave_possible = false;           // the storage format allows it
+  bool use_wave = false;                // resolved choice of the schedule
+  // staged sweeps: neighbour rows through a shared-memory ring (the block body
+  // of the wave sweep where possible, or of two half-sweep launches)
+  bool staged_possible = false;         // format and every L allow it
+  bool use_staged = false;              // HSG_SWEEP_STAGED in use
+  int Lh_max = 0;
+  int wave_lag = 0;                     // lag in use (even blocks)
+  int* d_wave_order = nullptr;          // [2 max_sweep_blocks] ticket order of every pass
+  int4* d_wave_deps = nullptr;          // [max_sweep_blocks] even-block ranges of each odd block
+  unsigned int* d_wave_flags = nullptr; // [max_sweep_blocks] completion flags of the even blocks
+  unsigned int* d_wave_state = nullptr; // tickets taken, blocks finished, epoch
 
   std::vector<int> pass_bound{0, 0};    // [n_passes + 1] block table bounds
   int* d_pass_bound = nullptr;
@@ -209,7 +224,13 @@ SweepParams sweep_params(hsg_ctx* c, int parity, int sweep_offset) {
   p.epart = c->d_epart;
   p.n_blocks = c->n_sweep_blocks;
   p.blk_base = 0;
+  p.n_launch = c->n_sweep_blocks;
+  p.reverse = 0;
   p.dec = c->dec;
+  p.stage_bytes = c->staged_possible ? staged_stage_bytes(c->fmt, c->Lh_max) : 0;
+  p.stage_off = 0;
+  p.err = c->d_bar + 5;
+  p.timeout_ns = (unsigned long long)std::max(1, c->opt.barrier_timeout_ms) * 1000000ull;
   uint32_t k0 = c->seed_lo, k1 = c->seed_hi;
   for (int r = 0; r < 10; ++r) {
     p.rk[2 * r] = k0;
@@ -285,9 +306,48 @@ ConvParams conv_params(hsg_ctx* c, float* xyz, const long long* xyz_off) {
 hsg_status half_sweeps(hsg_ctx* c, bool hb, int sweep_offset, bool energy = false, int b0 = 0,
                        int b1 = -1) {
   if (b1 < 0) b1 = c->n_sweep_blocks;
+  if (!hb && c->use_staged) {
+    int off = 0;
+    const size_t smem = staged_smem(c->fmt, c->GPT, energy, c->Lh_max, &off);
+    for (int parity = 0; parity < 2; ++parity) {
+      SweepParams p = sweep_params(c, parity, sweep_offset);
+      p.blk_base = b0;
+      p.n_launch = b1 - b0;
+      p.reverse = parity;
+      p.stage_off = off;
+      HSG_CUDA(c, launch_staged_half(c->fmt, c->j16, energy, p, b1 - b0, smem, c->stream));
+    }
+    return HSG_OK;
+  }
+  if (!hb && c->use_wave) {
+    // both half-sweeps in one launch; the ticket order of the block range is
+    // the concatenation of its passes' orders
+    WaveParams w;
+    w.sw = sweep_params(c, 0, sweep_offset);
+    int off = 0;
+    size_t smem = c->staged_possible ? staged_smem(c->fmt, c->GPT, energy, c->Lh_max, &off)
+                                     : (energy ? sizeof(float) * (SWEEP_BS / 32) * c->GPT * c->VEC : 0);
+    w.sw.stage_off = off;
+    w.order = c->d_wave_order;
+    w.deps = c->d_wave_deps;
+    w.flags = c->d_wave_flags;
+    w.state = c->d_wave_state;
+    w.err = c->d_bar + 5;
+    w.timeout_ns = (unsigned long long)std::max(1, c->opt.barrier_timeout_ms) * 1000000ull;
+    w.t0 = 2 * b0;
+    w.n_tickets = 2 * (b1 - b0);
+    HSG_CUDA(c, launch_wave(c->fmt, c->j16, energy, c->staged_possible, w, smem, c->stream));
+    return HSG_OK;
+  }
   for (int parity = 0; parity < 2; ++parity) {
     SweepParams p = sweep_params(c, parity, sweep_offset);
     p.blk_base = b0;
+    p.n_launch = b1 - b0;
+    // Consecutive launches walk the planes in opposite directions (the blocks
+    // of a launch are independent, so the order changes no result): each
+    // launch starts on the planes whose spins the previous one left in L2.
+    // Packed formats: the decode launch runs forward, the sweep backward.
+    p.reverse = c->dec_once ? 1 : parity;
     // packed formats: decode the other parity once for the six neighbour loads
     if (c->dec_once) HSG_CUDA(c, launch_decode_parity(c->fmt, p, 1 - parity, b1 - b0, c->stream));
     HSG_CUDA(c, launch_half_sweep(c->fmt, hb, c->j16, c->opt.fast_math != 0, energy, c->dec_once, p,
@@ -466,11 +526,12 @@ hsg_status enqueue_step(hsg_ctx* c) {
 // A bounded device wait that ran out (persistent schedule, staged measurement)
 // after the stream has been synchronised.
 hsg_status poll_device_error(hsg_ctx* c) {
-  unsigned int err[3] = {0u, 0u, 0u};
+  unsigned int err[4] = {0u, 0u, 0u, 0u};
   HSG_CUDA(c, cudaMemcpy(err, c->d_bar + 2, sizeof(err), cudaMemcpyDeviceToHost));
   if (err[0]) return fail(c, HSG_ETIMEOUT, "a grid barrier wait of the persistent step kernel timed out");
   if (err[1]) return fail(c, HSG_ETIMEOUT, "a wait for a staged spin copy of a measurement kernel timed out");
   if (err[2]) return fail(c, HSG_ETIMEOUT, "a wait for a staged plane copy of the fused sweep kernel timed out");
+  if (err[3]) return fail(c, HSG_ETIMEOUT, "a wait of the wave sweep kernel for its even blocks timed out");
   return HSG_OK;
 }
 
@@ -515,12 +576,103 @@ int default_gpt(hsg_ctx*, const int* L, int n_samples, int G) {
   return (int)std::max(1ll, std::min((long long)G, gpt));
 }
 
+// Plan of the wave sweep for the block table `blocks` and the passes in
+// c->pass_bound.  An odd block covering planes [z0, z1] of its sample and chunk
+// group depends on the even blocks of planes z0-1 .. z1+1 (periodic; at most two
+// ranges of the table).  Per pass, the even blocks keep table order (z-major
+// within a chunk group) and each odd block is placed `lag` even blocks after the
+// last even block it depends on, so every dependency holds an earlier ticket.
+hsg_status plan_wave(hsg_ctx* c, const std::vector<int4>& blocks, int lag) {
+  if (!c->d_wave_order) {
+    HSG_TRY(dev_alloc(c, &c->d_wave_order, sizeof(int) * 2 * c->max_sweep_blocks));
+    HSG_TRY(dev_alloc(c, &c->d_wave_deps, sizeof(int4) * c->max_sweep_blocks));
+    HSG_TRY(dev_alloc(c, &c->d_wave_flags, sizeof(unsigned int) * c->max_sweep_blocks));
+    HSG_TRY(dev_alloc(c, &c->d_wave_state, sizeof(unsigned int) * 4));
+    HSG_CUDA(c, cudaMemset(c->d_wave_flags, 0, sizeof(unsigned int) * c->max_sweep_blocks));
+    HSG_CUDA(c, cudaMemset(c->d_wave_state, 0, sizeof(unsigned int) * 4));
+  }
+  if (lag <= 0) {
+    int per_sm = 0, n_sm = 0, off = 0;
+    const size_t smem = c->staged_possible ? staged_smem(c->fmt, c->GPT, false, c->Lh_max, &off) : 0;
+    HSG_CUDA(c, wave_occupancy(c->fmt, c->j16, c->staged_possible, smem, &per_sm));
+    HSG_CUDA(c, cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, c->device));
+    lag = std::max(1, n_sm * per_sm / 2);
+  }
+  const int nb = (int)blocks.size();
+  std::vector<int4> deps(nb, make_int4(0, 0, 0, 0));
+  std::vector<int> order(2 * (size_t)nb);
+  for (size_t ps = 0; ps + 1 < c->pass_bound.size(); ++ps) {
+    const int b0 = c->pass_bound[ps], b1 = c->pass_bound[ps + 1];
+    std::vector<std::pair<long long, int>> keyed;   // (position key, ticket code)
+    keyed.reserve(2 * (size_t)(b1 - b0));
+    for (int b = b0; b < b1; ++b) {
+      const int4 k = blocks[b];
+      const SampleDev& d = c->sd[k.x];
+      const int L = d.L;
+      const long long P = (long long)L * d.Lh, half = d.N / 2;   // half-sites per plane, per parity
+      const int per_g = (int)((half + SWEEP_BS - 1) / SWEEP_BS);
+      const int e_first = d.blk0 + k.y * per_g;
+      const long long h_end = std::min<long long>((long long)k.z + SWEEP_BS, half);
+      const int z0 = (int)(k.z / P), z1 = (int)((h_end - 1) / P);
+      // even blocks of planes [p0, p1] (no wrap): [first, last + 1)
+      auto range = [&](int p0, int p1) {
+        return std::make_pair(e_first + (int)(p0 * P / SWEEP_BS),
+                              e_first + (int)(((p1 + 1) * P - 1) / SWEEP_BS) + 1);
+      };
+      int4 dep;
+      if (z1 - z0 + 3 >= L) {
+        dep = make_int4(e_first, e_first + per_g, 0, 0);
+      } else if (z0 == 0) {
+        const auto r1 = range(0, z1 + 1), r2 = range(L - 1, L - 1);
+        dep = make_int4(r1.first, r1.second, r2.first, r2.second);
+      } else if (z1 == L - 1) {
+        const auto r1 = range(z0 - 1, L - 1), r2 = range(0, 0);
+        dep = make_int4(r1.first, r1.second, r2.first, r2.second);
+      } else {
+        const auto r = range(z0 - 1, z1 + 1);
+        dep = make_int4(r.first, r.second, 0, 0);
+      }
+      deps[b] = dep;
+      const int last = std::max(dep.y, dep.w) - 1;
+      keyed.push_back({2ll * (b - b0), b << 1});
+      keyed.push_back({2ll * (last - b0 + lag) + 1, (b << 1) | 1});
+    }
+    std::stable_sort(keyed.begin(), keyed.end(),
+                     [](const std::pair<long long, int>& a, const std::pair<long long, int>& b) {
+                       return a.first < b.first;
+                     });
+    for (size_t i = 0; i < keyed.size(); ++i) order[2 * (size_t)b0 + i] = keyed[i].second;
+    // check before any launch: each dependency is an even block of the same
+    // sample and chunk group inside this pass, with an earlier ticket
+    std::vector<int> ticket(b1 - b0, -1);
+    for (size_t i = 0; i < keyed.size(); ++i)
+      if ((keyed[i].second & 1) == 0) ticket[(keyed[i].second >> 1) - b0] = (int)i;
+    for (size_t i = 0; i < keyed.size(); ++i) {
+      if ((keyed[i].second & 1) == 0) continue;
+      const int b = keyed[i].second >> 1;
+      const int4 k = blocks[b], dep = deps[b];
+      for (const auto& r : {std::make_pair(dep.x, dep.y), std::make_pair(dep.z, dep.w)})
+        for (int e = r.first; e < r.second; ++e)
+          if (e < b0 || e >= b1 || blocks[e].x != k.x || blocks[e].y != k.y || ticket[e - b0] >= (int)i)
+            return fail(c, HSG_ESTATE, "wave sweep plan: bad dependency");
+    }
+  }
+  HSG_CUDA(c, cudaMemcpyAsync(c->d_wave_order, order.data(), sizeof(int) * order.size(),
+                              cudaMemcpyHostToDevice, c->stream));
+  HSG_CUDA(c, cudaMemcpyAsync(c->d_wave_deps, deps.data(), sizeof(int4) * deps.size(),
+                              cudaMemcpyHostToDevice, c->stream));
+  HSG_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->wave_lag = lag;
+  return HSG_OK;
+}
+
 // Build the sweep block table for `gpt` chunks per thread, cut it into passes
 // whose footprint (spins of their chunk groups plus the records of their
 // samples) stays within `pass_bytes` (0: one pass; a pass holds at least one
 // chunk group), and set up the chosen step schedule (drops a captured graph:
 // its parameters change).
-hsg_status configure_schedule(hsg_ctx* c, int variant, int gpt, long long pass_bytes, bool fused) {
+hsg_status configure_schedule(hsg_ctx* c, int variant, int gpt, long long pass_bytes, int sweep,
+                              int lag) {
   gpt = std::max(1, std::min(c->G, gpt));
   const int n_gg = (c->G + gpt - 1) / gpt;
   const long long site_chunk_bytes = (long long)c->PL * c->VEC * c->ELEM;
@@ -574,11 +726,18 @@ hsg_status configure_schedule(hsg_ctx* c, int variant, int gpt, long long pass_b
     c->graph = nullptr;
   }
   c->variant = variant;
-  // the fused over-relaxation sweep serves the two-pass schedule in one pass
+  // the fused over-relaxation sweep serves the two-pass schedule in one pass,
+  // the wave sweep the two-pass schedule with any passes
   c->use_fused = false;
-  if (fused && variant == HSG_VARIANT_TWO_PASS && bounds.size() == 2) {
+  c->use_wave = false;
+  c->use_staged = sweep == HSG_SWEEP_STAGED && variant == HSG_VARIANT_TWO_PASS && c->staged_possible;
+  if (sweep == HSG_SWEEP_FUSED && variant == HSG_VARIANT_TWO_PASS && bounds.size() == 2) {
     HSG_TRY(plan_fused(c));
     c->use_fused = c->fused_possible;
+  }
+  if (sweep == HSG_SWEEP_WAVE && variant == HSG_VARIANT_TWO_PASS && c->wave_possible) {
+    HSG_TRY(plan_wave(c, blocks, lag));
+    c->use_wave = true;
   }
   if (variant == HSG_VARIANT_PERSISTENT) {
     c->persist_smem = sizeof(float) * (SWEEP_BS / 32) * c->GPT * c->VEC;
@@ -664,7 +823,7 @@ hsg_status copy_chain_state(hsg_ctx* c, unsigned char* host, bool to_host) {
 struct TuneChoice {
   int variant, gpt;
   long long pass_bytes;
-  bool fused;
+  int sweep, lag;
 };
 constexpr int TUNE_REPS = 5;
 std::mutex g_tune_mu;
@@ -676,7 +835,7 @@ std::string tune_key(hsg_ctx* c) {
                   std::to_string(c->opt.n_hb_per_step) + "/" + std::to_string(c->opt.n_or_per_step) +
                   "/" + std::to_string(c->opt.pass_bytes) + "/" +
                   std::to_string(c->opt.chunks_per_thread) + "/" +
-                  std::to_string(c->opt.sweep_kernel) + "/L";
+                  std::to_string(c->opt.sweep_kernel) + "/" + std::to_string(c->opt.wave_lag) + "/L";
   for (int L : c->L) k += std::to_string(L) + ",";
   return k;
 }
@@ -689,7 +848,7 @@ hsg_status autotune(hsg_ctx* c) {
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end())
       return configure_schedule(c, it->second.variant, it->second.gpt, it->second.pass_bytes,
-                                it->second.fused);
+                                it->second.sweep, it->second.lag);
   }
   // save the state the trial steps will change
   void* spins_copy = nullptr;
@@ -705,11 +864,27 @@ hsg_status autotune(hsg_ctx* c) {
   for (int g : {c->G, (c->G + 1) / 2, (c->G + 3) / 4, 2, 1, c->GPT})
     if (g >= 1 && g <= c->G && std::find(gpts.begin(), gpts.end(), g) == gpts.end()) gpts.push_back(g);
   if (c->opt.chunks_per_thread > 0) gpts.assign(1, c->GPT);
-  std::vector<bool> fused_opts;
-  if (c->opt.sweep_kernel != HSG_SWEEP_FUSED) fused_opts.push_back(false);
-  if (c->opt.sweep_kernel != HSG_SWEEP_HALF && c->fused_possible && c->opt.n_or_per_step >= 3)
-    fused_opts.push_back(true);
-  if (fused_opts.empty()) fused_opts.push_back(false);
+  // over-relaxation sweep kernels (with the wave sweep's lags) to try
+  std::vector<std::pair<int, int>> sweeps;
+  const int sk = c->opt.sweep_kernel;
+  if (sk == HSG_SWEEP_AUTO || sk == HSG_SWEEP_HALF) sweeps.push_back({HSG_SWEEP_HALF, 0});
+  if ((sk == HSG_SWEEP_AUTO || sk == HSG_SWEEP_FUSED) && c->fused_possible && c->opt.n_or_per_step >= 3)
+    sweeps.push_back({HSG_SWEEP_FUSED, 0});
+  if ((sk == HSG_SWEEP_AUTO || sk == HSG_SWEEP_WAVE) && c->wave_possible) {
+    if (c->opt.wave_lag > 0) {
+      sweeps.push_back({HSG_SWEEP_WAVE, c->opt.wave_lag});
+    } else {
+      int per_sm = 0, n_sm = 0, off = 0;
+      const size_t smem = c->staged_possible ? staged_smem(c->fmt, c->GPT, false, c->Lh_max, &off) : 0;
+      HSG_CUDA(c, wave_occupancy(c->fmt, c->j16, c->staged_possible, smem, &per_sm));
+      HSG_CUDA(c, cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, c->device));
+      const int resident = std::max(4, n_sm * per_sm);
+      for (int lag : {resident / 4, resident / 2, resident}) sweeps.push_back({HSG_SWEEP_WAVE, lag});
+    }
+  }
+  if ((sk == HSG_SWEEP_AUTO || sk == HSG_SWEEP_STAGED) && c->staged_possible)
+    sweeps.push_back({HSG_SWEEP_STAGED, 0});
+  if (sweeps.empty()) sweeps.push_back({HSG_SWEEP_HALF, 0});
   cudaEvent_t e0, e1;
   HSG_CUDA(c, cudaEventCreate(&e0));
   HSG_CUDA(c, cudaEventCreate(&e1));
@@ -728,15 +903,17 @@ hsg_status autotune(hsg_ctx* c) {
     }
   }
   float best = 1e30f;
-  TuneChoice bestc{HSG_VARIANT_TWO_PASS, c->GPT, budgets[0], fused_opts[0]};
+  TuneChoice bestc{HSG_VARIANT_TWO_PASS, c->GPT, budgets[0], sweeps[0].first, sweeps[0].second};
   for (long long pb : budgets) {
     for (int v : {HSG_VARIANT_TWO_PASS, HSG_VARIANT_PERSISTENT}) {
-      for (bool fu : fused_opts) {
-        // the fused sweep runs in the two-pass schedule with one pass only
-        if (fu && (v != HSG_VARIANT_TWO_PASS || pb != 0)) continue;
+      for (const auto& sw : sweeps) {
+        // the fused sweep runs in the two-pass schedule with one pass only, the
+        // wave sweep in the two-pass schedule; the persistent schedule has its own
+        if (sw.first != HSG_SWEEP_HALF && v != HSG_VARIANT_TWO_PASS) continue;
+        if (sw.first == HSG_SWEEP_FUSED && pb != 0) continue;
         for (int g : gpts) {
-          HSG_TRY(configure_schedule(c, v, g, pb, fu));
-          if (fu && !c->use_fused) continue;
+          HSG_TRY(configure_schedule(c, v, g, pb, sw.first, sw.second));
+          if (sw.first == HSG_SWEEP_FUSED && !c->use_fused) continue;
           HSG_TRY(run_steps(c, 1));
           float t[TUNE_REPS];
           for (int r = 0; r < TUNE_REPS; ++r) {
@@ -751,7 +928,7 @@ hsg_status autotune(hsg_ctx* c) {
           const float ms = t[TUNE_REPS / 2];
           if (ms < best) {
             best = ms;
-            bestc = TuneChoice{v, g, pb, fu};
+            bestc = TuneChoice{v, g, pb, sw.first, sw.second};
           }
         }
       }
@@ -769,7 +946,7 @@ hsg_status autotune(hsg_ctx* c) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune_cache[key] = bestc;
   }
-  return configure_schedule(c, bestc.variant, bestc.gpt, bestc.pass_bytes, bestc.fused);
+  return configure_schedule(c, bestc.variant, bestc.gpt, bestc.pass_bytes, bestc.sweep, bestc.lag);
 }
 
 hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double* temps,
@@ -793,8 +970,9 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   if (opt.variant < HSG_VARIANT_AUTO || opt.variant > HSG_VARIANT_PERSISTENT)
     return bad_arg(nullptr, "unknown variant");
   if (opt.chunks_per_thread < 0) return bad_arg(nullptr, "chunks_per_thread < 0");
-  if (opt.sweep_kernel < HSG_SWEEP_AUTO || opt.sweep_kernel > HSG_SWEEP_FUSED)
+  if (opt.sweep_kernel < HSG_SWEEP_AUTO || opt.sweep_kernel > HSG_SWEEP_STAGED)
     return bad_arg(nullptr, "unknown sweep_kernel");
+  if (opt.wave_lag < 0) return bad_arg(nullptr, "wave_lag < 0");
   const int W = n_temps * n_replicas;
   if (W > 1024) return bad_arg(nullptr, "n_temps * n_replicas must be <= 1024");
   const int Wp = (W + 7) / 8 * 8;
@@ -966,7 +1144,7 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   HSG_ALLOC(c->d_acc, sizeof(unsigned long long) * n_samples * n_replicas * std::max(1, n_temps - 1));
   HSG_ALLOC(c->d_counters, sizeof(unsigned long long) * 2 * n_samples);
   HSG_ALLOC(c->d_active, sizeof(unsigned char) * n_samples);
-  HSG_ALLOC(c->d_bar, sizeof(unsigned int) * 5);
+  HSG_ALLOC(c->d_bar, sizeof(unsigned int) * 6);
   HSG_ALLOC(c->d_moved, sizeof(unsigned long long) * n_samples * n_replicas * n_temps);
   HSG_ALLOC(c->d_tstate, sizeof(unsigned char) * n_samples * n_replicas * n_temps);
   HSG_ALLOC(c->d_tunnel, sizeof(unsigned int) * n_samples * n_replicas * n_temps);
@@ -1027,7 +1205,7 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   if (e == cudaSuccess) e = cudaMemset(c->d_moved, 0, sizeof(unsigned long long) * perm.size());
   if (e == cudaSuccess) e = cudaMemset(c->d_tunnel, 0, sizeof(unsigned int) * perm.size());
   if (e == cudaSuccess) e = cudaMemset(c->d_E, 0, sizeof(double) * n_samples * Wp);
-  if (e == cudaSuccess) e = cudaMemset(c->d_bar, 0, sizeof(unsigned int) * 5);
+  if (e == cudaSuccess) e = cudaMemset(c->d_bar, 0, sizeof(unsigned int) * 6);
   if (e == cudaSuccess) e = cudaMemset(c->spins, 0, c->spin_bytes);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -1044,8 +1222,14 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
     c->fused_possible = fmt != FMT_YX4;
     for (int s = 0; s < n_samples; ++s)
       if (L[s] % 4 != 0 || L[s] < 8) c->fused_possible = false;
-    const bool fused = opt.sweep_kernel == HSG_SWEEP_FUSED;
-    hsg_status st2 = configure_schedule(c, want, c->GPT, opt.pass_bytes, fused);
+    c->wave_possible = fmt_has_wave(fmt);
+    c->staged_possible = c->wave_possible;
+    for (int s = 0; s < n_samples; ++s) {
+      c->staged_possible = c->staged_possible && lattice_has_staged(L[s]);
+      c->Lh_max = std::max(c->Lh_max, L[s] / 2);
+    }
+    const int sweep = opt.sweep_kernel == HSG_SWEEP_AUTO ? HSG_SWEEP_HALF : opt.sweep_kernel;
+    hsg_status st2 = configure_schedule(c, want, c->GPT, opt.pass_bytes, sweep, opt.wave_lag);
     if (st2 != HSG_OK) return cleanup_fail(st2);
   }
   ConvParams cp = conv_params(c, nullptr, nullptr);
@@ -1617,7 +1801,11 @@ hsg_status hsg_get_info(hsg_ctx* c, hsg_info* info) {
   info->sweep_count = cnt[0];
   info->pt_count = cnt[1];
   info->stream = (void*)c->stream;
-  info->sweep_kernel = c->use_fused ? HSG_SWEEP_FUSED : HSG_SWEEP_HALF;
+  info->sweep_kernel = c->use_wave ? HSG_SWEEP_WAVE
+                      : c->use_staged ? HSG_SWEEP_STAGED
+                      : (c->use_fused ? HSG_SWEEP_FUSED : HSG_SWEEP_HALF);
+  info->staged = (c->use_wave && c->staged_possible) || c->use_staged;
+  info->wave_lag = c->use_wave ? c->wave_lag : 0;
   info->fused_band_rows = c->fused_ny.empty() ? 0 : c->fused_ny[0];
   info->fused_items = c->n_fused_items;
   return HSG_OK;

@@ -63,8 +63,16 @@ struct SweepParams {
   double* epart;            // energy partials [2][n_blocks][Wp] (energy variant only)
   int n_blocks;
   int blk_base;             // block table entry of launch block 0 (a pass's first block)
+  int n_launch;             // blocks of this launch
+  int reverse;              // nonzero: launch block k runs table entry blk_base + n_launch - 1 - k
+                            // (so a launch starts on the planes the previous one ended with)
   uint32_t rk[20];          // Philox round keys of the seed
   const unsigned char* dec; // packed formats: the opposite parity as binary32 (see SampleDev)
+  // staged sweeps (hsg_wave.cu): bytes of one stage of neighbour rows, offset of
+  // stage 0 in dynamic shared memory, the error word of their bounded waits
+  int stage_bytes, stage_off;
+  unsigned int* err;
+  unsigned long long timeout_ns;
 };
 
 struct EnergyParams {
@@ -208,6 +216,37 @@ struct FusedParams {
 cudaError_t prepare_fused(int fmt, bool j16, size_t smem, int* blocks_per_sm);
 cudaError_t launch_fused(int fmt, bool j16, const FusedParams& p, int grid, size_t smem,
                          cudaStream_t st);
+
+// Wavefront over-relaxation sweep (hsg_wave.cu): both half-sweeps of one pass
+// in one launch of 2 (b1 - b0) blocks, odd blocks trailing the even blocks of
+// their planes (see the file).
+struct WaveParams {
+  SweepParams sw;           // parity set per block
+  const int* order;         // [2 n_blocks]: per ticket, (block << 1) | parity; a pass's tickets at 2 b0
+  const int4* deps;         // [n_blocks]: for an odd block, even blocks [x, y) and [z, w) it waits for
+  unsigned int* flags;      // [n_blocks]: completion flag of each even block (epoch + 1)
+  unsigned int* state;      // [0] tickets taken, [1] blocks finished, [2] epoch
+  unsigned int* err;        // set when a wait ran out
+  unsigned long long timeout_ns;
+  int t0, n_tickets;        // this launch's tickets: order[t0 .. t0 + n_tickets)
+};
+bool fmt_has_wave(int fmt);
+// Staged sweeps: every block copies the opposite-parity rows its sites read
+// (plane z: rows y0-1 .. y0+R, planes z-1 and z+1: rows y0 .. y0+R-1; R = 256 /
+// (L/2)) into a two-stage shared-memory ring with cp.async.bulk, one chunk group
+// per stage.  Possible for every sample with L a power of 2, L >= 32.
+constexpr int STAGED_STAGES = 2;
+constexpr int STAGED_HEAD = 256;          // mbarriers and stage counters
+bool lattice_has_staged(int L);
+int staged_stage_bytes(int fmt, int Lh_max);
+size_t staged_smem(int fmt, int gpt, bool energy, int Lh_max, int* stage_off);
+// blocks per SM of the wave kernel (staged: with that dynamic shared memory)
+cudaError_t wave_occupancy(int fmt, bool j16, bool staged, size_t smem, int* blocks_per_sm);
+cudaError_t launch_wave(int fmt, bool j16, bool energy, bool staged, const WaveParams& p, size_t smem,
+                        cudaStream_t st);
+// one half-sweep (p.parity) of over-relaxation with the staged block body
+cudaError_t launch_staged_half(int fmt, bool j16, bool energy, const SweepParams& p, int n_blocks,
+                               size_t smem, cudaStream_t st);
 
 // The packed spin formats (one or two 32-bit words per system) decode each
 // neighbour spin once into a binary32 buffer before a half-sweep instead of

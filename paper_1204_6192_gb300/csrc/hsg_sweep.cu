@@ -28,7 +28,8 @@ constexpr int sweep_min_blocks() {
 template <int F, bool HB, bool J16, bool FAST, bool EN, bool DEC>
 __global__ void __launch_bounds__(SWEEP_BS, sweep_min_blocks<F, HB, J16, EN>()) k_half_sweep(const SweepParams p) {
   extern __shared__ float esum[];
-  sweep_block<F, HB, J16, FAST, EN, false, DEC>(p, p.blk_base + (int)blockIdx.x, esum);
+  const int k = p.reverse ? p.n_launch - 1 - (int)blockIdx.x : (int)blockIdx.x;
+  sweep_block<F, HB, J16, FAST, EN, false, DEC>(p, p.blk_base + k, esum);
 }
 
 // Decode the spins of one parity into binary32 (the chunk layout of FMT_F32,

@@ -22,7 +22,7 @@ PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2, "angle16": 3, "oct16": 4, "yx4": 
 STATUS = {0: "HSG_OK", 1: "HSG_EINVAL", 2: "HSG_ENOMEM", 3: "HSG_ECUDA", 4: "HSG_ETIMEOUT",
           5: "HSG_ESTATE"}
 VARIANT_AUTO, VARIANT_TWO_PASS, VARIANT_PERSISTENT = 0, 1, 2
-SWEEP_AUTO, SWEEP_HALF, SWEEP_FUSED = 0, 1, 2
+SWEEP_AUTO, SWEEP_HALF, SWEEP_FUSED, SWEEP_WAVE, SWEEP_STAGED = 0, 1, 2, 3, 4
 
 
 class HsgError(RuntimeError):
@@ -37,7 +37,7 @@ class Options(ctypes.Structure):
                 ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("variant", ctypes.c_int),
                 ("barrier_timeout_ms", ctypes.c_int), ("inject_barrier_fault", ctypes.c_int),
                 ("pass_bytes", ctypes.c_longlong), ("chunks_per_thread", ctypes.c_int),
-                ("sweep_kernel", ctypes.c_int)]
+                ("sweep_kernel", ctypes.c_int), ("wave_lag", ctypes.c_int)]
 
 
 class Obs(ctypes.Structure):
@@ -55,7 +55,8 @@ class Info(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("chunks_per_thread", ctypes.c_int),
                 ("n_passes", ctypes.c_int), ("pass_bytes", ctypes.c_longlong),
                 ("n_overlap_pairs", ctypes.c_int), ("sweep_kernel", ctypes.c_int),
-                ("fused_band_rows", ctypes.c_int), ("fused_items", ctypes.c_int)]
+                ("fused_band_rows", ctypes.c_int), ("fused_items", ctypes.c_int),
+                ("wave_lag", ctypes.c_int), ("staged", ctypes.c_int)]
 
 
 _lib = None
@@ -138,7 +139,8 @@ class Context:
                  j_fp16: bool = False, fast_math: bool = False, n_hb: int = 1, n_or: int = 5,
                  device: int = 0, stream: Optional[int] = None, variant: int = VARIANT_AUTO,
                  barrier_timeout_ms: int = 2000, inject_barrier_fault: bool = False,
-                 pass_bytes: int = 0, chunks_per_thread: int = 0, sweep_kernel: int = SWEEP_AUTO):
+                 pass_bytes: int = 0, chunks_per_thread: int = 0, sweep_kernel: int = SWEEP_AUTO,
+                 wave_lag: int = 0):
         L = lib()
         self._ctx = ctypes.c_void_p()
         opt = default_options()
@@ -155,6 +157,7 @@ class Context:
         opt.pass_bytes = int(pass_bytes)
         opt.chunks_per_thread = int(chunks_per_thread)
         opt.sweep_kernel = int(sweep_kernel)
+        opt.wave_lag = int(wave_lag)
         self.samples = list(samples)
         self.n_samples = len(self.samples)
         self.n_temps = len(self.samples[0].temps)

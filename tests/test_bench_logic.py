@@ -42,8 +42,8 @@ def test_algorithmic_bytes_fp32_and_batches():
 
 def test_roofline_entry_fractions():
     wl = inputs.workload("L128_fp16")
-    # half-sweep kernel in the step: (ms per OR launch, fused?, ms per half-sweep, ms per HB)
-    rl = bench.roofline_entry(_fake_ctx(48), wl, (0.17634, False, 0.17634, 0.33),
+    # half-sweep kernel in the step: (ms per OR launch, sweep kind, ms per half-sweep, ms per HB)
+    rl = bench.roofline_entry(_fake_ctx(48), wl, (0.17634, "half", 0.17634, 0.33),
                               value_ns=0.004177, peak=6686.5, peak_kind="measured")
     # the kernel on the fused bytes: 616.6 MB / 0.17634 ms = 3.50 TB/s = 0.52 of 6686.5 GB/s
     assert rl["frac"] == pytest.approx(0.523, abs=2e-3)
@@ -51,11 +51,12 @@ def test_roofline_entry_fractions():
     # the step: 12.25 B / 6686.5 GB/s = 1.832 ps against 4.177 ps
     assert rl["step_frac"] == pytest.approx(0.4386, abs=2e-3)
     # fused kernel: one launch moves a whole sweep's bytes (1.233 GB)
-    rl = bench.roofline_entry(_fake_ctx(48), wl, (0.30, True, 0.176, 0.33), value_ns=0.0035,
-                              peak=6686.5, peak_kind="measured")
-    assert rl["algorithmic_bytes_per_launch"] == 2 * 616562688
-    assert rl["frac"] == pytest.approx(2 * 616562688 / 0.30e-3 / 1e9 / 6686.5, rel=1e-3)
-    assert rl["half_sweep"]["frac"] == pytest.approx(0.524, abs=2e-3)
+    for kind in ("fused", "wave"):
+        rl = bench.roofline_entry(_fake_ctx(48), wl, (0.30, kind, 0.176, 0.33), value_ns=0.0035,
+                                  peak=6686.5, peak_kind="measured")
+        assert rl["algorithmic_bytes_per_launch"] == 2 * 616562688
+        assert rl["frac"] == pytest.approx(2 * 616562688 / 0.30e-3 / 1e9 / 6686.5, rel=1e-3)
+        assert rl["half_sweep"]["frac"] == pytest.approx(0.524, abs=2e-3)
 
 
 def test_launches_per_step():
@@ -64,6 +65,8 @@ def test_launches_per_step():
     assert bench.launches_per_step(info, wl) == 12 + 2
     info.sweep_kernel = 2                    # two fused pairs, one half-sweep sweep with energies
     assert bench.launches_per_step(info, wl) == 2 + 4 + 2 + 2
+    info.sweep_kernel = 3                    # one wave launch per OR sweep
+    assert bench.launches_per_step(info, wl) == 2 + 5 + 2
     info = types.SimpleNamespace(variant=1, sweep_kernel=1, n_passes=17, n_samples=512, Wp=32)
     assert bench.launches_per_step(info, inputs.workload("batch512_mixedL", steps=1)) == 17 * 12 + 3
 
