@@ -49,9 +49,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--schedule", default="auto", choices=["auto", "two_pass", "persistent"],
                     help="step schedule: tuned at the first step (default) or fixed")
-    ap.add_argument("--sweep-kernel", default="auto", choices=["auto", "half", "fused", "wave"],
+    ap.add_argument("--sweep-kernel", default="auto", choices=["auto", "half", "fused", "wave", "staged"],
                     help="over-relaxation sweep kernel: tuned (default), one launch per half-sweep, "
-                         "or the fused one-pass sweep")
+                         "the fused one-pass sweep, the wave sweep, or half-sweeps with staged rows")
     return ap.parse_args()
 
 
@@ -183,7 +183,7 @@ def run_ours(args, wl, torch, dev, rank, world, measure_every, do_roofline=True)
     variant = {"auto": hsg.VARIANT_AUTO, "two_pass": hsg.VARIANT_TWO_PASS,
                "persistent": hsg.VARIANT_PERSISTENT}[getattr(args, "schedule", "auto")]
     kernel = {"auto": hsg.SWEEP_AUTO, "half": hsg.SWEEP_HALF, "fused": hsg.SWEEP_FUSED,
-              "wave": hsg.SWEEP_WAVE}[getattr(args, "sweep_kernel", "auto")]
+              "wave": hsg.SWEEP_WAVE, "staged": hsg.SWEEP_STAGED}[getattr(args, "sweep_kernel", "auto")]
     ctx = hsg.Context(wl.samples, wl.n_replicas, wl.seed + rank, precision=wl.precision,
                       j_fp16=wl.j_fp16, n_hb=wl.n_hb, n_or=wl.n_or, device=dev.index,
                       stream=stream.cuda_stream, variant=variant, sweep_kernel=kernel)
@@ -234,7 +234,7 @@ def timed_steps(ctx, stream, torch, steps, measure_every, flush=None):
     return total, n_meas
 
 
-SWEEP_NAMES = {1: "half", 2: "fused", 3: "wave"}
+SWEEP_NAMES = {1: "half", 2: "fused", 3: "wave", 4: "staged"}
 
 
 def one_launch_per_sweep(info):
@@ -636,6 +636,7 @@ def schedule_of(info, short=False):
         return (("persistent" if persistent else "graph") + f"/gpt{info.chunks_per_thread}"
                 + f"/p{info.n_passes}" + ("" if kind == "half" else f"/{kind}"))
     or_sweep = {"half": "one launch per half-sweep",
+                "staged": "one launch per half-sweep, neighbour rows staged in shared memory",
                 "fused": "fused (one launch per sweep, through shared memory)",
                 "wave": "wave (one launch per sweep, odd blocks trailing even blocks in L2)"}[kind]
     out = {"variant": "persistent" if persistent else "two_pass (CUDA graph)",
@@ -673,13 +674,14 @@ def roofline_entry(ctx, wl, rl, value_ns, peak, peak_kind):
     ms_or, kind, ms_half, ms_hb = rl
     A_half = algorithmic_half_sweep_bytes(ctx, wl, fused=True)
     A2 = algorithmic_half_sweep_bytes(ctx, wl, fused=False)
-    A = A_half if kind == "half" else 2 * A_half
+    A = A_half if kind in ("half", "staged") else 2 * A_half
     achieved = A / (ms_or * 1e-3) / 1e9
-    key = {"half": "or_half_sweep", "fused": "fused_sweep", "wave": "wave_sweep"}[kind]
+    key = {"half": "or_half_sweep", "fused": "fused_sweep", "wave": "wave_sweep",
+           "staged": "staged_half_sweep"}[kind]
     traffic = traffic_summary(f"{key}_{wl.precision}")
     floor_ns = bytes_per_update(wl, ctx.W, fused=True) / peak      # ns per update at the peak
     name = {"half": "k_half_sweep OR", "fused": "k_fused_or (one sweep)",
-            "wave": "k_wave_sweep OR (one sweep)"}[kind]
+            "wave": "k_wave_sweep OR (one sweep)", "staged": "k_staged_half OR"}[kind]
     return {"bound": "hbm",
             "kernel": f"{name} {wl.precision}",
             "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -707,7 +709,7 @@ def config_line(args, name, torch, dev, peak):
     k2 = 30 if flush else 20
     ms2, _ = timed_steps(r2["ctx"], r2["stream"], torch, k2, args.measure_every, flush=buf)
     ms_or, kind, _, _ = roofline(r2["ctx"], r2["stream"], torch, w2, half=False)
-    A = algorithmic_half_sweep_bytes(r2["ctx"], w2, fused=True) * (1 if kind == "half" else 2)
+    A = algorithmic_half_sweep_bytes(r2["ctx"], w2, fused=True) * (1 if kind in ("half", "staged") else 2)
     out = {"ns": round(ms2 * 1e6 / (sw2 * sp2 * k2), 6), "ms_step": round(ms2 / k2, 4),
            "or_frac": round(A / (ms_or * 1e-3) / 1e9 / peak, 3),
            "schedule": schedule_of(r2["ctx"].info(), short=True),

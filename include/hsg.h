@@ -127,7 +127,9 @@ typedef struct {
                                memory with bulk copies.  HSG_SWEEP_STAGED keeps one launch
                                per half-sweep but with that staged block body (same
                                conditions).  0 (default): chosen by the automatic
-                               schedule.  Results do not depend on it (bit for bit). */
+                               schedule among the half-sweep, fused and staged kernels
+                               (the wave sweep only when requested).  Results do not
+                               depend on it (bit for bit). */
   int wave_lag;             /* HSG_SWEEP_WAVE: even-parity blocks scheduled between the last
                                even block an odd block reads and that odd block (more: fewer
                                waits, more spins held in L2).  0 (default): chosen from the

@@ -579,9 +579,9 @@ int default_gpt(hsg_ctx*, const int* L, int n_samples, int G) {
 // Plan of the wave sweep for the block table `blocks` and the passes in
 // c->pass_bound.  An odd block covering planes [z0, z1] of its sample and chunk
 // group depends on the even blocks of planes z0-1 .. z1+1 (periodic; at most two
-// ranges of the table).  Per pass, the even blocks keep table order (z-major
-// within a chunk group) and each odd block is placed `lag` even blocks after the
-// last even block it depends on, so every dependency holds an earlier ticket.
+// ranges of the table).  Per pass, the even blocks go in the order (sample,
+// first site, chunk group) and each odd block is placed `lag` even blocks after
+// the last even block it depends on, so every dependency holds an earlier ticket.
 hsg_status plan_wave(hsg_ctx* c, const std::vector<int4>& blocks, int lag) {
   if (!c->d_wave_order) {
     HSG_TRY(dev_alloc(c, &c->d_wave_order, sizeof(int) * 2 * c->max_sweep_blocks));
@@ -603,6 +603,18 @@ hsg_status plan_wave(hsg_ctx* c, const std::vector<int4>& blocks, int lag) {
   std::vector<int> order(2 * (size_t)nb);
   for (size_t ps = 0; ps + 1 < c->pass_bound.size(); ++ps) {
     const int b0 = c->pass_bound[ps], b1 = c->pass_bound[ps + 1];
+    // even blocks sample by sample, plane by plane, and within a run of sites
+    // all chunk groups: the blocks in flight then cover few planes (with all
+    // their systems), which keeps what the odd blocks re-read small enough for L2
+    std::vector<int> epos_order;
+    for (int b = b0; b < b1; ++b) epos_order.push_back(b);
+    std::stable_sort(epos_order.begin(), epos_order.end(), [&](int a, int b) {
+      if (blocks[a].x != blocks[b].x) return blocks[a].x < blocks[b].x;
+      if (blocks[a].z != blocks[b].z) return blocks[a].z < blocks[b].z;
+      return blocks[a].y < blocks[b].y;
+    });
+    std::vector<int> epos(b1 - b0);
+    for (int q = 0; q < b1 - b0; ++q) epos[epos_order[q] - b0] = q;
     std::vector<std::pair<long long, int>> keyed;   // (position key, ticket code)
     keyed.reserve(2 * (size_t)(b1 - b0));
     for (int b = b0; b < b1; ++b) {
@@ -633,9 +645,13 @@ hsg_status plan_wave(hsg_ctx* c, const std::vector<int4>& blocks, int lag) {
         dep = make_int4(r.first, r.second, 0, 0);
       }
       deps[b] = dep;
-      const int last = std::max(dep.y, dep.w) - 1;
-      keyed.push_back({2ll * (b - b0), b << 1});
-      keyed.push_back({2ll * (last - b0 + lag) + 1, (b << 1) | 1});
+      if (dep.x < b0 || dep.y > b1 || dep.x >= dep.y || (dep.w > dep.z && (dep.z < b0 || dep.w > b1)))
+        return fail(c, HSG_ESTATE, "wave sweep plan: dependency outside the pass");
+      int last = 0;   // the latest position among the even blocks it depends on
+      for (int e = dep.x; e < dep.y; ++e) last = std::max(last, epos[e - b0]);
+      for (int e = dep.z; e < dep.w; ++e) last = std::max(last, epos[e - b0]);
+      keyed.push_back({2ll * epos[b - b0], b << 1});
+      keyed.push_back({2ll * ((long long)last + lag) + 1, (b << 1) | 1});
     }
     std::stable_sort(keyed.begin(), keyed.end(),
                      [](const std::pair<long long, int>& a, const std::pair<long long, int>& b) {
@@ -815,7 +831,7 @@ hsg_status copy_chain_state(hsg_ctx* c, unsigned char* host, bool to_host) {
 
 // Autotuner: the schedules, sweep kernels and chunks-per-thread settings
 // compute identical results, so they are timed on the live context and the
-// fastest is kept; the state is saved before and restored after, so the
+// fastest is kept (by a margin of 1%); the state is saved before and restored after, so the
 // Markov chain is untouched.  Each candidate runs one warm-up step, then
 // TUNE_REPS timings of 2 steps each; the median decides (a single timing let
 // noise pick between close candidates).  Results are cached per problem shape
@@ -870,7 +886,9 @@ hsg_status autotune(hsg_ctx* c) {
   if (sk == HSG_SWEEP_AUTO || sk == HSG_SWEEP_HALF) sweeps.push_back({HSG_SWEEP_HALF, 0});
   if ((sk == HSG_SWEEP_AUTO || sk == HSG_SWEEP_FUSED) && c->fused_possible && c->opt.n_or_per_step >= 3)
     sweeps.push_back({HSG_SWEEP_FUSED, 0});
-  if ((sk == HSG_SWEEP_AUTO || sk == HSG_SWEEP_WAVE) && c->wave_possible) {
+  // the wave sweep only on request (slower than two half-sweep launches on every
+  // shape measured): at the requested lag, or at half and twice the default
+  if (sk == HSG_SWEEP_WAVE && c->wave_possible) {
     if (c->opt.wave_lag > 0) {
       sweeps.push_back({HSG_SWEEP_WAVE, c->opt.wave_lag});
     } else {
@@ -879,7 +897,7 @@ hsg_status autotune(hsg_ctx* c) {
       HSG_CUDA(c, wave_occupancy(c->fmt, c->j16, c->staged_possible, smem, &per_sm));
       HSG_CUDA(c, cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, c->device));
       const int resident = std::max(4, n_sm * per_sm);
-      for (int lag : {resident / 4, resident / 2, resident}) sweeps.push_back({HSG_SWEEP_WAVE, lag});
+      for (int lag : {resident / 4, resident}) sweeps.push_back({HSG_SWEEP_WAVE, lag});
     }
   }
   if ((sk == HSG_SWEEP_AUTO || sk == HSG_SWEEP_STAGED) && c->staged_possible)
@@ -926,7 +944,10 @@ hsg_status autotune(hsg_ctx* c) {
           HSG_TRY(poll_device_error(c));
           std::sort(t, t + TUNE_REPS);
           const float ms = t[TUNE_REPS / 2];
-          if (ms < best) {
+          // a candidate replaces the current choice only when it is at least
+          // 1% faster, so that timing noise between near-equal candidates does
+          // not decide (candidates are tried simplest first)
+          if (ms < best * 0.99f) {
             best = ms;
             bestc = TuneChoice{v, g, pb, sw.first, sw.second};
           }

@@ -51,6 +51,10 @@ def test_roofline_entry_fractions():
     # the step: 12.25 B / 6686.5 GB/s = 1.832 ps against 4.177 ps
     assert rl["step_frac"] == pytest.approx(0.4386, abs=2e-3)
     # fused kernel: one launch moves a whole sweep's bytes (1.233 GB)
+    rl = bench.roofline_entry(_fake_ctx(48), wl, (0.17634, "staged", 0.17634, 0.33),
+                              value_ns=0.004177, peak=6686.5, peak_kind="measured")
+    assert rl["frac"] == pytest.approx(0.523, abs=2e-3)
+    assert rl["kernel"].startswith("k_staged_half")
     for kind in ("fused", "wave"):
         rl = bench.roofline_entry(_fake_ctx(48), wl, (0.30, kind, 0.176, 0.33), value_ns=0.0035,
                                   peak=6686.5, peak_kind="measured")
@@ -67,6 +71,8 @@ def test_launches_per_step():
     assert bench.launches_per_step(info, wl) == 2 + 4 + 2 + 2
     info.sweep_kernel = 3                    # one wave launch per OR sweep
     assert bench.launches_per_step(info, wl) == 2 + 5 + 2
+    info.sweep_kernel = 4                    # staged: one launch per half-sweep
+    assert bench.launches_per_step(info, wl) == 12 + 2
     info = types.SimpleNamespace(variant=1, sweep_kernel=1, n_passes=17, n_samples=512, Wp=32)
     assert bench.launches_per_step(info, inputs.workload("batch512_mixedL", steps=1)) == 17 * 12 + 3
 
