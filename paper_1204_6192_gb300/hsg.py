@@ -338,16 +338,33 @@ class Context:
                                                  _ptr(tunnel, ctypes.c_uint32), ctypes.byref(n)))
         return moved, tunnel, int(n.value)
 
-    def checkpoint(self) -> bytes:
-        """The chain's state as a bytes blob (hsg_checkpoint_save)."""
+    def checkpoint_size(self) -> int:
+        """Bytes of a checkpoint blob of this context (hsg_checkpoint_size)."""
         n = ctypes.c_size_t()
         self._check(lib().hsg_checkpoint_size(self._ctx, ctypes.byref(n)))
-        buf = ctypes.create_string_buffer(n.value)
-        self._check(lib().hsg_checkpoint_save(self._ctx, buf, n.value))
+        return int(n.value)
+
+    def checkpoint(self, out: Optional[np.ndarray] = None):
+        """The chain's state (hsg_checkpoint_save): a bytes blob, or written into
+        `out` (a uint8 array of at least checkpoint_size() bytes, e.g. pinned
+        host memory), which is returned."""
+        n = self.checkpoint_size()
+        if out is not None:
+            if out.dtype != np.uint8 or not out.flags.c_contiguous or out.size < n:
+                raise ValueError("out must be a contiguous uint8 array of checkpoint_size() bytes")
+            self._check(lib().hsg_checkpoint_save(self._ctx, ctypes.c_void_p(out.ctypes.data), out.size))
+            return out
+        buf = ctypes.create_string_buffer(n)
+        self._check(lib().hsg_checkpoint_save(self._ctx, buf, n))
         return buf.raw
 
-    def restore(self, blob: bytes):
-        """Load a blob from checkpoint() (hsg_checkpoint_load)."""
+    def restore(self, blob):
+        """Load a blob from checkpoint() (hsg_checkpoint_load): bytes or a uint8 array."""
+        if isinstance(blob, np.ndarray):
+            if blob.dtype != np.uint8 or not blob.flags.c_contiguous:
+                raise ValueError("blob must be a contiguous uint8 array")
+            self._check(lib().hsg_checkpoint_load(self._ctx, ctypes.c_void_p(blob.ctypes.data), blob.size))
+            return
         self._check(lib().hsg_checkpoint_load(self._ctx, blob, len(blob)))
 
     def info(self) -> Info:

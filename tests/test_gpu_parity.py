@@ -444,6 +444,26 @@ def test_checkpoint_resume_is_bit_identical(variant):
     assert ref[5:] == got[5:] == (30, 5)
 
 
+def test_checkpoint_into_caller_buffer_equals_bytes_blob():
+    """checkpoint(out=uint8 array) writes the same blob as checkpoint() (the
+    bench's end-to-end leg uploads it from pinned memory), and restore() of the
+    array continues the chain exactly as restore() of the bytes."""
+    smp = inputs.small_sample(8, n_temps=4, h_r=0.1, disorder_seed=9)
+    a = hsg.Context([smp], 2, 6, precision="fp16", j_fp16=True)
+    a.step(2)
+    blob = a.checkpoint()
+    arr = np.zeros(a.checkpoint_size() + 16, dtype=np.uint8)
+    assert a.checkpoint(out=arr) is arr
+    assert bytes(arr[:len(blob)]) == blob
+    a.step(2)
+    ref = [x.copy() for x in a.get_spins()]
+    a.restore(arr)
+    a.step(2)
+    for x, y in zip(ref, a.get_spins()):
+        np.testing.assert_array_equal(x, y)
+    a.close()
+
+
 def test_checkpoint_rejects_other_contexts():
     smp = inputs.small_sample(6, n_temps=4, disorder_seed=1)
     a = hsg.Context([smp], 2, 3)
