@@ -97,7 +97,9 @@ typedef struct {
                                out ends the launch and the next synchronising call returns
                                HSG_ETIMEOUT */
   int inject_barrier_fault; /* testing only: nonzero makes one block skip the first grid
-                               barrier of the next persistent launch, so the others time out */
+                               barrier of the next persistent launch, so the others time out,
+                               or (wave sweep, outside hsg_step) makes one odd block of the next
+                               hsg_sweep_or launch wait for a flag that no block sets */
   long long pass_bytes;     /* system blocking of hsg_step: the systems are cut into passes
                                (ranges of 4-system chunks, samples kept whole where they fit)
                                of at most this many bytes of spins plus couplings, and each

@@ -336,6 +336,16 @@ hsg_status half_sweeps(hsg_ctx* c, bool hb, int sweep_offset, bool energy = fals
     w.timeout_ns = (unsigned long long)std::max(1, c->opt.barrier_timeout_ms) * 1000000ull;
     w.t0 = 2 * b0;
     w.n_tickets = 2 * (b1 - b0);
+    w.never = (int)c->max_sweep_blocks;
+    w.inject_block = -1;
+    // fault injection (tests only; not inside a step graph, which every replay would repeat):
+    // the first odd block of the range also waits for a flag no block sets
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    HSG_CUDA(c, cudaStreamIsCapturing(c->stream, &cap));
+    if (c->inject_fault && cap == cudaStreamCaptureStatusNone) {
+      w.inject_block = b0;
+      c->inject_fault = false;
+    }
     HSG_CUDA(c, launch_wave(c->fmt, c->j16, energy, c->staged_possible, w, smem, c->stream));
     return HSG_OK;
   }
@@ -586,9 +596,10 @@ hsg_status plan_wave(hsg_ctx* c, const std::vector<int4>& blocks, int lag) {
   if (!c->d_wave_order) {
     HSG_TRY(dev_alloc(c, &c->d_wave_order, sizeof(int) * 2 * c->max_sweep_blocks));
     HSG_TRY(dev_alloc(c, &c->d_wave_deps, sizeof(int4) * c->max_sweep_blocks));
-    HSG_TRY(dev_alloc(c, &c->d_wave_flags, sizeof(unsigned int) * c->max_sweep_blocks));
+    // (one more flag than blocks: the one fault injection waits for, never set)
+    HSG_TRY(dev_alloc(c, &c->d_wave_flags, sizeof(unsigned int) * (c->max_sweep_blocks + 1)));
     HSG_TRY(dev_alloc(c, &c->d_wave_state, sizeof(unsigned int) * 4));
-    HSG_CUDA(c, cudaMemset(c->d_wave_flags, 0, sizeof(unsigned int) * c->max_sweep_blocks));
+    HSG_CUDA(c, cudaMemset(c->d_wave_flags, 0, sizeof(unsigned int) * (c->max_sweep_blocks + 1)));
     HSG_CUDA(c, cudaMemset(c->d_wave_state, 0, sizeof(unsigned int) * 4));
   }
   if (lag <= 0) {

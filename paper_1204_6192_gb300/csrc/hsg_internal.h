@@ -229,6 +229,9 @@ struct WaveParams {
   unsigned int* err;        // set when a wait ran out
   unsigned long long timeout_ns;
   int t0, n_tickets;        // this launch's tickets: order[t0 .. t0 + n_tickets)
+  // fault injection (tests only): odd block `inject_block` (-1: none) also waits
+  // for flags[never], which no block sets
+  int inject_block, never;
 };
 bool fmt_has_wave(int fmt);
 // Staged sweeps: every block copies the opposite-parity rows its sites read

@@ -334,6 +334,7 @@ __global__ void __launch_bounds__(SWEEP_BS, 4) k_wave_sweep(const WaveParams P) 
       late |= !wait_flag(P.flags + i, want, P.timeout_ns);
     for (int i = d.z + (int)threadIdx.x; i < d.w; i += SWEEP_BS)
       late |= !wait_flag(P.flags + i, want, P.timeout_ns);
+    if (b == P.inject_block && threadIdx.x == 0) late |= !wait_flag(P.flags + P.never, want, P.timeout_ns);
     __threadfence();
     if (STG) asm volatile("fence.proxy.async.global;" ::: "memory");
     if (__syncthreads_or(late)) {

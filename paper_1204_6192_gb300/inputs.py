@@ -146,6 +146,12 @@ def workload(name: str, steps: Optional[int] = None) -> Workload:
         prec = name.split("_")[1]
         w = Workload(name, [s], n_replicas=2, seed=1, precision=prec, j_fp16=True,
                      steps=5_000)
+    elif name == "L128_fp16_w16":
+        # the bench lattice with 2 replicas x 8 temperatures (201 MB of FP16 spins, more
+        # than L2): the small case for multi-pass profiler captures of the sweep kernels
+        t = geometric_temperatures(0.08, 0.3, 8)
+        s = make_sample(128, t, 0.1, disorder_seed=5)
+        w = Workload(name, [s], n_replicas=2, seed=1, precision="fp16", j_fp16=True, steps=2_000)
     elif name in ("L128_fp16", "L128_fp32", "L128_oct16", "L128_bf16", "L128_yx4"):
         t = geometric_temperatures(0.08, 0.3, 24)
         s = make_sample(128, t, 0.1, disorder_seed=5)

@@ -175,3 +175,23 @@ def test_wave_fullsize_bench_configuration():
         b = run(w.samples, w.n_replicas, w.seed, kernel, "fp16", True, n_sweeps=2, steps=1)
         assert b["staged"] == 1
         assert_same(a, b)
+
+
+def test_wave_wait_timeout_is_reported():
+    """One odd block of a wave launch waits (host-requested fault) for a
+    completion flag that no block sets: its bounded wait runs out, the launch
+    ends, the host gets HSG_ETIMEOUT (sticky), and the device stays usable for
+    a new context."""
+    smp = inputs.small_sample(16, n_temps=4, h_r=0.1, disorder_seed=16)
+    ctx = hsg.Context([smp], 2, 1, variant=hsg.VARIANT_TWO_PASS, sweep_kernel=hsg.SWEEP_WAVE,
+                      barrier_timeout_ms=200, inject_barrier_fault=True)
+    ctx.sweep_or(1)
+    with pytest.raises(hsg.HsgError) as ei:
+        ctx.sync()
+    assert ei.value.status == 4
+    with pytest.raises(hsg.HsgError):          # sticky
+        ctx.sweep_or(1)
+    ctx.close()
+    a = run([smp], 2, 1, hsg.SWEEP_HALF, n_sweeps=2)
+    b = run([smp], 2, 1, hsg.SWEEP_WAVE, n_sweeps=2)
+    assert_same(a, b)
