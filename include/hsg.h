@@ -92,8 +92,9 @@ typedef struct {
   int variant;        /* step schedule: 0 = automatic, else an HSG_VARIANT_* value */
   int barrier_timeout_ms;   /* bound of every device wait: the grid barriers of the
                                persistent schedule, the waits of the measurement kernels
-                               for their staged spin copies and of the fused and wave sweeps
-                               for their plane copies and even blocks (default 2000); a wait that runs
+                               for their staged spin copies, of the fused and staged sweeps
+                               for their row copies and of the wave sweep for its even blocks
+                               (default 2000); a wait that runs
                                out ends the launch and the next synchronising call returns
                                HSG_ETIMEOUT */
   int inject_barrier_fault; /* testing only: nonzero makes one block skip the first grid
@@ -337,8 +338,8 @@ typedef struct {
   int n_passes;            /* system-blocked passes per step (1: no blocking) */
   long long pass_bytes;    /* footprint bound of a pass in use (0: one pass) */
   int n_overlap_pairs;     /* replica pairs hsg_measure_overlaps reports (0 if n_replicas < 2) */
-  int sweep_kernel;        /* HSG_SWEEP_HALF, HSG_SWEEP_FUSED or HSG_SWEEP_WAVE: the
-                              over-relaxation sweep in use */
+  int sweep_kernel;        /* HSG_SWEEP_HALF, HSG_SWEEP_FUSED, HSG_SWEEP_WAVE or
+                              HSG_SWEEP_STAGED: the over-relaxation sweep in use */
   int fused_band_rows;     /* fused sweep: rows of y per block of sample 0 (L: whole planes) */
   int fused_items;         /* fused sweep: work items (columns of planes) per launch */
   int wave_lag;            /* wave sweep: the lag in use (even blocks) */
