@@ -102,6 +102,29 @@ def test_staged_equals_half_sweeps_l64(kernel, precision, j16):
     assert_same(a, b)
 
 
+@pytest.mark.parametrize("kernel", [hsg.SWEEP_STAGED, hsg.SWEEP_WAVE])
+def test_staged_ragged_chunk_groups(kernel):
+    """L = 64, 48 systems (12 chunk groups) at 5 chunk groups per thread: blocks
+    of 5, 5 and 2 groups, the last shorter than the two-stage ring's depth."""
+    smp = inputs.small_sample(64, n_temps=24, h_r=0.1, disorder_seed=65, t_min=0.08, t_max=0.3)
+    a = run([smp], 2, 3, hsg.SWEEP_HALF, "fp16", True, n_sweeps=2, steps=1, chunks_per_thread=5)
+    b = run([smp], 2, 3, kernel, "fp16", True, n_sweeps=2, steps=1, chunks_per_thread=5)
+    assert b["staged"] == 1
+    assert_same(a, b)
+
+
+@pytest.mark.parametrize("kernel", [hsg.SWEEP_STAGED, hsg.SWEEP_WAVE])
+def test_staged_l256_two_rows_per_block(kernel):
+    """L = 256 (16.8M sites, 2 rows of 128 sites per block), 2 x 4 systems,
+    FP16 spins and couplings: two OR sweeps and a step against the per-half-sweep
+    kernel, bit for bit."""
+    smp = inputs.small_sample(256, n_temps=4, h_r=0.1, disorder_seed=256, t_min=0.1, t_max=0.4)
+    a = run([smp], 2, 5, hsg.SWEEP_HALF, "fp16", True, n_sweeps=2, steps=1)
+    b = run([smp], 2, 5, kernel, "fp16", True, n_sweeps=2, steps=1)
+    assert b["staged"] == 1
+    assert_same(a, b)
+
+
 @pytest.mark.parametrize("lag", [1, 100, 1 << 20])
 def test_staged_wave_lags_and_mixed_batch(lag):
     """A batch of L = 32, 64, 32 (16 and 8 rows per block, stage size of the
