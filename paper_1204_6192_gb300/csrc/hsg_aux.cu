@@ -189,14 +189,44 @@ cudaError_t launch_pt(const PTParams& p, cudaStream_t st) {
 // block, for steps with few systems: each warp sums the level-1 partials of its
 // systems (the same code and order as k_energy_final2), then, after a block
 // barrier, one thread per chain walks its pairs as k_pt does.  One launch
-// instead of two.
-__global__ void __launch_bounds__(1024) k_energy2_pt(const EnergyParams e, const PTParams p) {
+// instead of two.  With `staged`, the permutations, energies and inverse
+// temperatures are first copied into shared memory (dynamic, laid out as
+// [samples][Wp] and [samples][R_T] doubles, then [chains][R_T] ints and the
+// chains' uniforms [chains][R_T - 1]): each pair of a chain reads its slot's
+// configuration and then that configuration's energy, two dependent loads that
+// now hit shared memory instead of L2, and the uniforms are drawn by all threads
+// at once instead of by each chain's thread.  The same arithmetic on the same
+// values, so the same decisions.
+__global__ void __launch_bounds__(1024) k_energy2_pt(const EnergyParams e, const PTParams p, int staged) {
+  extern __shared__ double pt_smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int gw = warp; gw < e.n_samples * e.Wp; gw += nw)
     energy_final2_warp<false>(e, gw / e.Wp, gw % e.Wp, lane);
   __syncthreads();
   const int n_chains = p.n_samples * p.R_O;
-  for (int c = threadIdx.x; c < n_chains; c += blockDim.x) pt_chain<false>(p, c);
+  if (staged) {
+    const int np = n_chains * p.R_T, ne = p.n_samples * p.Wp, nb = p.n_samples * p.R_T;
+    const int R1 = p.R_T > 1 ? p.R_T - 1 : 1, nu = n_chains * R1;
+    double* sE = pt_smem;
+    double* sib = sE + ne;
+    int* sperm = reinterpret_cast<int*>(sib + nb);
+    float* su = reinterpret_cast<float*>(sperm + np);
+    for (int i = threadIdx.x; i < ne; i += blockDim.x) sE[i] = p.E[i];
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) sib[i] = p.inv_temps[i];
+    for (int i = threadIdx.x; i < np; i += blockDim.x) sperm[i] = p.perm[i];
+    if (p.bump_pt)
+      for (int i = threadIdx.x; i < nu; i += blockDim.x) su[i] = pt_uniform(p, i / R1, i % R1);
+    __syncthreads();
+    for (int c = threadIdx.x; c < n_chains; c += blockDim.x) {
+      const int s = c / p.R_O, r = c - s * p.R_O;
+      pt_chain_on<false>(p, c, sperm + c * p.R_T, sE + s * p.Wp + r * p.R_T, sib + s * p.R_T,
+                         su + c * R1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < np; i += blockDim.x) p.perm[i] = sperm[i];
+  } else {
+    for (int c = threadIdx.x; c < n_chains; c += blockDim.x) pt_chain<false>(p, c);
+  }
   __syncthreads();
   for (int s = threadIdx.x; s < p.n_samples; s += blockDim.x) {
     if (!p.active[s]) continue;
@@ -216,7 +246,12 @@ cudaError_t launch_energy_final_pt(const EnergyParams& e, const PTParams& p, cud
   k_energy_final1<<<dim3(e.splits, (e.Wp + 31) / 32, e.n_samples), 256, 0, st>>>(e);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  k_energy2_pt<<<1, 1024, 0, st>>>(e, p);
+  // shared-memory copies of the chains (48 kB at most without an opt-in)
+  const size_t n_chains = (size_t)p.n_samples * p.R_O;
+  const size_t smem = sizeof(double) * ((size_t)p.n_samples * p.Wp + (size_t)p.n_samples * p.R_T) +
+                      sizeof(int) * n_chains * p.R_T + sizeof(float) * n_chains * std::max(1, p.R_T - 1);
+  const bool staged = smem <= 48 * 1024;
+  k_energy2_pt<<<1, 1024, staged ? smem : 0, st>>>(e, p, staged ? 1 : 0);
   return cudaGetLastError();
 }
 

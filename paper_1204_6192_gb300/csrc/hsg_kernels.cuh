@@ -281,15 +281,17 @@ __device__ __forceinline__ bool pt_accept(double x, float u) {
 // temperature random walk (Sec. 4): per slot, the passes after which the
 // configuration that held it has moved (p_diff = moved / passes), and per
 // configuration the closed loops T_1 -> T_R -> T_1 (tunnelling events).
+// The chain's permutation row, energies and inverse temperatures are read (and
+// the permutation written) through perm, E and ib: the global arrays, or copies
+// in shared memory (then CG is false and the caller writes perm back).  uf: the
+// chain's R_T - 1 uniforms, drawn beforehand (same counters), or null.
 template <bool CG>
-__device__ __forceinline__ void pt_chain(const PTParams& p, int c) {
+__device__ __forceinline__ void pt_chain_on(const PTParams& p, int c, int* perm, const double* E,
+                                            const double* ib, const float* uf = nullptr) {
   const int s = c / p.R_O, r = c - s * p.R_O;
   if (!p.active[s]) return;
   // the sample's own PT pass counter keys its random numbers
   const uint32_t step = (uint32_t)(CG ? __ldcg(p.counters + 2 * s + 1) : p.counters[2 * s + 1]);
-  int* perm = p.perm + (long long)c * p.R_T;
-  const double* E = p.E + (long long)s * p.Wp + r * p.R_T;
-  const double* ib = p.inv_temps + (long long)s * p.R_T;
   if (p.bump_pt) {
     unsigned long long* moved = p.moved + (long long)c * p.R_T;
     bool prev_acc = false;
@@ -297,7 +299,7 @@ __device__ __forceinline__ void pt_chain(const PTParams& p, int c) {
     // time ahead of the sequential chain, so the Philox evaluations overlap
     float uk[32];
     for (int k = 0; k + 1 < p.R_T; ++k) {
-      if ((k & 31) == 0) {
+      if (!uf && (k & 31) == 0) {
 #pragma unroll 4
         for (int j = 0; j < 32; ++j)
           uk[j] = (k + j + 1 < p.R_T)
@@ -309,7 +311,7 @@ __device__ __forceinline__ void pt_chain(const PTParams& p, int c) {
       const double dbeta = ib[k + 1] - ib[k];
       const double dE = (CG ? __ldcg(E + b) : E[b]) - (CG ? __ldcg(E + a) : E[a]);
       const double x = dbeta * dE;
-      const bool acc = pt_accept(x, uk[k & 31]);
+      const bool acc = pt_accept(x, uf ? uf[k] : uk[k & 31]);
       // the configuration that held slot k before the pass moved iff pair (k-1, k)
       // moved it down or, failing that, pair (k, k+1) moved it up
       if (acc || prev_acc) moved[k] += 1ull;
@@ -333,6 +335,20 @@ __device__ __forceinline__ void pt_chain(const PTParams& p, int c) {
   }
   float* beta = p.beta + (long long)s * p.Wp + r * p.R_T;
   for (int t = 0; t < p.R_T; ++t) beta[perm[t]] = (float)ib[t];
+}
+
+// The uniform of pair k of chain c in the current PT pass (as pt_chain_on draws it).
+__device__ __forceinline__ float pt_uniform(const PTParams& p, int c, int k) {
+  const int s = c / p.R_O;
+  const uint32_t step = (uint32_t)p.counters[2 * s + 1];
+  return u01(philox4x32_10(make_uint4((uint32_t)k, (uint32_t)c, step, TAG_PT), p.seed_lo, p.seed_hi).x);
+}
+
+template <bool CG>
+__device__ __forceinline__ void pt_chain(const PTParams& p, int c) {
+  const int s = c / p.R_O, r = c - s * p.R_O;
+  pt_chain_on<CG>(p, c, p.perm + (long long)c * p.R_T, p.E + (long long)s * p.Wp + r * p.R_T,
+                  p.inv_temps + (long long)s * p.R_T);
 }
 
 }  // namespace hsg
