@@ -439,6 +439,8 @@ void orc_pt(const double* E, const double* temps, int32_t* perm, int R_O, int R_
 void orc_measure(const double* s, int L, int R_T, const int32_t* perm, double* q,
                  double* qk) {
   long N = (long)L * L * L;
+  /* temperature slots are independent: each keeps its own sums in site order */
+#pragma omp parallel for schedule(static)
   for (int t = 0; t < R_T; ++t) {
     const double* sa = s + 3 * (long)perm[t] * N;
     const double* sb = s + 3 * ((long)R_T + perm[R_T + t]) * N;
@@ -446,14 +448,20 @@ void orc_measure(const double* s, int L, int R_T, const int32_t* perm, double* q
     double acck[3][3][3][2] = {{{{0}}}};
     for (long i = 0; i < N; ++i) {
       int coord[3] = {(int)(i % L), (int)((i / L) % L), (int)(i / ((long)L * L))};
+      /* e^{i k_a x_a} of this site for the three modes */
+      double cs[3], sn[3];
+      for (int a = 0; a < 3; ++a) {
+        double arg = 2.0 * ORC_PI * (double)coord[a] / (double)L;
+        cs[a] = cos(arg);
+        sn[a] = sin(arg);
+      }
       for (int mu = 0; mu < 3; ++mu) {
         for (int nu = 0; nu < 3; ++nu) {
           double p = sa[3 * i + mu] * sb[3 * i + nu];
           acc[mu][nu] += p;
           for (int a = 0; a < 3; ++a) {
-            double arg = 2.0 * ORC_PI * (double)coord[a] / (double)L;
-            acck[a][mu][nu][0] += p * cos(arg);
-            acck[a][mu][nu][1] += p * sin(arg);
+            acck[a][mu][nu][0] += p * cs[a];
+            acck[a][mu][nu][1] += p * sn[a];
           }
         }
       }

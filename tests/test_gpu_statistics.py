@@ -74,15 +74,19 @@ def series_gpu(smp, steps, precision="fp32", j16=False, fast_math=False, seed=1)
     return np.array(E), np.array(Q)
 
 
-def series_oracle(smp, steps, seed=1):
+def series_oracle(smp, steps, seed=1, skip=0):
+    """The oracle's series; the first `skip` steps are run but not measured."""
     sim = oracle.OracleSim([smp], 2, seed)
     E, Q = [], []
-    for _ in range(steps):
+    for k in range(steps):
         sim.step(1)
+        if k < skip:
+            continue
         m = sim.measure()[0]
         E.append(m["E"])
         Q.append((m["q"] ** 2).sum(axis=(1, 2)))
     return np.array(E), np.array(Q)
+
 
 
 def per_slot(E, Q, N):
@@ -97,16 +101,18 @@ def binned(x, nbins):
     return x.mean(axis=0), bins.std(axis=0, ddof=1) / np.sqrt(nbins)
 
 
-def ensemble(runner, smp, N):
+def ensemble(runner, smp, N, measured_from=0):
     """Per run (seed) and slot, the means of e(T) and q^2 over steps
-    ENSEMBLE_SKIP.. of the run: arrays [runs, slots]."""
+    ENSEMBLE_SKIP.. of the run: arrays [runs, slots].  runner(seed) returns the
+    series from step `measured_from` on."""
     e, q = [], []
     for seed in range(1, ENSEMBLE_SEEDS + 1):
         E, Q = runner(seed)
         ee, qq = per_slot(E, Q, N)
-        e.append(ee[ENSEMBLE_SKIP:].mean(axis=0))
-        q.append(qq[ENSEMBLE_SKIP:].mean(axis=0))
+        e.append(ee[ENSEMBLE_SKIP - measured_from:].mean(axis=0))
+        q.append(qq[ENSEMBLE_SKIP - measured_from:].mean(axis=0))
     return np.array(e), np.array(q)
+
 
 
 def paired(gpu, orc, shape):
@@ -155,7 +161,8 @@ def oracle_reference(shape, fp16_couplings):
         if SHAPES[shape][7]:
             ref = per_slot(*series_oracle(smp, steps), N=N)
         else:
-            ref = ensemble(lambda sd: series_oracle(smp, steps, seed=sd), smp, N)
+            ref = ensemble(lambda sd: series_oracle(smp, steps, seed=sd, skip=ENSEMBLE_SKIP), smp, N,
+                           measured_from=ENSEMBLE_SKIP)
         _cache[key] = (smp, ref)
     return _cache[key]
 
