@@ -137,6 +137,9 @@ typedef struct {
                                even block an odd block reads and that odd block (more: fewer
                                waits, more spins held in L2).  0 (default): chosen from the
                                number of resident blocks and by the automatic schedule. */
+  int inject_alloc_fault;   /* testing only: n > 0 makes the n-th device allocation of the
+                               context fail as an out-of-memory would (HSG_ENOMEM; during
+                               hsg_create the partial context is released); 0: off */
 } hsg_options;
 
 enum {

@@ -16,6 +16,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhsg.so")
+# the same library with device bounds checks compiled in (-DHSG_CHECK)
+BUILD_CHECK = os.path.join(HERE, "_build_check")
+LIB_CHECK = os.path.join(HERE, "libhsg_check.so")
 SOURCES = ["hsg_api.cu", "hsg_sweep.cu", "hsg_aux.cu", "hsg_persist.cu", "hsg_noalloc.cu",
            "hsg_overlap.cu", "hsg_multihit.cu", "hsg_fused.cu", "hsg_wave.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -51,17 +54,22 @@ def _stale(obj: str, src: str) -> bool:
     return any(os.path.getmtime(d) > t for d in [src] + _deps())
 
 
-def build(verbose: bool = False, force: bool = False, extra_flags=None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, force: bool = False, extra_flags=None, check: bool = False) -> str:
+    """Build libhsg.so (check=True: libhsg_check.so, with the device bounds
+    checks of HSG_CHECK compiled in) and return its path."""
+    build_dir, lib = (BUILD_CHECK, LIB_CHECK) if check else (BUILD, LIB)
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                     "-I", os.path.join(ROOT, "include")] + list(extra_flags or [])
+    if check:
+        flags.append("-DHSG_CHECK")
     if verbose:
         flags += ["-Xptxas", "-v"]
 
     def compile_one(src):
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(build_dir, src.replace(".cu", ".o"))
         if force or verbose or _stale(o, s):
             p = subprocess.run([cc, "-c", s, "-o", o] + flags, capture_output=True, text=True)
             if p.returncode != 0:
@@ -75,14 +83,14 @@ def build(verbose: bool = False, force: bool = False, extra_flags=None) -> str:
     if verbose:
         for _, log in results:
             sys.stderr.write(log)
-    if force or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        tmp = LIB + ".tmp"
+    if force or not os.path.exists(lib) or any(os.path.getmtime(o) > os.path.getmtime(lib) for o in objs):
+        tmp = lib + ".tmp"
         p = subprocess.run([cc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static"],
                            capture_output=True, text=True)
         if p.returncode != 0:
             raise RuntimeError("link failed:\n" + p.stderr)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

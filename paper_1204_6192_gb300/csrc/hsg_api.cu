@@ -3,6 +3,7 @@
 // tempering and measurements, and the C ABI declared in include/hsg.h.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -91,7 +92,7 @@ struct hsg_ctx {
   int variant = HSG_VARIANT_TWO_PASS;   // resolved step schedule
   bool tune_pending = false;            // automatic schedule not yet tuned
   long long max_sweep_blocks = 0;       // sweep table capacity (one chunk per thread)
-  unsigned int* d_bar = nullptr;        // grid barrier: arrivals, generation, error word; [3] measurement error word; [4] fused sweep error word; [5] wave sweep error word
+  unsigned int* d_bar = nullptr;        // grid barrier: arrivals, generation, error word; [3] measurement error word; [4] fused sweep error word; [5] wave and staged sweep error word; [6] device bounds checks (HSG_CHECK builds)
   int persist_grid = 0;
   size_t persist_smem = 0;
   bool inject_fault = false;
@@ -138,6 +139,8 @@ struct hsg_ctx {
   hsg_status err = HSG_OK;
   std::string msg;
   std::vector<void*> allocations;
+  int alloc_count = 0;                  // device allocations made
+  int alloc_fail_at = 0;                // fault injection: fail this allocation (1-based; 0: off)
 };
 
 namespace {
@@ -175,6 +178,16 @@ hsg_status bad_arg(hsg_ctx* c, const std::string& m) {
     if ((ctx)->err != HSG_OK) return (ctx)->err; \
   } while (0)
 
+// An NVTX range named after the API call for the duration of the host call
+// (the GPU work it enqueues shows under it in a profiler's timeline; without
+// a profiler attached a push and pop are a few instructions).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 void fastdiv(uint32_t d, uint32_t* m, uint32_t* s) {
   uint32_t l = 0;
   while ((1ull << l) < d) ++l;
@@ -184,6 +197,8 @@ void fastdiv(uint32_t d, uint32_t* m, uint32_t* s) {
 
 template <typename T>
 hsg_status dev_alloc(hsg_ctx* c, T** p, size_t bytes) {
+  if (c->alloc_fail_at > 0 && ++c->alloc_count == c->alloc_fail_at)
+    return fail(c, HSG_ENOMEM, "cudaMalloc(" + std::to_string(bytes) + "): injected allocation failure");
   void* q = nullptr;
   cudaError_t e = cudaMalloc(&q, bytes > 0 ? bytes : 16);
   if (e != cudaSuccess) {
@@ -230,6 +245,7 @@ SweepParams sweep_params(hsg_ctx* c, int parity, int sweep_offset) {
   p.stage_bytes = c->staged_possible ? staged_stage_bytes(c->fmt, c->Lh_max) : 0;
   p.stage_off = 0;
   p.err = c->d_bar + 5;
+  p.bounds_err = c->d_bar + 6;
   p.timeout_ns = (unsigned long long)std::max(1, c->opt.barrier_timeout_ms) * 1000000ull;
   uint32_t k0 = c->seed_lo, k1 = c->seed_hi;
   for (int r = 0; r < 10; ++r) {
@@ -536,8 +552,9 @@ hsg_status enqueue_step(hsg_ctx* c) {
 // A bounded device wait that ran out (persistent schedule, staged measurement)
 // after the stream has been synchronised.
 hsg_status poll_device_error(hsg_ctx* c) {
-  unsigned int err[4] = {0u, 0u, 0u, 0u};
+  unsigned int err[5] = {0u, 0u, 0u, 0u, 0u};
   HSG_CUDA(c, cudaMemcpy(err, c->d_bar + 2, sizeof(err), cudaMemcpyDeviceToHost));
+  if (err[4]) return fail(c, HSG_ESTATE, "a device bounds check of a sweep kernel failed (HSG_CHECK build)");
   if (err[0]) return fail(c, HSG_ETIMEOUT, "a grid barrier wait of the persistent step kernel timed out");
   if (err[1]) return fail(c, HSG_ETIMEOUT, "a wait for a staged spin copy of a measurement kernel timed out");
   if (err[2]) return fail(c, HSG_ETIMEOUT, "a wait for a staged plane copy of the fused sweep kernel timed out");
@@ -1005,6 +1022,7 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   if (opt.sweep_kernel < HSG_SWEEP_AUTO || opt.sweep_kernel > HSG_SWEEP_STAGED)
     return bad_arg(nullptr, "unknown sweep_kernel");
   if (opt.wave_lag < 0) return bad_arg(nullptr, "wave_lag < 0");
+  if (opt.inject_alloc_fault < 0) return bad_arg(nullptr, "inject_alloc_fault < 0");
   const int W = n_temps * n_replicas;
   if (W > 1024) return bad_arg(nullptr, "n_temps * n_replicas must be <= 1024");
   const int Wp = (W + 7) / 8 * 8;
@@ -1029,6 +1047,7 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
 
   hsg_ctx* c = new hsg_ctx();
   c->opt = opt;
+  c->alloc_fail_at = opt.inject_alloc_fault;
   c->device = opt.device;
   c->fmt = fmt;
   c->VEC = VEC;
@@ -1176,7 +1195,7 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   HSG_ALLOC(c->d_acc, sizeof(unsigned long long) * n_samples * n_replicas * std::max(1, n_temps - 1));
   HSG_ALLOC(c->d_counters, sizeof(unsigned long long) * 2 * n_samples);
   HSG_ALLOC(c->d_active, sizeof(unsigned char) * n_samples);
-  HSG_ALLOC(c->d_bar, sizeof(unsigned int) * 6);
+  HSG_ALLOC(c->d_bar, sizeof(unsigned int) * 8);
   HSG_ALLOC(c->d_moved, sizeof(unsigned long long) * n_samples * n_replicas * n_temps);
   HSG_ALLOC(c->d_tstate, sizeof(unsigned char) * n_samples * n_replicas * n_temps);
   HSG_ALLOC(c->d_tunnel, sizeof(unsigned int) * n_samples * n_replicas * n_temps);
@@ -1237,7 +1256,7 @@ hsg_status create_impl(hsg_ctx** out, int n_samples, const int* L, const double*
   if (e == cudaSuccess) e = cudaMemset(c->d_moved, 0, sizeof(unsigned long long) * perm.size());
   if (e == cudaSuccess) e = cudaMemset(c->d_tunnel, 0, sizeof(unsigned int) * perm.size());
   if (e == cudaSuccess) e = cudaMemset(c->d_E, 0, sizeof(double) * n_samples * Wp);
-  if (e == cudaSuccess) e = cudaMemset(c->d_bar, 0, sizeof(unsigned int) * 6);
+  if (e == cudaSuccess) e = cudaMemset(c->d_bar, 0, sizeof(unsigned int) * 8);
   if (e == cudaSuccess) e = cudaMemset(c->spins, 0, c->spin_bytes);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -1295,6 +1314,7 @@ void hsg_default_options(hsg_options* opt) {
 
 hsg_status hsg_create(hsg_ctx** out, int L, const double* temps, int n_temps, int n_replicas,
                       const float* J, const float* H, uint64_t seed, const hsg_options* opt) {
+  NvtxRange nvtx_("hsg_create");
   const float* Jp[1] = {J};
   const float* Hp[1] = {H};
   return create_impl(out, 1, &L, temps, n_temps, n_replicas, Jp, Hp, seed, opt);
@@ -1303,10 +1323,12 @@ hsg_status hsg_create(hsg_ctx** out, int L, const double* temps, int n_temps, in
 hsg_status hsg_create_batch(hsg_ctx** out, int n_samples, const int* L, const double* temps,
                             int n_temps, int n_replicas, const float* const* J,
                             const float* const* H, uint64_t seed, const hsg_options* opt) {
+  NvtxRange nvtx_("hsg_create_batch");
   return create_impl(out, n_samples, L, temps, n_temps, n_replicas, J, H, seed, opt);
 }
 
 hsg_status hsg_sweep_or(hsg_ctx* c, int n) {
+  NvtxRange nvtx_("hsg_sweep_or");
   HSG_CHECK_CTX(c);
   if (n < 0) return bad_arg(c, "n_sweeps < 0");
   if (n == 0) return HSG_OK;
@@ -1318,6 +1340,7 @@ hsg_status hsg_sweep_or(hsg_ctx* c, int n) {
 }
 
 hsg_status hsg_sweep_hb(hsg_ctx* c, int n) {
+  NvtxRange nvtx_("hsg_sweep_hb");
   HSG_CHECK_CTX(c);
   if (n < 0) return bad_arg(c, "n_sweeps < 0");
   if (n == 0) return HSG_OK;
@@ -1329,6 +1352,7 @@ hsg_status hsg_sweep_hb(hsg_ctx* c, int n) {
 }
 
 hsg_status hsg_pt_exchange(hsg_ctx* c) {
+  NvtxRange nvtx_("hsg_pt_exchange");
   HSG_CHECK_CTX(c);
   HSG_CUDA(c, cudaSetDevice(c->device));
   HSG_TRY(enqueue_energy(c));
@@ -1338,6 +1362,7 @@ hsg_status hsg_pt_exchange(hsg_ctx* c) {
 }
 
 hsg_status hsg_pt_exchange_energies(hsg_ctx* c, const double* E_sys) {
+  NvtxRange nvtx_("hsg_pt_exchange_energies");
   HSG_CHECK_CTX(c);
   if (!E_sys) return bad_arg(c, "E_sys is NULL");
   HSG_CUDA(c, cudaSetDevice(c->device));
@@ -1376,6 +1401,7 @@ static hsg_status multihit_table(hsg_ctx* c, int T) {
 }
 
 hsg_status hsg_step_multihit(hsg_ctx* c, int n_steps, int tile, int n_rounds, int n_or, int n_hb) {
+  NvtxRange nvtx_("hsg_step_multihit");
   HSG_CHECK_CTX(c);
   if (n_steps < 0) return bad_arg(c, "n_steps < 0");
   if (tile != 4 && tile != 8) return bad_arg(c, "tile must be 4 or 8");
@@ -1415,6 +1441,7 @@ hsg_status hsg_step_multihit(hsg_ctx* c, int n_steps, int tile, int n_rounds, in
 }
 
 hsg_status hsg_step(hsg_ctx* c, int n_steps) {
+  NvtxRange nvtx_("hsg_step");
   HSG_CHECK_CTX(c);
   if (n_steps < 0) return bad_arg(c, "n_steps < 0");
   if (n_steps == 0) return HSG_OK;
@@ -1426,6 +1453,7 @@ hsg_status hsg_step(hsg_ctx* c, int n_steps) {
 }
 
 hsg_status hsg_energies(hsg_ctx* c, double* E_sys) {
+  NvtxRange nvtx_("hsg_energies");
   HSG_CHECK_CTX(c);
   if (!E_sys) return bad_arg(c, "E_sys is NULL");
   HSG_CUDA(c, cudaSetDevice(c->device));
@@ -1472,6 +1500,7 @@ static OverlapParams overlap_params(hsg_ctx* c, const StagedGeom& g) {
 }
 
 hsg_status hsg_measure(hsg_ctx* c, hsg_obs* o) {
+  NvtxRange nvtx_("hsg_measure");
   HSG_CHECK_CTX(c);
   if (!o) return bad_arg(c, "obs is NULL");
   HSG_CUDA(c, cudaSetDevice(c->device));
@@ -1567,6 +1596,7 @@ static hsg_status ensure_kappa(hsg_ctx* c, int Gu) {
 }
 
 hsg_status hsg_measure_overlaps(hsg_ctx* c, double* D, double* C) {
+  NvtxRange nvtx_("hsg_measure_overlaps");
   HSG_CHECK_CTX(c);
   if (!D && !C) return bad_arg(c, "D and C are both NULL");
   if (c->R_O < 2) return bad_arg(c, "overlaps need n_replicas >= 2");
@@ -1635,6 +1665,7 @@ hsg_status hsg_measure_overlaps(hsg_ctx* c, double* D, double* C) {
 }
 
 hsg_status hsg_get_spins(hsg_ctx* c, float* xyz) {
+  NvtxRange nvtx_("hsg_get_spins");
   HSG_CHECK_CTX(c);
   if (!xyz) return bad_arg(c, "xyz is NULL");
   HSG_CUDA(c, cudaSetDevice(c->device));
@@ -1648,6 +1679,7 @@ hsg_status hsg_get_spins(hsg_ctx* c, float* xyz) {
 }
 
 hsg_status hsg_set_spins(hsg_ctx* c, const float* xyz) {
+  NvtxRange nvtx_("hsg_set_spins");
   HSG_CHECK_CTX(c);
   if (!xyz) return bad_arg(c, "xyz is NULL");
   HSG_CUDA(c, cudaSetDevice(c->device));
@@ -1752,6 +1784,7 @@ hsg_status hsg_checkpoint_size(hsg_ctx* c, size_t* bytes) {
 }
 
 hsg_status hsg_checkpoint_save(hsg_ctx* c, void* buf, size_t bytes) {
+  NvtxRange nvtx_("hsg_checkpoint_save");
   HSG_CHECK_CTX(c);
   if (!buf) return bad_arg(c, "buf is NULL");
   const size_t need = sizeof(CheckpointHeader) + c->spin_bytes + chain_state_bytes(c);
@@ -1783,6 +1816,7 @@ hsg_status hsg_checkpoint_save(hsg_ctx* c, void* buf, size_t bytes) {
 }
 
 hsg_status hsg_checkpoint_load(hsg_ctx* c, const void* buf, size_t bytes) {
+  NvtxRange nvtx_("hsg_checkpoint_load");
   HSG_CHECK_CTX(c);
   if (!buf) return bad_arg(c, "buf is NULL");
   if (bytes < sizeof(CheckpointHeader)) return bad_arg(c, "checkpoint too short");

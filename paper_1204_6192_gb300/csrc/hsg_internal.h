@@ -73,7 +73,18 @@ struct SweepParams {
   int stage_bytes, stage_off;
   unsigned int* err;
   unsigned long long timeout_ns;
+  unsigned int* bounds_err;  // HSG_CHECK builds: set when a device bounds check fails
 };
+
+// Device bounds checks of the sweep kernels, compiled in with -DHSG_CHECK: a
+// check that fails records it in an error word (the host reports HSG_ESTATE)
+// and the caller skips the access; nothing traps.  Without HSG_CHECK the
+// condition is not evaluated and the access goes ahead.
+#ifdef HSG_CHECK
+#define HSG_OUT_OF_BOUNDS(cond, errword) (!(cond) ? (atomicExch((errword), 1u), true) : false)
+#else
+#define HSG_OUT_OF_BOUNDS(cond, errword) false
+#endif
 
 struct EnergyParams {
   const unsigned char* spins;

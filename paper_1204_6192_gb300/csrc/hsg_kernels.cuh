@@ -22,7 +22,7 @@ __device__ __forceinline__ void sweep_block(const SweepParams& p, int bidx, floa
   const SampleDev& sd = p.samples[blk.x];
   const uint32_t h = (uint32_t)blk.z + threadIdx.x;
   const uint32_t half_n = (uint32_t)sd.N >> 1;
-  const bool active = h < half_n;
+  bool active = h < half_n;
   if (!EN && !active) return;
   const int g0 = blk.y * p.GPT;
   const int g1 = min(p.G, g0 + p.GPT);
@@ -43,6 +43,21 @@ __device__ __forceinline__ void sweep_block(const SweepParams& p, int bidx, floa
   long long nb_off[6], own_off = 0;
   if (active) {
     gm = site_geom(sd, h, p.parity);
+    {
+      // HSG_CHECK builds: the site in this parity's half, its neighbours in the
+      // other half, the chunk groups within the sample (else skip the site)
+      const uint32_t own0 = (uint32_t)p.parity * half_n, nb0 = (uint32_t)(1 - p.parity) * half_n;
+      bool bad = HSG_OUT_OF_BOUNDS(gm.own >= own0 && gm.own < own0 + half_n && g1 <= p.G, p.bounds_err);
+#pragma unroll
+      for (int n = 0; n < 6; ++n)
+        bad = bad || HSG_OUT_OF_BOUNDS(gm.nb[n] >= nb0 && gm.nb[n] < nb0 + half_n, p.bounds_err);
+      if (bad) {
+        active = false;
+        if (!EN) return;
+      }
+    }
+  }
+  if (active) {
     load_record<J16>(p.rec, sd.rec_off + gm.own, j6, h3);
     if (MIXED) load_record_j16(p.rec, sd.rec_off + gm.own, jh);
     if constexpr (EN) {

@@ -116,6 +116,13 @@ __device__ __forceinline__ void staged_block(const SweepParams& p, int bidx, uns
       c_src = sd.spin_off + (long long)pl * sd.plane_stride + (long long)(ob + (uint32_t)row * Lh) * CH;
       c_dst = (uint32_t)((pl * pc + dst) * CH);
       c_bytes = (uint32_t)(nrows * Lh * CH);
+      // HSG_CHECK builds: the rows within the opposite half, the copy within its
+      // stage (else copy the same number of bytes from the plane's start: the
+      // stage's byte count still completes, the results are flagged)
+      if (HSG_OUT_OF_BOUNDS(row >= 0 && (long long)(row + nrows) * Lh <= (long long)half_n &&
+                                c_dst + c_bytes <= (uint32_t)p.stage_bytes,
+                            p.bounds_err))
+        c_src = sd.spin_off + (long long)pl * sd.plane_stride;
     }
   }
   auto issue = [&](int i) {   // the copies of chunk group g0 + i into stage i % S (one warp)
@@ -151,7 +158,21 @@ __device__ __forceinline__ void staged_block(const SweepParams& p, int bidx, uns
   off[3] = lr * Lh + hx;
   off[4] = (2 * R + 2) * Lh + lr * Lh + hx;
   off[5] = (R + 2) * Lh + lr * Lh + hx;
-  const uint32_t own = (uint32_t)par * half_n + (uint32_t)blk.z + (uint32_t)tid;
+  uint32_t own = (uint32_t)par * half_n + (uint32_t)blk.z + (uint32_t)tid;
+  bool store_ok = true;
+  {
+    // HSG_CHECK builds: the site in this parity's half and its neighbours within
+    // the stage plane (else read in-bounds slots and write nothing back)
+    bool bad = HSG_OUT_OF_BOUNDS((uint32_t)blk.z + (uint32_t)tid < half_n, p.bounds_err);
+#pragma unroll
+    for (int n = 0; n < 6; ++n) bad = bad || HSG_OUT_OF_BOUNDS(off[n] >= 0 && off[n] < pc, p.bounds_err);
+    if (bad) {
+      own = (uint32_t)par * half_n;
+#pragma unroll
+      for (int n = 0; n < 6; ++n) off[n] = 0;
+      store_ok = false;
+    }
+  }
   float j6[6], h3[3];
   uint32_t jh[6];
   load_record<J16>(p.rec, sd.rec_off + own, j6, h3);
@@ -254,7 +275,7 @@ __device__ __forceinline__ void staged_block(const SweepParams& p, int bidx, uns
 #pragma unroll
     for (int k = 0; k < VEC / 2; ++k) or_move2(sv.x[k], sv.y[k], sv.z[k], hf.x[k], hf.y[k], hf.z[k]);
     encode<F>(sv, c);
-    store_chunks<F>(own_p, ps, c);
+    if (store_ok) store_chunks<F>(own_p, ps, c);
     if constexpr (EN) {
       // energy of the new state from the stored values: every bond joins one
       // odd and one even site, E = - sum_odd s_i.h_i - sum_even H_j.s_j

@@ -37,7 +37,8 @@ class Options(ctypes.Structure):
                 ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("variant", ctypes.c_int),
                 ("barrier_timeout_ms", ctypes.c_int), ("inject_barrier_fault", ctypes.c_int),
                 ("pass_bytes", ctypes.c_longlong), ("chunks_per_thread", ctypes.c_int),
-                ("sweep_kernel", ctypes.c_int), ("wave_lag", ctypes.c_int)]
+                ("sweep_kernel", ctypes.c_int), ("wave_lag", ctypes.c_int),
+                ("inject_alloc_fault", ctypes.c_int)]
 
 
 class Obs(ctypes.Structure):
@@ -60,6 +61,15 @@ class Info(ctypes.Structure):
 
 
 _lib = None
+
+
+def use_library(path: str):
+    """Load this build of the library instead of libhsg.so (e.g. libhsg_check.so,
+    the build with device bounds checks); call before anything else of this module."""
+    global LIB_PATH
+    if _lib is not None:
+        raise RuntimeError("the library is already loaded")
+    LIB_PATH = path
 
 
 def lib() -> ctypes.CDLL:
@@ -140,7 +150,7 @@ class Context:
                  device: int = 0, stream: Optional[int] = None, variant: int = VARIANT_AUTO,
                  barrier_timeout_ms: int = 2000, inject_barrier_fault: bool = False,
                  pass_bytes: int = 0, chunks_per_thread: int = 0, sweep_kernel: int = SWEEP_AUTO,
-                 wave_lag: int = 0):
+                 wave_lag: int = 0, inject_alloc_fault: int = 0):
         L = lib()
         self._ctx = ctypes.c_void_p()
         opt = default_options()
@@ -158,6 +168,7 @@ class Context:
         opt.chunks_per_thread = int(chunks_per_thread)
         opt.sweep_kernel = int(sweep_kernel)
         opt.wave_lag = int(wave_lag)
+        opt.inject_alloc_fault = int(inject_alloc_fault)
         self.samples = list(samples)
         self.n_samples = len(self.samples)
         self.n_temps = len(self.samples[0].temps)

@@ -80,3 +80,32 @@ def test_single_temperature_has_no_exchange():
     sweeps, passes = ctx.counters()
     assert int(sweeps[0]) == 24 and int(passes[0]) == 4
     ctx.close()
+
+
+def test_allocation_failure_releases_the_partial_context():
+    """Each device allocation of hsg_create made to fail in turn (host-requested,
+    as an out-of-memory would): the call returns HSG_ENOMEM naming the failed
+    allocation and releases what it had allocated (device memory back where it
+    was), and a context created with one more allocation allowed runs a step."""
+    import torch
+    smp = inputs.small_sample(16, n_temps=4, h_r=0.1, disorder_seed=5)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    n = 1
+    while True:
+        try:
+            ctx = hsg.Context([smp], 2, 1, variant=hsg.VARIANT_TWO_PASS,
+                              sweep_kernel=hsg.SWEEP_HALF, inject_alloc_fault=n)
+        except hsg.HsgError as e:
+            assert e.status == 2 and "injected allocation failure" in str(e), str(e)
+            n += 1
+            assert n < 200
+            continue
+        break
+    ctx.step(1)
+    ctx.sync()
+    assert ctx.info().pt_count == 1
+    ctx.close()
+    assert n > 10                       # the create path has that many allocations
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) < (64 << 20)
